@@ -1,0 +1,185 @@
+"""CPU oracle for the checkerboard Metropolis sweep of the 2D Ising model.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference arm of ``bench.py`` may import this package.  The
+product path (``paper_2402_06415_gb300``) never imports it; the two share no
+code.  What the oracle computes, and which passage of arXiv 2402.06415 each
+part follows, is stated in ``ising_oracle.c`` (sweep, Philox, counter map),
+``closed_forms.py`` (Onsager / Yang / Kaufman) and ``exact.py`` (brute force).
+
+The C part is compiled by :func:`build` (plain gcc, no CUDA) into
+``liboracle.so`` next to this file and called through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ising_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+TAG_INIT = 1
+TAG_MET = 2
+TAG_PT = 3
+
+BETA_C = float(np.log(1.0 + np.sqrt(2.0)) / 2.0)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``ising_oracle.c`` with gcc into ``liboracle.so``."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        u32, i32, u64, i64, dbl = (ctypes.c_uint32, ctypes.c_int, ctypes.c_uint64,
+                                   ctypes.c_int64, ctypes.c_double)
+        p = ctypes.c_void_p
+        L.orc_philox4x32_10.argtypes = [p, p, p]
+        L.orc_philox4x32_10.restype = None
+        L.orc_words_per_row.argtypes = [i32]
+        L.orc_words_per_row.restype = i32
+        L.orc_threshold.argtypes = [dbl, i32]
+        L.orc_threshold.restype = u32
+        L.orc_decide.argtypes = [i32, u32, u32, u32]
+        L.orc_decide.restype = i32
+        L.orc_met_planes.argtypes = [u64, u32, u32, i32, u32, p]
+        L.orc_met_planes.restype = None
+        L.orc_assemble_u.argtypes = [p, i32]
+        L.orc_assemble_u.restype = u32
+        L.orc_site_uniform.argtypes = [i32, u64, u32, u32, i32, i32]
+        L.orc_site_uniform.restype = u32
+        L.orc_n_anti.argtypes = [i32, p, i32, i32]
+        L.orc_n_anti.restype = i32
+        L.orc_energy_mag.argtypes = [i32, p, p, p]
+        L.orc_energy_mag.restype = None
+        L.orc_init.argtypes = [i32, u64, u32, p]
+        L.orc_init.restype = None
+        L.orc_half_sweep.argtypes = [i32, u32, u32, u64, u32, u32, i32, p]
+        L.orc_half_sweep.restype = None
+        L.orc_sweep.argtypes = [i32, dbl, u64, u32, u32, i32, i32, p, p, p]
+        L.orc_sweep.restype = i32
+        L.orc_accept_count.argtypes = [i32, u32, u32]
+        L.orc_accept_count.restype = u64
+        L.orc_n_anti_all.argtypes = [i32, i32, p, p]
+        L.orc_n_anti_all.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ---------------------------------------------------------------------------
+# numpy-facing wrappers
+# ---------------------------------------------------------------------------
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for counter ``ctr`` (4 x u32) and ``key`` (2 x u32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def threshold(beta: float, dE: int) -> int:
+    """floor(exp(-beta dE) 2^32) as used by the acceptance test."""
+    return int(lib().orc_threshold(float(beta), int(dE)))
+
+
+def decide(n_anti: int, u: int, thr4: int, thr8: int) -> bool:
+    return bool(lib().orc_decide(int(n_anti), int(u), int(thr4), int(thr8)))
+
+
+def accept_count(n_anti: int, thr4: int, thr8: int) -> int:
+    """Exact count of 32-bit uniforms for which the decision flips."""
+    return int(lib().orc_accept_count(int(n_anti), int(thr4), int(thr8)))
+
+
+def met_planes(seed: int, replica: int, sweep: int, colour: int, group: int) -> np.ndarray:
+    out = np.zeros(32, dtype=np.uint32)
+    lib().orc_met_planes(seed, replica, sweep, colour, group, _ptr(out))
+    return out
+
+
+def assemble_u(planes: np.ndarray, lane: int) -> int:
+    P = np.ascontiguousarray(planes, dtype=np.uint32)
+    return int(lib().orc_assemble_u(_ptr(P), int(lane)))
+
+
+def site_uniform(L: int, seed: int, replica: int, sweep: int, x: int, y: int) -> int:
+    return int(lib().orc_site_uniform(L, seed, replica, sweep, x, y))
+
+
+def n_anti(s: np.ndarray, x: int, y: int) -> int:
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    return int(lib().orc_n_anti(s.shape[0], _ptr(s), x, y))
+
+
+def n_anti_all(S: np.ndarray) -> np.ndarray:
+    """n_anti of every site for a stack of configurations (n, L, L)."""
+    S = np.ascontiguousarray(S, dtype=np.int8)
+    if S.ndim == 2:
+        S = S[None]
+    out = np.zeros(S.shape, dtype=np.int32)
+    lib().orc_n_anti_all(S.shape[1], S.shape[0], _ptr(S), _ptr(out))
+    return out
+
+
+def energy_mag(s: np.ndarray):
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    E = ctypes.c_int64()
+    M = ctypes.c_int64()
+    lib().orc_energy_mag(s.shape[0], _ptr(s), ctypes.byref(E), ctypes.byref(M))
+    return int(E.value), int(M.value)
+
+
+def init(L: int, seed: int, replica: int = 0) -> np.ndarray:
+    """Seeded random start, int8 +-1, row-major [y][x]."""
+    s = np.zeros((L, L), dtype=np.int8)
+    lib().orc_init(L, seed, replica, _ptr(s))
+    return s
+
+
+def half_sweep(s: np.ndarray, beta: float, seed: int, replica: int, sweep: int,
+               colour: int) -> None:
+    """In-place colour-``colour`` half sweep with the uniforms of ``sweep``."""
+    assert s.dtype == np.int8 and s.flags["C_CONTIGUOUS"]
+    lib().orc_half_sweep(s.shape[0], threshold(beta, 4), threshold(beta, 8), seed,
+                         replica, sweep, colour, _ptr(s))
+
+
+def sweep(s: np.ndarray, beta: float, seed: int, n_sweeps: int, t0: int = 0,
+          replica: int = 0, measure_every: int = 1):
+    """Run ``n_sweeps`` sweeps in place; returns the (E, M) records as int64
+    arrays (one record after each sweep t with (t+1) % measure_every == 0)."""
+    assert s.dtype == np.int8 and s.flags["C_CONTIGUOUS"] and s.shape[0] == s.shape[1]
+    L = s.shape[0]
+    n_rec = sum(1 for t in range(t0, t0 + n_sweeps) if (t + 1) % measure_every == 0)
+    E = np.zeros(max(n_rec, 1), dtype=np.int64)
+    M = np.zeros(max(n_rec, 1), dtype=np.int64)
+    got = lib().orc_sweep(L, float(beta), seed, replica, t0, n_sweeps, measure_every,
+                          _ptr(s), _ptr(E), _ptr(M))
+    if got < 0:
+        raise ValueError("oracle sweep rejected its arguments")
+    assert got == n_rec
+    return E[:n_rec], M[:n_rec]
