@@ -1,0 +1,172 @@
+/*
+ * ising.h -- C-ABI of the GB300 checkerboard Metropolis library (libising.so).
+ *
+ * The library runs the data-parallel hot path of arXiv 2402.06415 ("Many-body
+ * computing on Field Programmable Gate Arrays"): the Monte Carlo sweep that the
+ * paper splits into two sublattices updated alternately (Results A, Fig. 2),
+ * with the three per-site steps of its Supplementary MC details: (1) draw a
+ * uniform decision number, (2) compute the local energy change dE and
+ * P(dE) = exp(-beta dE), (3) accept iff p < P.  The model is the 2D
+ * square-lattice Ising ferromagnet (J = 1, h = 0, periodic boundaries), where
+ * dE = 2 s_x sum_n s_n (the integer analogue of the paper's Eq. S1).
+ *
+ * Conventions for every entry point:
+ *  - Return value: an ising_status; ISING_OK (0) on success, a negative code
+ *    otherwise.  On error a message is available from ising_last_error() (per
+ *    calling thread) and no allocation made by the failing call is leaked.
+ *  - Device work is enqueued on the CUDA stream given to ising_create (a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream) and calls
+ *    return before it finishes, except where a call says it synchronises.
+ *  - Host pointers are caller-owned and only read/written during the call.
+ *    Device pointers (the *_device variants) must be device memory of the
+ *    context's device; they are used asynchronously on the context's stream.
+ *  - A context is not thread-safe: serialise calls on one context.
+ *  - Spin layouts:
+ *      int8 spins:  L*L int8 values +1/-1, row-major, index y*L + x.
+ *      packed bits: 2*L*Wc uint32 words, Wc = ceil(L/64); word [c][y][w] holds
+ *                   the colour-c sites of row y with colour index
+ *                   j = 32w .. 32w+31 (colour c = (x+y)&1, x = 2j + ((y+c)&1)),
+ *                   bit (j & 31) set means +1; bits with j >= L/2 are zero.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = the 64-bit
+ *    seed, counter = (group, sweep, replica, tag|colour|block); a site's
+ *    uniform u is assembled from bit (j & 31) of 32 plane words (plane k gives
+ *    bit 31-k).  The flip rule is: n_anti >= 2 antiparallel neighbours -> flip;
+ *    n_anti == 1 -> flip iff u < floor(exp(-4 beta) 2^32);
+ *    n_anti == 0 -> flip iff u < floor(exp(-8 beta) 2^32).  Results are
+ *    bit-identical across kernels, layouts and launch shapes.
+ */
+#ifndef ISING_H
+#define ISING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ising_ctx ising_ctx;
+
+typedef enum {
+  ISING_OK = 0,
+  ISING_EINVAL = -1,    /* bad argument (message says which) */
+  ISING_ENOMEM = -2,    /* device or host allocation failed */
+  ISING_ECUDA = -3,     /* a CUDA call failed (message has the CUDA error) */
+  ISING_ETIMEOUT = -4,  /* a bounded device wait ran out */
+  ISING_EINTERNAL = -5  /* internal consistency check failed */
+} ising_status;
+
+typedef enum { ISING_LAYOUT_I8 = 0, ISING_LAYOUT_BITS = 1 } ising_layout;
+
+typedef enum {
+  ISING_KERNEL_AUTO = 0,     /* pick per lattice (tiled if it applies, else half) */
+  ISING_KERNEL_HALF = 1,     /* one launch per half sweep, spins in global memory */
+  ISING_KERNEL_TILED = 2,    /* packed layout: shared-memory tile + halo, k sweeps per launch */
+  ISING_KERNEL_RESIDENT = 3  /* int8 layout: whole lattice in one CTA's shared memory */
+} ising_kernel;
+
+/* Create a context for one L x L lattice (Results A; the sweep of Fig. 2b).
+ * L: even, 4 <= L <= 65536.  beta: inverse temperature, finite and > 0.
+ * layout: ising_layout.  stream: cudaStream_t (borrowed, may be NULL).
+ * The lattice starts all -1 with seed 0, replica 0, sweep counter 0.
+ * Allocates the lattice (and, for the tiled kernel, a second ping-pong copy)
+ * plus a record ring of 65536 (E, M) entries on the current CUDA device.
+ * Errors: EINVAL (arguments), ENOMEM, ECUDA. */
+int ising_create(ising_ctx** out, int L, double beta, int layout, void* stream);
+
+/* Seeded random start (independent +-1 with probability 1/2, one Philox bit
+ * per site, tag INIT); resets the sweep counter to 0 and clears the records.
+ * Async. */
+int ising_seed(ising_ctx* ctx, uint64_t seed);
+
+/* Set the Philox key (the seed) without touching the spins, the sweep counter
+ * or the records: with ising_set_spins / ising_set_bits and
+ * ising_set_sweep_counter this resumes a saved chain bit-exactly. */
+int ising_set_key(ising_ctx* ctx, uint64_t seed);
+
+/* Replica id r used in the Philox counter (default 0).  Async-safe (host). */
+int ising_set_replica(ising_ctx* ctx, uint32_t replica);
+
+/* Set beta (> 0, finite); recomputes the integer thresholds on the host. */
+int ising_set_beta(ising_ctx* ctx, double beta);
+
+/* Set the sweep counter t of the next sweep (for resuming a chain). */
+int ising_set_sweep_counter(ising_ctx* ctx, int64_t t);
+
+/* Current seed, replica and sweep counter. */
+int ising_get_state(ising_ctx* ctx, uint64_t* seed, uint32_t* replica, int64_t* sweep);
+
+/* Run n_sweeps full sweeps (colour 0 then colour 1; Results A / Fig. 2b)
+ * starting at the current sweep counter t.  After every sweep t with
+ * (t + 1) % measure_every == 0 the energy E = -sum s s' (2 L^2 bonds) and
+ * magnetisation M = sum s are recorded (measure_every = 0: no records).
+ * n_sweeps >= 0, measure_every >= 0, t + n_sweeps < 2^32.  Async. */
+int ising_sweep(ising_ctx* ctx, int n_sweeps, int measure_every);
+
+/* E and M of the current configuration.  Synchronises the stream. */
+int ising_measure(ising_ctx* ctx, int64_t* E, int64_t* M);
+
+/* Number of records taken since the last ising_seed (the ring keeps the last
+ * 65536). */
+int ising_series_count(ising_ctx* ctx, int64_t* count);
+
+/* Copy the last n records (oldest first) into host arrays E_out[n], M_out[n].
+ * 0 <= n <= min(count, 65536).  Synchronises the stream. */
+int ising_series(ising_ctx* ctx, int64_t* E_out, int64_t* M_out, int n);
+
+/* int8 spins to/from host memory (layout above).  get synchronises; set
+ * copies synchronously from the host buffer and validates +-1 values. */
+int ising_get_spins(ising_ctx* ctx, int8_t* host_out);
+int ising_set_spins(ising_ctx* ctx, const int8_t* host_in);
+
+/* Packed words to/from host memory (layout above, 2*L*Wc uint32).  get
+ * synchronises; set copies synchronously and zeroes unused bits. */
+int ising_get_bits(ising_ctx* ctx, uint32_t* host_out);
+int ising_set_bits(ising_ctx* ctx, const uint32_t* host_in);
+
+/* Same as get/set_spins / get/set_bits with device buffers, async on the stream. */
+int ising_get_spins_device(ising_ctx* ctx, int8_t* dev_out);
+int ising_set_spins_device(ising_ctx* ctx, const int8_t* dev_in);
+int ising_get_bits_device(ising_ctx* ctx, uint32_t* dev_out);
+int ising_set_bits_device(ising_ctx* ctx, const uint32_t* dev_in);
+
+/* Words per colour row for lattice size L (ceil(L/64)). */
+int ising_words_per_row(int L);
+
+/* Choose the sweep kernel and its launch shape.  kernel: ising_kernel.
+ * sweeps_per_launch k (tiled: 1..8), tile_rows = number of row strips the
+ * lattice is cut into (tiled), tile_words = words per tile row (tiled; must
+ * divide Wc and be a multiple of 4), grid/block: launch shape (0 = default).
+ * The choice never changes results, only speed.  EINVAL if the kernel does
+ * not apply to this lattice/layout. */
+int ising_set_kernel(ising_ctx* ctx, int kernel, int sweeps_per_launch, int tile_rows,
+                     int tile_words, int grid, int block);
+
+/* The kernel configuration in use (after AUTO resolution). */
+int ising_get_kernel(ising_ctx* ctx, int* kernel, int* sweeps_per_launch, int* tile_rows,
+                     int* tile_words, int* grid, int* block);
+
+/* Integer thresholds floor(exp(-beta dE) 2^32) for dE = 4 and 8 (Supplementary
+ * MC step 2), computed in double on the host. */
+int ising_thresholds(double beta, uint32_t* t4, uint32_t* t8);
+
+/* Launch accounting and live kernel timing.  With timing enabled, every sweep
+ * kernel launch is bracketed by CUDA events on the context's stream;
+ * ising_kernel_time synchronises and returns the summed device time (ms) and
+ * launch count of the sweep kernels since timing was last enabled.
+ * ising_launch_count returns all kernels this context launched so far. */
+int ising_set_timing(ising_ctx* ctx, int enable);
+int ising_kernel_time(ising_ctx* ctx, double* ms, int64_t* launches);
+int ising_launch_count(ising_ctx* ctx, int64_t* launches);
+
+/* Free everything the context owns.  NULL-safe.  Synchronises the stream. */
+int ising_destroy(ising_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* ising_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_H */

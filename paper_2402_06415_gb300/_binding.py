@@ -1,0 +1,339 @@
+"""ctypes binding of libising.so: the C-ABI of include/ising.h, same names.
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+There is no CPU fallback; if libising.so is missing or cannot be loaded every
+call raises.  Functions return None on success and raise :class:`IsingError`
+(with the library's message) on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libising.so")
+
+ISING_OK = 0
+ISING_EINVAL = -1
+ISING_ENOMEM = -2
+ISING_ECUDA = -3
+ISING_ETIMEOUT = -4
+ISING_EINTERNAL = -5
+
+ISING_LAYOUT_I8 = 0
+ISING_LAYOUT_BITS = 1
+
+ISING_KERNEL_AUTO = 0
+ISING_KERNEL_HALF = 1
+ISING_KERNEL_TILED = 2
+ISING_KERNEL_RESIDENT = 3
+
+_STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT",
+                 -5: "EINTERNAL"}
+
+
+class IsingError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s (%d): %s" % (_STATUS_NAMES.get(status, "?"), status, message))
+        self.status = status
+        self.message = message
+
+
+# (name, restype, argtypes) of every exported entry point of include/ising.h
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+_PROTOS = [
+    ("ising_create", _i, [ctypes.POINTER(_p), _i, _d, _i, _p]),
+    ("ising_seed", _i, [_p, _u64]),
+    ("ising_set_key", _i, [_p, _u64]),
+    ("ising_set_replica", _i, [_p, _u32]),
+    ("ising_set_beta", _i, [_p, _d]),
+    ("ising_set_sweep_counter", _i, [_p, _i64]),
+    ("ising_get_state", _i, [_p, _p, _p, _p]),
+    ("ising_sweep", _i, [_p, _i, _i]),
+    ("ising_measure", _i, [_p, _p, _p]),
+    ("ising_series_count", _i, [_p, _p]),
+    ("ising_series", _i, [_p, _p, _p, _i]),
+    ("ising_get_spins", _i, [_p, _p]),
+    ("ising_set_spins", _i, [_p, _p]),
+    ("ising_get_bits", _i, [_p, _p]),
+    ("ising_set_bits", _i, [_p, _p]),
+    ("ising_get_spins_device", _i, [_p, _p]),
+    ("ising_set_spins_device", _i, [_p, _p]),
+    ("ising_get_bits_device", _i, [_p, _p]),
+    ("ising_set_bits_device", _i, [_p, _p]),
+    ("ising_words_per_row", _i, [_i]),
+    ("ising_set_kernel", _i, [_p, _i, _i, _i, _i, _i, _i]),
+    ("ising_get_kernel", _i, [_p, _p, _p, _p, _p, _p, _p]),
+    ("ising_thresholds", _i, [_d, _p, _p]),
+    ("ising_set_timing", _i, [_p, _i]),
+    ("ising_kernel_time", _i, [_p, _p, _p]),
+    ("ising_launch_count", _i, [_p, _p]),
+    ("ising_destroy", _i, [_p]),
+    ("ising_last_error", ctypes.c_char_p, []),
+]
+
+EXPORTED = [name for (name, _, _) in _PROTOS]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libising.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import build as _build
+
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libising.so is missing; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _PROTOS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != ISING_OK:
+        raise IsingError(status, lib().ising_last_error().decode("utf-8", "replace"))
+
+
+def _ptr(a) -> ctypes.c_void_p:
+    """Host numpy array (C-contiguous) or torch tensor -> raw pointer."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if hasattr(a, "is_contiguous") and not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C-ABI)
+# ---------------------------------------------------------------------------
+
+def ising_create(L: int, beta: float, layout: int = ISING_LAYOUT_BITS, stream=None) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().ising_create(ctypes.byref(out), int(L), float(beta), int(layout),
+                              _stream_ptr(stream)))
+    return out.value
+
+
+def ising_seed(ctx: int, seed: int) -> None:
+    _check(lib().ising_seed(ctx, int(seed)))
+
+
+def ising_set_key(ctx: int, seed: int) -> None:
+    _check(lib().ising_set_key(ctx, int(seed)))
+
+
+def ising_set_replica(ctx: int, replica: int) -> None:
+    _check(lib().ising_set_replica(ctx, int(replica)))
+
+
+def ising_set_beta(ctx: int, beta: float) -> None:
+    _check(lib().ising_set_beta(ctx, float(beta)))
+
+
+def ising_set_sweep_counter(ctx: int, t: int) -> None:
+    _check(lib().ising_set_sweep_counter(ctx, int(t)))
+
+
+def ising_get_state(ctx: int):
+    seed, rep, sw = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_int64()
+    _check(lib().ising_get_state(ctx, ctypes.byref(seed), ctypes.byref(rep), ctypes.byref(sw)))
+    return int(seed.value), int(rep.value), int(sw.value)
+
+
+def ising_sweep(ctx: int, n_sweeps: int, measure_every: int = 0) -> None:
+    _check(lib().ising_sweep(ctx, int(n_sweeps), int(measure_every)))
+
+
+def ising_measure(ctx: int):
+    E, M = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ising_measure(ctx, ctypes.byref(E), ctypes.byref(M)))
+    return int(E.value), int(M.value)
+
+
+def ising_series_count(ctx: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().ising_series_count(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def ising_series(ctx: int, n: int | None = None):
+    if n is None:
+        n = min(ising_series_count(ctx), 65536)
+    E = np.zeros(max(n, 1), dtype=np.int64)
+    M = np.zeros(max(n, 1), dtype=np.int64)
+    _check(lib().ising_series(ctx, _ptr(E), _ptr(M), int(n)))
+    return E[:n], M[:n]
+
+
+def ising_get_spins(ctx: int, L: int, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty((L, L), dtype=np.int8)
+    _check(lib().ising_get_spins(ctx, _ptr(out)))
+    return out
+
+
+def ising_set_spins(ctx: int, spins: np.ndarray) -> None:
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    _check(lib().ising_set_spins(ctx, _ptr(s)))
+
+
+def ising_words_per_row(L: int) -> int:
+    return int(lib().ising_words_per_row(int(L)))
+
+
+def ising_get_bits(ctx: int, L: int, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty((2, L, ising_words_per_row(L)), dtype=np.uint32)
+    _check(lib().ising_get_bits(ctx, _ptr(out)))
+    return out
+
+
+def ising_set_bits(ctx: int, words: np.ndarray) -> None:
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    _check(lib().ising_set_bits(ctx, _ptr(w)))
+
+
+def ising_get_spins_device(ctx: int, dev_out) -> None:
+    _check(lib().ising_get_spins_device(ctx, _ptr(dev_out)))
+
+
+def ising_set_spins_device(ctx: int, dev_in) -> None:
+    _check(lib().ising_set_spins_device(ctx, _ptr(dev_in)))
+
+
+def ising_get_bits_device(ctx: int, dev_out) -> None:
+    _check(lib().ising_get_bits_device(ctx, _ptr(dev_out)))
+
+
+def ising_set_bits_device(ctx: int, dev_in) -> None:
+    _check(lib().ising_set_bits_device(ctx, _ptr(dev_in)))
+
+
+def ising_set_kernel(ctx: int, kernel: int, sweeps_per_launch: int = 1, tile_rows: int = 1,
+                     tile_words: int = 4, grid: int = 0, block: int = 0) -> None:
+    _check(lib().ising_set_kernel(ctx, int(kernel), int(sweeps_per_launch), int(tile_rows),
+                                  int(tile_words), int(grid), int(block)))
+
+
+def ising_get_kernel(ctx: int) -> dict:
+    v = [ctypes.c_int() for _ in range(6)]
+    _check(lib().ising_get_kernel(ctx, *[ctypes.byref(x) for x in v]))
+    keys = ["kernel", "sweeps_per_launch", "tile_rows", "tile_words", "grid", "block"]
+    return {k: int(x.value) for k, x in zip(keys, v)}
+
+
+def ising_thresholds(beta: float):
+    t4, t8 = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().ising_thresholds(float(beta), ctypes.byref(t4), ctypes.byref(t8)))
+    return int(t4.value), int(t8.value)
+
+
+def ising_set_timing(ctx: int, enable: bool) -> None:
+    _check(lib().ising_set_timing(ctx, 1 if enable else 0))
+
+
+def ising_kernel_time(ctx: int):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().ising_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)
+
+
+def ising_launch_count(ctx: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().ising_launch_count(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def ising_destroy(ctx: int) -> None:
+    _check(lib().ising_destroy(ctx))
+
+
+def ising_last_error() -> str:
+    return lib().ising_last_error().decode("utf-8", "replace")
+
+
+class Lattice:
+    """Owning wrapper around one ising_ctx (closes it on exit / deletion)."""
+
+    def __init__(self, L: int, beta: float, layout: int = ISING_LAYOUT_BITS, stream=None,
+                 seed: int | None = None, replica: int = 0):
+        self.L = int(L)
+        self.layout = layout
+        self.ctx = ising_create(L, beta, layout, stream)
+        if replica:
+            ising_set_replica(self.ctx, replica)
+        if seed is not None:
+            ising_seed(self.ctx, seed)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ising_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seed(self, seed: int):
+        ising_seed(self.ctx, seed)
+
+    def sweep(self, n: int, measure_every: int = 0):
+        ising_sweep(self.ctx, n, measure_every)
+
+    def measure(self):
+        return ising_measure(self.ctx)
+
+    def series(self, n=None):
+        return ising_series(self.ctx, n)
+
+    def spins(self) -> np.ndarray:
+        return ising_get_spins(self.ctx, self.L)
+
+    def set_spins(self, s):
+        ising_set_spins(self.ctx, s)
+
+    def bits(self) -> np.ndarray:
+        return ising_get_bits(self.ctx, self.L)
+
+    def set_bits(self, w):
+        ising_set_bits(self.ctx, w)
+
+    def set_kernel(self, *a, **k):
+        ising_set_kernel(self.ctx, *a, **k)
+
+    def kernel(self) -> dict:
+        return ising_get_kernel(self.ctx)

@@ -1,0 +1,733 @@
+// C-ABI of libising.so (declarations and contracts in include/ising.h).
+//
+// Host-side control of the checkerboard Metropolis sweep: argument checks,
+// integer thresholds, record bookkeeping, kernel choice and launches on the
+// caller's stream.  No arithmetic of the method runs here except the two
+// thresholds floor(exp(-beta dE) 2^32), dE = 4, 8 (arXiv 2402.06415,
+// Supplementary MC details, step 2), computed once per beta.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "ising.h"
+
+using namespace ising;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int ok() {
+  g_err.clear();
+  return ISING_OK;
+}
+
+// Host-side fault injection for the failure-path tests: ISING_FAULT=alloc
+// makes device allocations fail, ISING_FAULT=launch makes sweep launches fail,
+// ISING_FAULT=copy makes host<->device copies fail.  Never touches the GPU.
+bool fault(const char* what) {
+  const char* f = std::getenv("ISING_FAULT");
+  return f && std::strstr(f, what) != nullptr;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e__ = (expr);                                                            \
+    if (e__ != cudaSuccess)                                                              \
+      return fail(ISING_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, \
+                  __LINE__);                                                             \
+  } while (0)
+
+constexpr int64_t kRecCap = 65536;
+
+uint32_t threshold(double beta, int dE) {
+  const double p = std::exp(-beta * (double)dE);
+  const double t = std::floor(p * 4294967296.0);
+  if (t >= 4294967295.0) return 0xffffffffu;
+  if (t <= 0.0) return 0u;
+  return (uint32_t)t;
+}
+
+int words_per_row(int L) { return (L / 2 + 31) / 32; }
+
+}  // namespace
+
+struct ising_ctx {
+  int L = 0, layout = 0, dev = 0, sms = 0;
+  double beta = 0;
+  uint32_t t4 = 0, t8 = 0;
+  uint64_t seed = 0;
+  uint32_t replica = 0;
+  int64_t sweep = 0;
+  cudaStream_t stream = nullptr;
+  int Wc = 0;
+  uint32_t* bits[2] = {nullptr, nullptr};
+  int cur = 0;
+  int8_t* spins = nullptr;
+  unsigned long long* rec = nullptr;  // [kRecCap][2]: anti-bond count, up-spin count
+  int64_t rec_count = 0;
+  unsigned long long* meas = nullptr;  // [2]
+  int kernel = ISING_KERNEL_HALF, k = 1, tile_rows = 1, tile_words = 4, grid = 0, block = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  int64_t launches = 0;
+
+  int64_t N() const { return (int64_t)L * L; }
+  size_t plane_words() const { return (size_t)2 * L * Wc; }
+  BitsLattice lat(int which) const { return BitsLattice{bits[which], L, Wc, Wc}; }
+  RngParams rng() const {
+    return RngParams{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), replica, t4, t8};
+  }
+};
+
+namespace {
+
+int dev_alloc(void** p, size_t bytes) {
+  if (fault("alloc")) return fail(ISING_ENOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? ISING_ENOMEM : ISING_ECUDA,
+                "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  return ISING_OK;
+}
+
+void free_all(ising_ctx* c) {
+  if (!c) return;
+  for (auto e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  cudaFree(c->bits[0]);
+  cudaFree(c->bits[1]);
+  cudaFree(c->spins);
+  cudaFree(c->rec);
+  cudaFree(c->meas);
+  c->bits[0] = c->bits[1] = nullptr;
+  c->spins = nullptr;
+  c->rec = nullptr;
+  c->meas = nullptr;
+}
+
+bool beta_ok(double beta) { return std::isfinite(beta) && beta > 0.0; }
+
+int check_ctx(ising_ctx* c) {
+  if (!c) return fail(ISING_EINVAL, "null context");
+  return ISING_OK;
+}
+
+// Kernel configuration validity for this lattice.
+int validate_kernel(const ising_ctx* c, int kernel, int k, int tile_rows, int tile_words) {
+  if (c->layout == ISING_LAYOUT_BITS) {
+    if (kernel == ISING_KERNEL_HALF) return ISING_OK;
+    if (kernel == ISING_KERNEL_TILED) {
+      if (c->Wc % 4 != 0 || c->L % 64 != 0)
+        return fail(ISING_EINVAL, "tiled kernel needs L %% 256 == 0 (L = %d)", c->L);
+      if (k < 1 || k > kMaxSweepsPerLaunch)
+        return fail(ISING_EINVAL, "sweeps_per_launch must be in 1..%d", kMaxSweepsPerLaunch);
+      if (tile_words < 4 || tile_words % 4 != 0 || c->Wc % tile_words != 0)
+        return fail(ISING_EINVAL, "tile_words must be a multiple of 4 dividing Wc = %d", c->Wc);
+      if (tile_rows < 1 || tile_rows > c->L)
+        return fail(ISING_EINVAL, "tile_rows must be in 1..L");
+      const size_t smem = tiled_smem_bytes(c->L, k, tile_rows, tile_words);
+      if (smem > 200 * 1024)
+        return fail(ISING_EINVAL, "tile needs %zu bytes of shared memory (> 200 KiB)", smem);
+      return ISING_OK;
+    }
+    return fail(ISING_EINVAL, "kernel %d does not apply to the packed layout", kernel);
+  }
+  if (kernel == ISING_KERNEL_HALF) return ISING_OK;
+  if (kernel == ISING_KERNEL_RESIDENT) {
+    if (resident_i8_smem_bytes(c->L) > 200 * 1024)
+      return fail(ISING_EINVAL, "resident kernel needs L*L <= 200 KiB (L = %d)", c->L);
+    return ISING_OK;
+  }
+  return fail(ISING_EINVAL, "kernel %d does not apply to the int8 layout", kernel);
+}
+
+void resolve_auto(ising_ctx* c) {
+  if (c->layout == ISING_LAYOUT_BITS) {
+    if (c->Wc % 4 == 0 && c->L % 64 == 0 && c->L >= 256) {
+      c->kernel = ISING_KERNEL_TILED;
+      c->k = 2;
+      int tw = 32;
+      while (tw > 4 && c->Wc % tw != 0) tw /= 2;
+      c->tile_words = tw;
+      c->tile_rows = c->L / 64 > 0 ? c->L / 64 : 1;
+    } else {
+      c->kernel = ISING_KERNEL_HALF;
+    }
+  } else {
+    c->kernel = resident_i8_smem_bytes(c->L) <= 64 * 1024 ? ISING_KERNEL_RESIDENT
+                                                          : ISING_KERNEL_HALF;
+  }
+  c->grid = 0;
+  c->block = 0;
+}
+
+int ensure_second_buffer(ising_ctx* c) {
+  if (c->bits[1]) return ISING_OK;
+  void* p = nullptr;
+  int st = dev_alloc(&p, c->plane_words() * sizeof(uint32_t));
+  if (st) return st;
+  c->bits[1] = (uint32_t*)p;
+  cudaError_t e = cudaMemsetAsync(c->bits[1], 0, c->plane_words() * sizeof(uint32_t), c->stream);
+  if (e != cudaSuccess) return fail(ISING_ECUDA, "memset: %s", cudaGetErrorString(e));
+  return ISING_OK;
+}
+
+cudaEvent_t next_event(ising_ctx* c) {
+  if (c->ev_used == c->ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev.push_back(e);
+  }
+  return c->ev[c->ev_used++];
+}
+
+// Brackets one sweep-kernel launch with events when timing is on.
+struct Timed {
+  ising_ctx* c;
+  explicit Timed(ising_ctx* cc) : c(cc) {
+    if (c->timing) {
+      cudaEvent_t e = next_event(c);
+      if (e) cudaEventRecord(e, c->stream);
+    }
+  }
+  ~Timed() {
+    if (c->timing) {
+      cudaEvent_t e = next_event(c);
+      if (e) cudaEventRecord(e, c->stream);
+    }
+  }
+};
+
+int zero_records(ising_ctx* c, int64_t first_rec, int64_t n_rec) {
+  if (n_rec <= 0) return ISING_OK;
+  const int64_t s0 = first_rec % kRecCap;
+  const int64_t n1 = std::min<int64_t>(n_rec, kRecCap - s0);
+  CUDA_TRY(cudaMemsetAsync(c->rec + 2 * s0, 0, (size_t)n1 * 2 * sizeof(unsigned long long),
+                           c->stream));
+  if (n_rec > n1)
+    CUDA_TRY(cudaMemsetAsync(c->rec, 0, (size_t)(n_rec - n1) * 2 * sizeof(unsigned long long),
+                             c->stream));
+  return ISING_OK;
+}
+
+int launch_result(ising_ctx* c, cudaError_t e, const char* what) {
+  ++c->launches;
+  if (e != cudaSuccess) return fail(ISING_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
+  return ISING_OK;
+}
+
+// Runs sweeps [t0, t0 + n) whose records (if any) all fit in the ring.
+int sweep_chunk(ising_ctx* c, int64_t t0, int n, int m) {
+  // record bookkeeping: record r of this chunk belongs to sweep t_r
+  int64_t first_t = -1, n_rec = 0;
+  if (m > 0) {
+    for (int64_t t = t0; t < t0 + n; ++t)
+      if ((t + 1) % m == 0) {
+        if (first_t < 0) first_t = t;
+        ++n_rec;
+      }
+  }
+  const int64_t rec0 = c->rec_count;
+  if (int st = zero_records(c, rec0, n_rec)) return st;
+  auto slot_of = [&](int64_t t) -> int64_t {  // -1 if sweep t is not recorded
+    if (m <= 0 || (t + 1) % m != 0) return -1;
+    return (rec0 + (t - first_t) / m) % kRecCap;
+  };
+  const RngParams rng = c->rng();
+  if (fault("launch")) return fail(ISING_ECUDA, "sweep launch failed (injected)");
+
+  if (c->layout == ISING_LAYOUT_BITS && c->kernel == ISING_KERNEL_HALF) {
+    for (int64_t t = t0; t < t0 + n; ++t) {
+      const int64_t sl = slot_of(t);
+      for (int col = 0; col < 2; ++col) {
+        Timed tm(c);
+        cudaError_t e = launch_half_sweep_bits(c->lat(c->cur), rng, col, (uint32_t)t,
+                                               (col == 1 && sl >= 0) ? c->rec + 2 * sl : nullptr,
+                                               c->grid, c->block, c->stream);
+        if (int st = launch_result(c, e, "half sweep")) return st;
+      }
+    }
+  } else if (c->layout == ISING_LAYOUT_BITS && c->kernel == ISING_KERNEL_TILED) {
+    for (int64_t t = t0; t < t0 + n; t += c->k) {
+      const int kk = (int)std::min<int64_t>(c->k, t0 + n - t);
+      RecordSlots slots;
+      for (int s = 0; s < kMaxSweepsPerLaunch; ++s)
+        slots.slot[s] = s < kk ? (int)slot_of(t + s) : -1;
+      Timed tm(c);
+      cudaError_t e = launch_tiled_sweep_bits(c->lat(c->cur), c->bits[1 - c->cur], rng,
+                                              (uint32_t)t, kk, slots, c->rec, c->tile_rows,
+                                              c->tile_words, c->grid, c->block, c->stream);
+      if (int st = launch_result(c, e, "tiled sweep")) return st;
+      c->cur = 1 - c->cur;
+    }
+  } else if (c->layout == ISING_LAYOUT_I8 && c->kernel == ISING_KERNEL_RESIDENT) {
+    Timed tm(c);
+    cudaError_t e = launch_resident_sweep_i8(
+        c->spins, c->L, rng, (uint32_t)t0, n, m, (uint32_t)(first_t < 0 ? 0 : first_t),
+        rec0 % kRecCap, kRecCap, c->rec, c->stream);
+    if (int st = launch_result(c, e, "resident sweep")) return st;
+  } else {
+    for (int64_t t = t0; t < t0 + n; ++t) {
+      const int64_t sl = slot_of(t);
+      for (int col = 0; col < 2; ++col) {
+        Timed tm(c);
+        cudaError_t e = launch_half_sweep_i8(c->spins, c->L, rng, col, (uint32_t)t,
+                                             (col == 1 && sl >= 0) ? c->rec + 2 * sl : nullptr,
+                                             c->stream);
+        if (int st = launch_result(c, e, "int8 half sweep")) return st;
+      }
+    }
+  }
+  c->rec_count += n_rec;
+  return ISING_OK;
+}
+
+int to_host_sync(ising_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (fault("copy")) return fail(ISING_ECUDA, "device-to-host copy failed (injected)");
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return ISING_OK;
+}
+
+int to_device_sync(ising_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (fault("copy")) return fail(ISING_ECUDA, "host-to-device copy failed (injected)");
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ising_last_error(void) { return g_err.c_str(); }
+
+int ising_words_per_row(int L) { return words_per_row(L); }
+
+int ising_thresholds(double beta, uint32_t* t4, uint32_t* t8) {
+  if (!beta_ok(beta)) return fail(ISING_EINVAL, "beta must be finite and > 0");
+  if (!t4 || !t8) return fail(ISING_EINVAL, "null output pointer");
+  *t4 = threshold(beta, 4);
+  *t8 = threshold(beta, 8);
+  return ok();
+}
+
+int ising_create(ising_ctx** out, int L, double beta, int layout, void* stream) {
+  if (!out) return fail(ISING_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (L < 4 || L > 65536 || (L & 1))
+    return fail(ISING_EINVAL, "L must be even and in [4, 65536] (got %d)", L);
+  if (!beta_ok(beta)) return fail(ISING_EINVAL, "beta must be finite and > 0");
+  if (layout != ISING_LAYOUT_I8 && layout != ISING_LAYOUT_BITS)
+    return fail(ISING_EINVAL, "unknown layout %d", layout);
+  ising_ctx* c = new (std::nothrow) ising_ctx();
+  if (!c) return fail(ISING_ENOMEM, "host allocation failed");
+  c->L = L;
+  c->layout = layout;
+  c->beta = beta;
+  c->t4 = threshold(beta, 4);
+  c->t8 = threshold(beta, 8);
+  c->stream = (cudaStream_t)stream;
+  c->Wc = words_per_row(L);
+  int st = ISING_OK;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(ISING_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+  }
+  void* p = nullptr;
+  if (layout == ISING_LAYOUT_BITS) {
+    st = dev_alloc(&p, c->plane_words() * sizeof(uint32_t));
+    c->bits[0] = (uint32_t*)p;
+  } else {
+    st = dev_alloc(&p, (size_t)c->N());
+    c->spins = (int8_t*)p;
+  }
+  if (!st) {
+    st = dev_alloc(&p, (size_t)kRecCap * 2 * sizeof(unsigned long long));
+    c->rec = (unsigned long long*)p;
+  }
+  if (!st) {
+    st = dev_alloc(&p, 2 * sizeof(unsigned long long));
+    c->meas = (unsigned long long*)p;
+  }
+  if (!st) {
+    resolve_auto(c);
+    if (c->kernel == ISING_KERNEL_TILED) st = ensure_second_buffer(c);
+  }
+  if (!st) {
+    // all -1 start: zero bits / int8 0xff
+    cudaError_t e2 = layout == ISING_LAYOUT_BITS
+                         ? cudaMemsetAsync(c->bits[0], 0, c->plane_words() * 4, c->stream)
+                         : cudaMemsetAsync(c->spins, 0xff, (size_t)c->N(), c->stream);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
+    if (e2 != cudaSuccess) st = fail(ISING_ECUDA, "memset: %s", cudaGetErrorString(e2));
+  }
+  if (st) {
+    std::string msg = g_err;
+    free_all(c);
+    delete c;
+    g_err = msg;
+    return st;
+  }
+  *out = c;
+  return ok();
+}
+
+int ising_destroy(ising_ctx* c) {
+  if (!c) return ok();
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return ok();
+}
+
+int ising_seed(ising_ctx* c, uint64_t seed) {
+  if (int st = check_ctx(c)) return st;
+  c->seed = seed;
+  c->sweep = 0;
+  c->rec_count = 0;
+  cudaError_t e;
+  if (c->layout == ISING_LAYOUT_BITS) {
+    c->cur = 0;
+    e = launch_init_bits(c->lat(0), c->rng(), c->stream);
+  } else {
+    e = launch_init_i8(c->spins, c->L, c->rng(), c->stream);
+  }
+  return launch_result(c, e, "init") ? ISING_ECUDA : ok();
+}
+
+int ising_set_key(ising_ctx* c, uint64_t seed) {
+  if (int st = check_ctx(c)) return st;
+  c->seed = seed;
+  return ok();
+}
+
+int ising_set_replica(ising_ctx* c, uint32_t replica) {
+  if (int st = check_ctx(c)) return st;
+  c->replica = replica;
+  return ok();
+}
+
+int ising_set_beta(ising_ctx* c, double beta) {
+  if (int st = check_ctx(c)) return st;
+  if (!beta_ok(beta)) return fail(ISING_EINVAL, "beta must be finite and > 0");
+  c->beta = beta;
+  c->t4 = threshold(beta, 4);
+  c->t8 = threshold(beta, 8);
+  return ok();
+}
+
+int ising_set_sweep_counter(ising_ctx* c, int64_t t) {
+  if (int st = check_ctx(c)) return st;
+  if (t < 0 || t >= (int64_t)1 << 32) return fail(ISING_EINVAL, "sweep counter out of range");
+  c->sweep = t;
+  return ok();
+}
+
+int ising_get_state(ising_ctx* c, uint64_t* seed, uint32_t* replica, int64_t* sweep) {
+  if (int st = check_ctx(c)) return st;
+  if (seed) *seed = c->seed;
+  if (replica) *replica = c->replica;
+  if (sweep) *sweep = c->sweep;
+  return ok();
+}
+
+int ising_sweep(ising_ctx* c, int n_sweeps, int measure_every) {
+  if (int st = check_ctx(c)) return st;
+  if (n_sweeps < 0) return fail(ISING_EINVAL, "n_sweeps must be >= 0");
+  if (measure_every < 0) return fail(ISING_EINVAL, "measure_every must be >= 0");
+  if (c->sweep + n_sweeps >= ((int64_t)1 << 32))
+    return fail(ISING_EINVAL, "sweep counter would exceed 2^32");
+  // chunk so that no chunk produces more records than the ring holds
+  int64_t t = c->sweep;
+  const int64_t end = c->sweep + n_sweeps;
+  const int64_t max_chunk = measure_every > 0 ? kRecCap * (int64_t)measure_every : end - t;
+  while (t < end) {
+    const int64_t n = std::min<int64_t>(end - t, std::max<int64_t>(max_chunk, 1));
+    int chunk = (int)std::min<int64_t>(n, 1 << 30);
+    if (int st = sweep_chunk(c, t, chunk, measure_every)) return st;
+    t += chunk;
+    c->sweep = t;
+  }
+  return ok();
+}
+
+int ising_measure(ising_ctx* c, int64_t* E, int64_t* M) {
+  if (int st = check_ctx(c)) return st;
+  if (!E || !M) return fail(ISING_EINVAL, "null output pointer");
+  CUDA_TRY(cudaMemsetAsync(c->meas, 0, 2 * sizeof(unsigned long long), c->stream));
+  cudaError_t e = c->layout == ISING_LAYOUT_BITS ? launch_measure_bits(c->lat(c->cur), c->meas, c->stream)
+                                                 : launch_measure_i8(c->spins, c->L, c->meas, c->stream);
+  if (int st = launch_result(c, e, "measure")) return st;
+  unsigned long long h[2];
+  if (int st = to_host_sync(c, h, c->meas, sizeof(h))) return st;
+  *E = 2 * (int64_t)h[0] - 2 * c->N();
+  *M = 2 * (int64_t)h[1] - c->N();
+  return ok();
+}
+
+int ising_series_count(ising_ctx* c, int64_t* count) {
+  if (int st = check_ctx(c)) return st;
+  if (!count) return fail(ISING_EINVAL, "null output pointer");
+  *count = c->rec_count;
+  return ok();
+}
+
+int ising_series(ising_ctx* c, int64_t* E_out, int64_t* M_out, int n) {
+  if (int st = check_ctx(c)) return st;
+  if (n < 0 || n > std::min<int64_t>(c->rec_count, kRecCap))
+    return fail(ISING_EINVAL, "n = %d exceeds the available records", n);
+  if (n == 0) return ok();
+  if (!E_out || !M_out) return fail(ISING_EINVAL, "null output pointer");
+  std::vector<unsigned long long> h((size_t)2 * n);
+  const int64_t first = c->rec_count - n;
+  const int64_t s0 = first % kRecCap;
+  const int64_t n1 = std::min<int64_t>(n, kRecCap - s0);
+  if (int st = to_host_sync(c, h.data(), c->rec + 2 * s0, (size_t)n1 * 16)) return st;
+  if (n > n1)
+    if (int st = to_host_sync(c, h.data() + 2 * n1, c->rec, (size_t)(n - n1) * 16)) return st;
+  for (int i = 0; i < n; ++i) {
+    E_out[i] = 2 * (int64_t)h[2 * i] - 2 * c->N();
+    M_out[i] = 2 * (int64_t)h[2 * i + 1] - c->N();
+  }
+  return ok();
+}
+
+static int get_spins_dev(ising_ctx* c, int8_t* dst) {
+  if (c->layout == ISING_LAYOUT_I8) {
+    CUDA_TRY(cudaMemcpyAsync(dst, c->spins, (size_t)c->N(), cudaMemcpyDeviceToDevice, c->stream));
+    return ISING_OK;
+  }
+  return launch_result(c, launch_unpack_bits(c->lat(c->cur), dst, c->stream), "unpack");
+}
+
+static int set_spins_dev(ising_ctx* c, const int8_t* src) {
+  if (c->layout == ISING_LAYOUT_I8) {
+    CUDA_TRY(cudaMemcpyAsync(c->spins, src, (size_t)c->N(), cudaMemcpyDeviceToDevice, c->stream));
+    return ISING_OK;
+  }
+  return launch_result(c, launch_pack_bits(c->lat(c->cur), src, c->stream), "pack");
+}
+
+static int get_bits_dev(ising_ctx* c, uint32_t* dst) {
+  if (c->layout == ISING_LAYOUT_BITS) {
+    CUDA_TRY(cudaMemcpyAsync(dst, c->bits[c->cur], c->plane_words() * 4, cudaMemcpyDeviceToDevice,
+                             c->stream));
+    return ISING_OK;
+  }
+  BitsLattice tmp{dst, c->L, c->Wc, c->Wc};
+  return launch_result(c, launch_pack_bits(tmp, c->spins, c->stream), "pack");
+}
+
+static int set_bits_dev(ising_ctx* c, const uint32_t* src) {
+  if (c->layout == ISING_LAYOUT_BITS) {
+    CUDA_TRY(cudaMemcpyAsync(c->bits[c->cur], src, c->plane_words() * 4, cudaMemcpyDeviceToDevice,
+                             c->stream));
+    return ISING_OK;
+  }
+  BitsLattice tmp{const_cast<uint32_t*>(src), c->L, c->Wc, c->Wc};
+  return launch_result(c, launch_unpack_bits(tmp, c->spins, c->stream), "unpack");
+}
+
+int ising_get_spins_device(ising_ctx* c, int8_t* dev_out) {
+  if (int st = check_ctx(c)) return st;
+  if (!dev_out) return fail(ISING_EINVAL, "null buffer");
+  if (int st = get_spins_dev(c, dev_out)) return st;
+  return ok();
+}
+
+int ising_set_spins_device(ising_ctx* c, const int8_t* dev_in) {
+  if (int st = check_ctx(c)) return st;
+  if (!dev_in) return fail(ISING_EINVAL, "null buffer");
+  if (int st = set_spins_dev(c, dev_in)) return st;
+  return ok();
+}
+
+int ising_get_bits_device(ising_ctx* c, uint32_t* dev_out) {
+  if (int st = check_ctx(c)) return st;
+  if (!dev_out) return fail(ISING_EINVAL, "null buffer");
+  if (int st = get_bits_dev(c, dev_out)) return st;
+  return ok();
+}
+
+int ising_set_bits_device(ising_ctx* c, const uint32_t* dev_in) {
+  if (int st = check_ctx(c)) return st;
+  if (!dev_in) return fail(ISING_EINVAL, "null buffer");
+  if (int st = set_bits_dev(c, dev_in)) return st;
+  return ok();
+}
+
+int ising_get_spins(ising_ctx* c, int8_t* host_out) {
+  if (int st = check_ctx(c)) return st;
+  if (!host_out) return fail(ISING_EINVAL, "null buffer");
+  if (c->layout == ISING_LAYOUT_I8) {
+    if (int st = to_host_sync(c, host_out, c->spins, (size_t)c->N())) return st;
+    return ok();
+  }
+  void* tmp = nullptr;
+  if (int st = dev_alloc(&tmp, (size_t)c->N())) return st;
+  int st = get_spins_dev(c, (int8_t*)tmp);
+  if (!st) st = to_host_sync(c, host_out, tmp, (size_t)c->N());
+  cudaFree(tmp);
+  return st ? st : ok();
+}
+
+int ising_set_spins(ising_ctx* c, const int8_t* host_in) {
+  if (int st = check_ctx(c)) return st;
+  if (!host_in) return fail(ISING_EINVAL, "null buffer");
+  for (int64_t i = 0; i < c->N(); ++i)
+    if (host_in[i] != 1 && host_in[i] != -1)
+      return fail(ISING_EINVAL, "spin %lld is %d, not +-1", (long long)i, (int)host_in[i]);
+  if (c->layout == ISING_LAYOUT_I8) {
+    if (int st = to_device_sync(c, c->spins, host_in, (size_t)c->N())) return st;
+    return ok();
+  }
+  void* tmp = nullptr;
+  if (int st = dev_alloc(&tmp, (size_t)c->N())) return st;
+  int st = to_device_sync(c, tmp, host_in, (size_t)c->N());
+  if (!st) st = set_spins_dev(c, (const int8_t*)tmp);
+  if (!st) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = fail(ISING_ECUDA, "sync: %s", cudaGetErrorString(e));
+  }
+  cudaFree(tmp);
+  return st ? st : ok();
+}
+
+int ising_get_bits(ising_ctx* c, uint32_t* host_out) {
+  if (int st = check_ctx(c)) return st;
+  if (!host_out) return fail(ISING_EINVAL, "null buffer");
+  if (c->layout == ISING_LAYOUT_BITS) {
+    if (int st = to_host_sync(c, host_out, c->bits[c->cur], c->plane_words() * 4)) return st;
+    return ok();
+  }
+  void* tmp = nullptr;
+  if (int st = dev_alloc(&tmp, c->plane_words() * 4)) return st;
+  int st = get_bits_dev(c, (uint32_t*)tmp);
+  if (!st) st = to_host_sync(c, host_out, tmp, c->plane_words() * 4);
+  cudaFree(tmp);
+  return st ? st : ok();
+}
+
+int ising_set_bits(ising_ctx* c, const uint32_t* host_in) {
+  if (int st = check_ctx(c)) return st;
+  if (!host_in) return fail(ISING_EINVAL, "null buffer");
+  // unused lanes of the last word of each row must be zero; copy-and-mask
+  // only when such lanes exist (L/2 not a multiple of 32)
+  const int nb = c->L / 2 - 32 * (c->Wc - 1);
+  std::vector<uint32_t> masked;
+  const uint32_t* src = host_in;
+  if (nb < 32) {
+    masked.assign(host_in, host_in + c->plane_words());
+    for (size_t r = 0; r < (size_t)2 * c->L; ++r) masked[r * c->Wc + c->Wc - 1] &= (1u << nb) - 1u;
+    src = masked.data();
+  }
+  if (c->layout == ISING_LAYOUT_BITS) {
+    if (int st = to_device_sync(c, c->bits[c->cur], src, c->plane_words() * 4)) return st;
+    return ok();
+  }
+  void* tmp = nullptr;
+  if (int st = dev_alloc(&tmp, c->plane_words() * 4)) return st;
+  int st = to_device_sync(c, tmp, src, c->plane_words() * 4);
+  if (!st) st = set_bits_dev(c, (const uint32_t*)tmp);
+  if (!st) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = fail(ISING_ECUDA, "sync: %s", cudaGetErrorString(e));
+  }
+  cudaFree(tmp);
+  return st ? st : ok();
+}
+
+int ising_set_kernel(ising_ctx* c, int kernel, int k, int tile_rows, int tile_words, int grid,
+                     int block) {
+  if (int st = check_ctx(c)) return st;
+  if (grid < 0 || block < 0 || (block && (block % 32 != 0 || block > 1024)))
+    return fail(ISING_EINVAL, "grid must be >= 0 and block a multiple of 32 in [32, 1024]");
+  if (kernel == ISING_KERNEL_AUTO) {
+    resolve_auto(c);
+    if (c->kernel == ISING_KERNEL_TILED)
+      if (int st = ensure_second_buffer(c)) return st;
+    return ok();
+  }
+  if (kernel == ISING_KERNEL_TILED && block && block != 256)
+    return fail(ISING_EINVAL, "the tiled kernel runs 256 threads per block");
+  if (int st = validate_kernel(c, kernel, k, tile_rows, tile_words)) return st;
+  if (kernel == ISING_KERNEL_TILED)
+    if (int st = ensure_second_buffer(c)) return st;
+  c->kernel = kernel;
+  c->k = kernel == ISING_KERNEL_TILED ? k : 1;
+  c->tile_rows = tile_rows;
+  c->tile_words = tile_words;
+  c->grid = grid;
+  c->block = block;
+  return ok();
+}
+
+int ising_get_kernel(ising_ctx* c, int* kernel, int* k, int* tile_rows, int* tile_words,
+                     int* grid, int* block) {
+  if (int st = check_ctx(c)) return st;
+  if (kernel) *kernel = c->kernel;
+  if (k) *k = c->k;
+  if (tile_rows) *tile_rows = c->tile_rows;
+  if (tile_words) *tile_words = c->tile_words;
+  if (grid) *grid = c->grid;
+  if (block) *block = c->block;
+  return ok();
+}
+
+int ising_set_timing(ising_ctx* c, int enable) {
+  if (int st = check_ctx(c)) return st;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->timing = enable != 0;
+  c->ev_used = 0;
+  return ok();
+}
+
+int ising_kernel_time(ising_ctx* c, double* ms, int64_t* launches) {
+  if (int st = check_ctx(c)) return st;
+  if (!ms || !launches) return fail(ISING_EINVAL, "null output pointer");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float f = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&f, c->ev[i], c->ev[i + 1]));
+    total += f;
+  }
+  *ms = total;
+  *launches = (int64_t)(c->ev_used / 2);
+  return ok();
+}
+
+int ising_launch_count(ising_ctx* c, int64_t* launches) {
+  if (int st = check_ctx(c)) return st;
+  if (!launches) return fail(ISING_EINVAL, "null output pointer");
+  *launches = c->launches;
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Internal launchers shared by the C-ABI layer (api.cu) and the kernel files.
+// Every launcher enqueues on `stream` and returns the launch status.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ising {
+
+// Per-sweep record slots for one launch that covers up to kMaxSweepsPerLaunch
+// sweeps: slot[s] >= 0 is the index (in units of 2 x u64: anti-bond count,
+// up-spin count) where sweep s of the launch adds its observables; -1 = none.
+constexpr int kMaxSweepsPerLaunch = 8;
+struct RecordSlots {
+  int slot[kMaxSweepsPerLaunch];
+};
+
+struct BitsLattice {
+  uint32_t* planes;  // [2][L][pitch] words; colour c plane at planes + c * L * pitch
+  int L;             // even, >= 4
+  int Wc;            // words per colour row = ceil(L / 64)
+  int pitch;         // row pitch in words (>= Wc)
+};
+
+struct RngParams {
+  uint32_t key0, key1;  // lo32 / hi32 of the seed
+  uint32_t replica;
+  uint32_t t4, t8;      // thresholds for dE = 4, 8
+};
+
+// ---- bit layout (k_bits.cu) ----
+cudaError_t launch_init_bits(const BitsLattice& lat, const RngParams& rng, cudaStream_t s);
+cudaError_t launch_half_sweep_bits(const BitsLattice& lat, const RngParams& rng, int colour,
+                                   uint32_t sweep, unsigned long long* rec /* or null */,
+                                   int grid, int block, cudaStream_t s);
+// Temporal blocking: k sweeps per launch, shared-memory tile with halo.  Reads
+// `in`, writes `out` (must differ).  Requires Wc % tile_words == 0,
+// tile_words % 4 == 0, pitch == Wc, L % 2 == 0, tile_rows_count <= L.
+cudaError_t launch_tiled_sweep_bits(const BitsLattice& in, uint32_t* out, const RngParams& rng,
+                                    uint32_t sweep0, int k, const RecordSlots& slots,
+                                    unsigned long long* rec_base, int n_tile_rows,
+                                    int tile_words, int grid, int block, cudaStream_t s);
+size_t tiled_smem_bytes(int L, int k, int n_tile_rows, int tile_words);
+cudaError_t launch_measure_bits(const BitsLattice& lat, unsigned long long* out2,
+                                cudaStream_t s);
+cudaError_t launch_unpack_bits(const BitsLattice& lat, int8_t* spins, cudaStream_t s);
+cudaError_t launch_pack_bits(const BitsLattice& lat, const int8_t* spins, cudaStream_t s);
+
+// ---- int8 layout (k_i8.cu) ----
+cudaError_t launch_init_i8(int8_t* s, int L, const RngParams& rng, cudaStream_t st);
+// Whole lattice resident in one CTA's shared memory; n sweeps in one launch.
+cudaError_t launch_resident_sweep_i8(int8_t* s, int L, const RngParams& rng, uint32_t sweep0,
+                                     int n_sweeps, int measure_every, uint32_t rec_first_t,
+                                     long long rec_slot0, long long rec_cap,
+                                     unsigned long long* rec, cudaStream_t st);
+size_t resident_i8_smem_bytes(int L);
+cudaError_t launch_half_sweep_i8(int8_t* s, int L, const RngParams& rng, int colour,
+                                 uint32_t sweep, unsigned long long* rec, cudaStream_t st);
+cudaError_t launch_measure_i8(const int8_t* s, int L, unsigned long long* out2, cudaStream_t st);
+
+}  // namespace ising
