@@ -354,15 +354,19 @@ def run_ours(args):
 
 
 def main(argv=None):
+    global SWEEPS_PER_STEP
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=SWEEPS_PER_STEP,
+                    help="sweeps per step (default 1000; smaller only for profiling runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    SWEEPS_PER_STEP = args.sweeps
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
