@@ -159,6 +159,33 @@ int ising_set_timing(ising_ctx* ctx, int enable);
 int ising_kernel_time(ising_ctx* ctx, double* ms, int64_t* launches);
 int ising_launch_count(ising_ctx* ctx, int64_t* launches);
 
+/* Allocation-free sweep (no counterpart in the paper: an interface for
+ * callers that may not allocate device memory while they run, e.g. a host
+ * application that gives all device memory to its own allocator, a real-time
+ * loop where cudaMalloc/cudaFree would stall the stream, or a plug-in that may
+ * not own device memory).  Runs n_sweeps sweeps of the packed tiled kernel on
+ * a caller-owned lattice: dev_in and dev_out are device buffers in the packed
+ * layout (2*L*(L/64) uint32, may be the same buffer), the sweep counter starts
+ * at sweep0, and after every sweep t with (t+1) % measure_every == 0 the E and
+ * M of that sweep go to the device arrays dev_E[i], dev_M[i] (i = record index
+ * in this call; measure_every = 0: no records, dev_E/dev_M may be NULL).
+ * sweeps_per_launch: 1..8.  Results are bit-identical to ising_sweep with the
+ * tiled kernel.
+ * Allocates nothing: scratch (a second lattice copy and the record
+ * accumulators) is a static device array of about 8 MiB that every GPU loading
+ * libising.so holds until the process exits.  Hence L must be a multiple of
+ * 256 and at most 8192, and at most 4096 records per call (EINVAL otherwise).
+ * The first call on a device looks up the array's device address (once per
+ * device, current device); make that first call before any stream capture.
+ * All calls on a device share the array and leave their contents in it (the
+ * record accumulators are cleared at the start of every call); calls that
+ * overlap on the GPU race on it, so order them on one stream.  Async on
+ * `stream`; errors: EINVAL, ECUDA (message from ising_last_error()). */
+int ising_sweep_bits_noalloc(const uint32_t* dev_in, uint32_t* dev_out, int L, double beta,
+                             uint64_t seed, uint32_t replica, int64_t sweep0, int n_sweeps,
+                             int measure_every, int64_t* dev_E, int64_t* dev_M,
+                             int sweeps_per_launch, void* stream);
+
 /* Free everything the context owns.  NULL-safe.  Synchronises the stream. */
 int ising_destroy(ising_ctx* ctx);
 

@@ -75,6 +75,7 @@ _PROTOS = [
     ("ising_set_timing", _i, [_p, _i]),
     ("ising_kernel_time", _i, [_p, _p, _p]),
     ("ising_launch_count", _i, [_p, _p]),
+    ("ising_sweep_bits_noalloc", _i, [_p, _p, _i, _d, _u64, _u32, _i64, _i, _i, _p, _p, _i, _p]),
     ("ising_destroy", _i, [_p]),
     ("ising_last_error", ctypes.c_char_p, []),
 ]
@@ -268,6 +269,18 @@ def ising_launch_count(ctx: int) -> int:
     n = ctypes.c_int64()
     _check(lib().ising_launch_count(ctx, ctypes.byref(n)))
     return int(n.value)
+
+
+def ising_sweep_bits_noalloc(dev_in, dev_out, L: int, beta: float, seed: int, replica: int,
+                             sweep0: int, n_sweeps: int, measure_every: int = 0, dev_E=None,
+                             dev_M=None, sweeps_per_launch: int = 2, stream=None) -> None:
+    """Allocation-free sweep on caller-owned device buffers (see include/ising.h)."""
+    E = _ptr(dev_E) if dev_E is not None else ctypes.c_void_p(0)
+    M = _ptr(dev_M) if dev_M is not None else ctypes.c_void_p(0)
+    _check(lib().ising_sweep_bits_noalloc(_ptr(dev_in), _ptr(dev_out), int(L), float(beta),
+                                          int(seed), int(replica), int(sweep0), int(n_sweeps),
+                                          int(measure_every), E, M, int(sweeps_per_launch),
+                                          _stream_ptr(stream)))
 
 
 def ising_destroy(ctx: int) -> None:

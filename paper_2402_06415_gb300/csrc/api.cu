@@ -320,6 +320,10 @@ int to_device_sync(ising_ctx* c, void* dst, const void* src, size_t bytes) {
 
 }  // namespace
 
+namespace ising {
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+}  // namespace ising
+
 extern "C" {
 
 const char* ising_last_error(void) { return g_err.c_str(); }

@@ -46,6 +46,9 @@ cudaError_t launch_measure_bits(const BitsLattice& lat, unsigned long long* out2
 cudaError_t launch_unpack_bits(const BitsLattice& lat, int8_t* spins, cudaStream_t s);
 cudaError_t launch_pack_bits(const BitsLattice& lat, const int8_t* spins, cudaStream_t s);
 
+// Sets the message returned by ising_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // ---- int8 layout (k_i8.cu) ----
 cudaError_t launch_init_i8(int8_t* s, int L, const RngParams& rng, cudaStream_t st);
 // Whole lattice resident in one CTA's shared memory; n sweeps in one launch.
