@@ -39,16 +39,23 @@ SEED = 1
 
 # Tiled-kernel launch shape for L = 16384 (sweeps per launch, row strips,
 # words per tile row); chosen by the tuning sweep recorded in the design doc.
-BENCH_KERNEL = {"kernel": 2, "k": 2, "tile_rows": 256, "tile_words": 32}
+BENCH_KERNEL = {"kernel": 2, "k": 3, "tile_rows": 152, "tile_words": 32}
 
 
-def configure_kernel(lat) -> dict:
-    """Apply the benchmark's kernel configuration to a Lattice (L = 16384)."""
+def configure_kernel(lat, tune: bool = False) -> dict:
+    """Apply the benchmark's kernel configuration to a Lattice (L = 16384):
+    the autotuner's choice among the warp-per-row tiled shapes when tune is
+    set (cached per GPU), else BENCH_KERNEL (or ISING_BENCH_KERNEL=k,rows,words)."""
     cfg = dict(BENCH_KERNEL)
     env = os.environ.get("ISING_BENCH_KERNEL")
     if env:
         k, tr, tw = (int(v) for v in env.split(","))
         cfg.update(k=k, tile_rows=tr, tile_words=tw)
+    elif tune:
+        from paper_2402_06415_gb300 import autotune
+
+        cands = [c for c in autotune.candidates(lat.L) if c["tile_words"] in (32, 64)]
+        cfg = dict(autotune.tune(lat.L, cands=cands)["config"])
     lat.set_kernel(cfg["kernel"], cfg["k"], cfg["tile_rows"], cfg["tile_words"])
     return cfg
 
@@ -225,7 +232,7 @@ def run_ours(args):
     L = L_BENCH
     lat = ising.Lattice(L, BETAS[0], ising.ISING_LAYOUT_BITS, stream=stream)
     ising.ising_set_replica(lat.ctx, rank)
-    cfg = configure_kernel(lat)
+    cfg = configure_kernel(lat, tune=not args.no_tune)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def one_step(i, timed_events):
@@ -316,7 +323,8 @@ def run_ours(args):
     roofline = {
         "bound": "alu", "achieved": alu_gops, "peak": peak, "unit": "Gop/s",
         "frac": alu_gops / peak, "traffic": None,
-        "kernel": "k_tiled_bits<%d>" % cfg["k"],
+        "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
+                   if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
         "peak_source": "152 SMs x 128 INT32 lanes x median SM clock under load",
         "per_launch_ms": per_launch_ms, "launches": kern_launches,
         "hbm_packed_accounting": {"achieved_gbs": hbm_gbs,
@@ -353,6 +361,68 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """4096 replicas (64 ladders x 64 betas in [0.35, 0.50], sizes drawn from
+    {16, ..., 128}), exchanges every 10 sweeps; one step = one graph replay of
+    a persistent launch covering all sweeps of the step."""
+    import numpy as np
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    Ls = workloads.batch_ladder_sizes()
+    betas = workloads.batch_betas()
+    pt = workloads.BATCH_PT_EVERY
+    sweeps = args.sweeps
+    stream = torch.cuda.current_stream()
+    b = ising.Batch(Ls, betas, pt, stream=stream, seed=SEED)
+    if args.batch_kernel:
+        wpi, thr = (int(v) for v in args.batch_kernel.split(","))
+        ising.ising_batch_set_kernel(b.h, wpi, thr, 0)
+    ising.ising_batch_capture(b.h, sweeps)
+    for _ in range(args.warmup):
+        b.run(sweeps)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(sweeps)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st, sw = ising.ising_batch_status(b.h)
+    ms = sum(a.elapsed_time(c) for a, c in times)
+    sites = sum(L * L for L in Ls) * len(betas)
+    value = sites * sweeps * args.steps / (ms * 1e6)
+    acc, att = b.swap_counts()
+    rate = (acc[:, :-1].sum(0) / np.maximum(att[:, :-1].sum(0), 1)).tolist()
+    info = ising.ising_batch_info(b.h)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batched: 4096 replicas (64 ladders x 64 betas in [0.35,0.50]), "
+                               "L per ladder from {16..128}, PT every 10 sweeps, one persistent "
+                               "launch per step replayed from a CUDA graph",
+                   "sweeps_per_step": sweeps, "replica_sites": sites, "items": info["items"],
+                   "grid": info["grid"], "status": st, "device_sweeps": sw},
+        "pt_accept_rate_by_pair": [round(x, 4) for x in rate],
+        "gpu_launches": args.steps, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main(argv=None):
     global SWEEPS_PER_STEP
     ap = argparse.ArgumentParser()
@@ -361,6 +431,13 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the fixed kernel shape instead of the autotuner's choice")
+    ap.add_argument("--workload", choices=["plain", "batch"], default="plain",
+                    help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
+                         "parallel tempering")
+    ap.add_argument("--batch-kernel", default="",
+                    help="batch work decomposition 'words_per_item,threads'")
     ap.add_argument("--sweeps", type=int, default=SWEEPS_PER_STEP,
                     help="sweeps per step (default 1000; smaller only for profiling runs)")
     args = ap.parse_args(argv)
@@ -369,6 +446,8 @@ def main(argv=None):
     SWEEPS_PER_STEP = args.sweeps
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -186,6 +186,77 @@ int ising_sweep_bits_noalloc(const uint32_t* dev_in, uint32_t* dev_out, int L, d
                              int measure_every, int64_t* dev_E, int64_t* dev_M,
                              int sweeps_per_launch, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched replicas with parallel tempering (no counterpart in the paper,
+ * whose MC runs one chain per lattice; the sweep each replica runs is the
+ * paper's checkerboard sweep, Results A / Supplementary MC steps 1-3).
+ * n_ladders ladders of n_beta replicas each; ladder l has lattice size L[l]
+ * (even, 4..256) and replica i of ladder l uses Philox replica id
+ * l * n_beta + i.  betas (ascending, > 0) are the temperature slots shared by
+ * all ladders.  Every sweep runs each replica at the beta of its slot; after
+ * every sweep t with (t + 1) % pt_every == 0 each ladder performs exchange step
+ * n = (t + 1) / pt_every - 1 over the slot pairs (a, a+1), a = n % 2, n % 2 + 2,
+ * ...: the two configurations swap slots iff u < floor(min(1,
+ * exp[(beta_a - beta_{a+1}) (E_a - E_{a+1})]) 2^32), u = word 0 of Philox
+ * counter (a, n, l, PT << 16) under the seed key.  A run is one persistent
+ * cooperative kernel launch; the state lives on the device.
+ * ------------------------------------------------------------------------ */
+typedef struct ising_batch ising_batch;
+
+/* Create (device allocations for all replicas) and seed with 0.  stream:
+ * cudaStream_t, borrowed.  Errors: EINVAL, ENOMEM, ECUDA. */
+int ising_batch_create(ising_batch** out, int n_ladders, const int* L, int n_beta,
+                       const double* betas, int pt_every, void* stream);
+
+/* Seeded random start of every replica (the INIT stream of its replica id),
+ * identity slot assignment, zero counters, sweep counter 0.  Synchronises. */
+int ising_batch_seed(ising_batch* b, uint64_t seed);
+
+/* Work decomposition: replica words per work item (16..16384, default 512),
+ * threads per CTA (128 or 256; 0 = 256), grid (0 = all resident CTAs).  Never
+ * changes results.  Drops a captured graph. */
+int ising_batch_set_kernel(ising_batch* b, int words_per_item, int threads, int grid);
+
+/* Keep E, M and the slot of every replica at each exchange step in a device
+ * ring of `capacity` steps (0 = off).  Drops a captured graph. */
+int ising_batch_set_series(ising_batch* b, int capacity);
+
+/* Run n_sweeps sweeps (with the exchange steps that fall in them) in one
+ * persistent launch, or by replaying the graph captured for this n_sweeps.
+ * Async; check ising_batch_status for a barrier timeout. */
+int ising_batch_run(ising_batch* b, int n_sweeps);
+
+/* Capture one run of n_sweeps into a CUDA graph; later ising_batch_run(b,
+ * n_sweeps) calls replay it (the sweep counter lives on the device, so every
+ * replay continues the chain). */
+int ising_batch_capture(ising_batch* b, int n_sweeps);
+
+/* Synchronise and read the device status word (0 ok; ETIMEOUT if a grid
+ * barrier ran out of its ~2 s budget, EINTERNAL on an impossible energy
+ * difference) and the device sweep counter. */
+int ising_batch_status(ising_batch* b, int* status, int64_t* sweep);
+
+/* Host copies of the slot assignment perm[l * n_beta + a] (replica index at
+ * slot a of ladder l) and of E, M of every replica after its last round. */
+int ising_batch_state(ising_batch* b, int32_t* perm, int64_t* E, int64_t* M);
+
+/* Accepted and attempted exchanges of pair (a, a+1) of ladder l at index
+ * l * n_beta + a (host arrays of n_ladders * n_beta). */
+int ising_batch_swap_counts(ising_batch* b, int64_t* accepts, int64_t* attempts);
+
+/* The last n_steps recorded exchange steps, oldest first: E, M and slot of
+ * every replica (host arrays of n_steps * n_ladders * n_beta). */
+int ising_batch_series(ising_batch* b, int n_steps, int32_t* E, int32_t* M, int16_t* slot);
+
+/* int8 spins (L*L, row-major) of replica i of ladder l.  Synchronises. */
+int ising_batch_get_spins(ising_batch* b, int ladder, int replica, int8_t* host_out);
+
+/* Work items, CTAs used, host-side sweep counter. */
+int ising_batch_info(ising_batch* b, int* n_items, int* grid, int64_t* sweep);
+
+/* Free everything (NULL-safe; synchronises). */
+int ising_batch_destroy(ising_batch* b);
+
 /* Free everything the context owns.  NULL-safe.  Synchronises the stream. */
 int ising_destroy(ising_ctx* ctx);
 

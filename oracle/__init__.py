@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
         L.orc_accept_count.restype = u64
         L.orc_n_anti_all.argtypes = [i32, i32, p, p]
         L.orc_n_anti_all.restype = None
+        L.orc_pt_step.argtypes = [i32, p, u64, u32, u32, p, p, p, p]
+        L.orc_pt_step.restype = None
         _lib = L
     return _lib
 
@@ -183,3 +185,62 @@ def sweep(s: np.ndarray, beta: float, seed: int, n_sweeps: int, t0: int = 0,
         raise ValueError("oracle sweep rejected its arguments")
     assert got == n_rec
     return E[:n_rec], M[:n_rec]
+
+
+# ---------------------------------------------------------------------------
+# Parallel-tempering ladders (replica exchange between adjacent betas)
+# ---------------------------------------------------------------------------
+
+def pt_step(betas, seed: int, ladder: int, n_step: int, E, perm, accepts=None, attempts=None):
+    """One exchange step of one ladder, in place on perm (and the counters)."""
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    Ea = np.ascontiguousarray(E, dtype=np.int64)
+    assert perm.dtype == np.int32 and perm.flags["C_CONTIGUOUS"]
+    acc = accepts if accepts is not None else np.zeros(len(b), dtype=np.int64)
+    att = attempts if attempts is not None else np.zeros(len(b), dtype=np.int64)
+    lib().orc_pt_step(len(b), _ptr(b), seed, ladder, n_step, _ptr(Ea), _ptr(perm), _ptr(acc),
+                      _ptr(att))
+
+
+def run_ladders(Ls, betas, seed: int, n_sweeps: int, pt_every: int, ladder_ids=None,
+                record=False):
+    """Serial reference of the batched run: ladder l has len(betas) replicas of
+    size Ls[l] x Ls[l]; replica i of ladder id l has Philox replica id
+    l * len(betas) + i and starts from the seeded random start.  Every sweep t
+    runs each replica at the beta of its current slot; after sweeps t with
+    (t + 1) % pt_every == 0 every ladder does exchange step (t + 1) / pt_every - 1.
+    Returns (spins, perm, E, M, accepts, attempts[, series]) with E, M of the last
+    sweep; series (record=True) lists (E, M, slot) arrays at every exchange step."""
+    nb = len(betas)
+    ids = list(ladder_ids) if ladder_ids is not None else list(range(len(Ls)))
+    nl = len(Ls)
+    spins = [[init(Ls[k], seed, ids[k] * nb + i) for i in range(nb)] for k in range(nl)]
+    perm = np.tile(np.arange(nb, dtype=np.int32), (nl, 1))
+    acc = np.zeros((nl, nb), dtype=np.int64)
+    att = np.zeros((nl, nb), dtype=np.int64)
+    E = np.zeros((nl, nb), dtype=np.int64)
+    M = np.zeros((nl, nb), dtype=np.int64)
+    series = []
+    t = 0
+    while t < n_sweeps:
+        n = min(pt_every - (t % pt_every), n_sweeps - t)
+        slots = np.zeros((nl, nb), dtype=np.int32)
+        for k in range(nl):
+            slot_of = np.empty(nb, dtype=np.int32)
+            slot_of[perm[k]] = np.arange(nb, dtype=np.int32)
+            slots[k] = slot_of
+            for i in range(nb):
+                e, m = sweep(spins[k][i], betas[slot_of[i]], seed, n, t0=t,
+                             replica=ids[k] * nb + i, measure_every=1)
+                E[k, i], M[k, i] = e[-1], m[-1]
+        t += n
+        if t % pt_every == 0:
+            if record:
+                series.append((E.copy(), M.copy(), slots.copy()))
+            for k in range(nl):
+                row = np.ascontiguousarray(perm[k])
+                pt_step(betas, seed, ids[k], t // pt_every - 1, E[k], row, acc[k], att[k])
+                perm[k] = row
+    if record:
+        return spins, perm, E, M, acc, att, series
+    return spins, perm, E, M, acc, att

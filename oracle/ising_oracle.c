@@ -260,3 +260,38 @@ void orc_n_anti_all(int L, int n, const int8_t *s, int32_t *out)
                 out[(size_t)k * L * L + (size_t)y * L + x] = orc_n_anti(L, sk, x, y);
     }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Parallel tempering (replica exchange) between adjacent temperatures of  */
+/* one ladder.  Not in the paper (its MC runs one chain per lattice); the  */
+/* textbook exchange rule: the configurations at slots a and a+1 swap with */
+/* probability min(1, exp[(beta_a - beta_{a+1}) (E_a - E_{a+1})]).  Here   */
+/* the swap is accepted iff u < floor(min(1, exp(d)) 2^32), u = word 0 of  */
+/* Philox(a, n_step, ladder, PT<<16).  Step n_step pairs slots             */
+/* (a, a+1) with a = n_step & 1, (n_step & 1) + 2, ...                     */
+/* perm[a] = replica index at slot a; E[i] = energy of replica i.          */
+/* ---------------------------------------------------------------------- */
+void orc_pt_step(int n_beta, const double *betas, uint64_t seed, uint32_t ladder,
+                 uint32_t n_step, const int64_t *E, int32_t *perm, int64_t *accepts,
+                 int64_t *attempts)
+{
+    for (int a = (int)(n_step & 1u); a + 1 < n_beta; a += 2) {
+        int32_t ra = perm[a], rb = perm[a + 1];
+        double d = (betas[a] - betas[a + 1]) * (double)(E[ra] - E[rb]);
+        uint64_t thr;
+        if (d >= 0.0) {
+            thr = 4294967296ull;
+        } else {
+            double t = floor(exp(d) * 4294967296.0);
+            thr = t <= 0.0 ? 0ull : (uint64_t)t;
+        }
+        uint32_t o[4];
+        orc_block(seed, (uint32_t)a, n_step, ladder, ORC_TAG_PT, 0, 0, o);
+        if (attempts) attempts[a] += 1;
+        if ((uint64_t)o[0] < thr) {
+            perm[a] = rb;
+            perm[a + 1] = ra;
+            if (accepts) accepts[a] += 1;
+        }
+    }
+}

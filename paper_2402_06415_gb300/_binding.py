@@ -76,6 +76,19 @@ _PROTOS = [
     ("ising_kernel_time", _i, [_p, _p, _p]),
     ("ising_launch_count", _i, [_p, _p]),
     ("ising_sweep_bits_noalloc", _i, [_p, _p, _i, _d, _u64, _u32, _i64, _i, _i, _p, _p, _i, _p]),
+    ("ising_batch_create", _i, [ctypes.POINTER(_p), _i, _p, _i, _p, _i, _p]),
+    ("ising_batch_seed", _i, [_p, _u64]),
+    ("ising_batch_set_kernel", _i, [_p, _i, _i, _i]),
+    ("ising_batch_set_series", _i, [_p, _i]),
+    ("ising_batch_run", _i, [_p, _i]),
+    ("ising_batch_capture", _i, [_p, _i]),
+    ("ising_batch_status", _i, [_p, _p, _p]),
+    ("ising_batch_state", _i, [_p, _p, _p, _p]),
+    ("ising_batch_swap_counts", _i, [_p, _p, _p]),
+    ("ising_batch_series", _i, [_p, _i, _p, _p, _p]),
+    ("ising_batch_get_spins", _i, [_p, _i, _i, _p]),
+    ("ising_batch_info", _i, [_p, _p, _p, _p]),
+    ("ising_batch_destroy", _i, [_p]),
     ("ising_destroy", _i, [_p]),
     ("ising_last_error", ctypes.c_char_p, []),
 ]
@@ -350,3 +363,128 @@ class Lattice:
 
     def kernel(self) -> dict:
         return ising_get_kernel(self.ctx)
+
+
+# ---------------------------------------------------------------------------
+# batched replicas with parallel tempering
+# ---------------------------------------------------------------------------
+
+def ising_batch_create(Ls, betas, pt_every: int, stream=None) -> int:
+    Lh = np.ascontiguousarray(Ls, dtype=np.int32)
+    bh = np.ascontiguousarray(betas, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(lib().ising_batch_create(ctypes.byref(out), len(Lh), _ptr(Lh), len(bh), _ptr(bh),
+                                    int(pt_every), _stream_ptr(stream)))
+    return out.value
+
+
+def ising_batch_seed(b: int, seed: int) -> None:
+    _check(lib().ising_batch_seed(b, int(seed)))
+
+
+def ising_batch_set_kernel(b: int, words_per_item: int = 512, threads: int = 256,
+                           grid: int = 0) -> None:
+    _check(lib().ising_batch_set_kernel(b, int(words_per_item), int(threads), int(grid)))
+
+
+def ising_batch_set_series(b: int, capacity: int) -> None:
+    _check(lib().ising_batch_set_series(b, int(capacity)))
+
+
+def ising_batch_run(b: int, n_sweeps: int) -> None:
+    _check(lib().ising_batch_run(b, int(n_sweeps)))
+
+
+def ising_batch_capture(b: int, n_sweeps: int) -> None:
+    _check(lib().ising_batch_capture(b, int(n_sweeps)))
+
+
+def ising_batch_status(b: int):
+    st, sw = ctypes.c_int(), ctypes.c_int64()
+    _check(lib().ising_batch_status(b, ctypes.byref(st), ctypes.byref(sw)))
+    return int(st.value), int(sw.value)
+
+
+def ising_batch_state(b: int, n_rep: int):
+    perm = np.zeros(n_rep, dtype=np.int32)
+    E = np.zeros(n_rep, dtype=np.int64)
+    M = np.zeros(n_rep, dtype=np.int64)
+    _check(lib().ising_batch_state(b, _ptr(perm), _ptr(E), _ptr(M)))
+    return perm, E, M
+
+
+def ising_batch_swap_counts(b: int, n_rep: int):
+    acc = np.zeros(n_rep, dtype=np.int64)
+    att = np.zeros(n_rep, dtype=np.int64)
+    _check(lib().ising_batch_swap_counts(b, _ptr(acc), _ptr(att)))
+    return acc, att
+
+
+def ising_batch_series(b: int, n_steps: int, n_rep: int):
+    E = np.zeros((max(n_steps, 1), n_rep), dtype=np.int32)
+    M = np.zeros((max(n_steps, 1), n_rep), dtype=np.int32)
+    S = np.zeros((max(n_steps, 1), n_rep), dtype=np.int16)
+    _check(lib().ising_batch_series(b, int(n_steps), _ptr(E), _ptr(M), _ptr(S)))
+    return E[:n_steps], M[:n_steps], S[:n_steps]
+
+
+def ising_batch_get_spins(b: int, ladder: int, replica: int, L: int) -> np.ndarray:
+    out = np.empty((L, L), dtype=np.int8)
+    _check(lib().ising_batch_get_spins(b, int(ladder), int(replica), _ptr(out)))
+    return out
+
+
+def ising_batch_info(b: int):
+    n, g, sw = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(lib().ising_batch_info(b, ctypes.byref(n), ctypes.byref(g), ctypes.byref(sw)))
+    return {"items": int(n.value), "grid": int(g.value), "sweep": int(sw.value)}
+
+
+def ising_batch_destroy(b: int) -> None:
+    _check(lib().ising_batch_destroy(b))
+
+
+class Batch:
+    """Owning wrapper of an ising_batch."""
+
+    def __init__(self, Ls, betas, pt_every: int, stream=None, seed: int | None = None):
+        self.Ls = [int(x) for x in Ls]
+        self.betas = np.asarray(betas, dtype=np.float64)
+        self.n_beta = len(self.betas)
+        self.n_rep = len(self.Ls) * self.n_beta
+        self.h = ising_batch_create(self.Ls, self.betas, pt_every, stream)
+        if seed is not None:
+            ising_batch_seed(self.h, seed)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ising_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, n):
+        ising_batch_run(self.h, n)
+
+    def state(self):
+        p, E, M = ising_batch_state(self.h, self.n_rep)
+        nl = len(self.Ls)
+        return p.reshape(nl, self.n_beta), E.reshape(nl, self.n_beta), M.reshape(nl, self.n_beta)
+
+    def swap_counts(self):
+        a, t = ising_batch_swap_counts(self.h, self.n_rep)
+        nl = len(self.Ls)
+        return a.reshape(nl, self.n_beta), t.reshape(nl, self.n_beta)
+
+    def spins(self, ladder, replica):
+        return ising_batch_get_spins(self.h, ladder, replica, self.Ls[ladder])

@@ -93,9 +93,7 @@ struct ising_ctx {
   int64_t N() const { return (int64_t)L * L; }
   size_t plane_words() const { return (size_t)2 * L * Wc; }
   BitsLattice lat(int which) const { return BitsLattice{bits[which], L, Wc, Wc}; }
-  RngParams rng() const {
-    return RngParams{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), replica, t4, t8};
-  }
+  RngParams rng() const { return make_rng(seed, replica, t4, t8); }
 };
 
 namespace {
@@ -147,7 +145,10 @@ int validate_kernel(const ising_ctx* c, int kernel, int k, int tile_rows, int ti
         return fail(ISING_EINVAL, "tile_words must be a multiple of 4 dividing Wc = %d", c->Wc);
       if (tile_rows < 1 || tile_rows > c->L)
         return fail(ISING_EINVAL, "tile_rows must be in 1..L");
-      const size_t smem = tiled_smem_bytes(c->L, k, tile_rows, tile_words);
+      if (c->L < 4 * k) return fail(ISING_EINVAL, "L must be at least 4 x sweeps_per_launch");
+      const size_t smem = (tile_words == 32 || tile_words == 64)
+                              ? tiled32_smem_bytes(c->L, k, tile_rows, tile_words)
+                              : tiled_smem_bytes(c->L, k, tile_rows, tile_words);
       if (smem > 200 * 1024)
         return fail(ISING_EINVAL, "tile needs %zu bytes of shared memory (> 200 KiB)", smem);
       return ISING_OK;
@@ -167,11 +168,14 @@ void resolve_auto(ising_ctx* c) {
   if (c->layout == ISING_LAYOUT_BITS) {
     if (c->Wc % 4 == 0 && c->L % 64 == 0 && c->L >= 256) {
       c->kernel = ISING_KERNEL_TILED;
-      c->k = 2;
+      c->k = 1;
       int tw = 32;
       while (tw > 4 && c->Wc % tw != 0) tw /= 2;
       c->tile_words = tw;
-      c->tile_rows = c->L / 64 > 0 ? c->L / 64 : 1;
+      // about 108-row strips: for L = 16384 that is 152 strips x 8 tiles,
+      // two tiles per resident CTA at 4 CTAs per SM
+      c->tile_rows = c->L >= 1024 ? (int)((int64_t)c->L * 152 / 16384) : c->L / 64;
+      if (c->tile_rows < 1) c->tile_rows = 1;
     } else {
       c->kernel = ISING_KERNEL_HALF;
     }
@@ -276,9 +280,14 @@ int sweep_chunk(ising_ctx* c, int64_t t0, int n, int m) {
       for (int s = 0; s < kMaxSweepsPerLaunch; ++s)
         slots.slot[s] = s < kk ? (int)slot_of(t + s) : -1;
       Timed tm(c);
-      cudaError_t e = launch_tiled_sweep_bits(c->lat(c->cur), c->bits[1 - c->cur], rng,
-                                              (uint32_t)t, kk, slots, c->rec, c->tile_rows,
-                                              c->tile_words, c->grid, c->block, c->stream);
+      cudaError_t e =
+          (c->tile_words == 32 || c->tile_words == 64)
+              ? launch_tiled32_sweep_bits(c->lat(c->cur), c->bits[1 - c->cur], rng, (uint32_t)t,
+                                          kk, slots, c->rec, c->tile_rows, c->tile_words, c->grid,
+                                          c->stream)
+              : launch_tiled_sweep_bits(c->lat(c->cur), c->bits[1 - c->cur], rng, (uint32_t)t, kk,
+                                        slots, c->rec, c->tile_rows, c->tile_words, c->grid,
+                                        c->block, c->stream);
       if (int st = launch_result(c, e, "tiled sweep")) return st;
       c->cur = 1 - c->cur;
     }

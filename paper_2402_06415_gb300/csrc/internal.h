@@ -26,7 +26,24 @@ struct RngParams {
   uint32_t key0, key1;  // lo32 / hi32 of the seed
   uint32_t replica;
   uint32_t t4, t8;      // thresholds for dE = 4, 8
+  // Philox round keys key0 + r W0, key1 + r W1 (r = 0..9), filled by
+  // make_rng(); passed by value so device code reads them as constants
+  uint32_t rk0[10], rk1[10];
 };
+
+inline RngParams make_rng(uint64_t seed, uint32_t replica, uint32_t t4, uint32_t t8) {
+  RngParams p;
+  p.key0 = (uint32_t)(seed & 0xffffffffu);
+  p.key1 = (uint32_t)(seed >> 32);
+  p.replica = replica;
+  p.t4 = t4;
+  p.t8 = t8;
+  for (int r = 0; r < 10; ++r) {
+    p.rk0[r] = p.key0 + (uint32_t)r * 0x9E3779B9u;
+    p.rk1[r] = p.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return p;
+}
 
 // ---- bit layout (k_bits.cu) ----
 cudaError_t launch_init_bits(const BitsLattice& lat, const RngParams& rng, cudaStream_t s);
@@ -41,6 +58,14 @@ cudaError_t launch_tiled_sweep_bits(const BitsLattice& in, uint32_t* out, const 
                                     unsigned long long* rec_base, int n_tile_rows,
                                     int tile_words, int grid, int block, cudaStream_t s);
 size_t tiled_smem_bytes(int L, int k, int n_tile_rows, int tile_words);
+// Same contract as launch_tiled_sweep_bits for tile_words in {32, 64} (faster
+// variant: one warp per tile row, compaction of undecided words).  grid <= 0:
+// one persistent CTA per resident slot.
+cudaError_t launch_tiled32_sweep_bits(const BitsLattice& in, uint32_t* out, const RngParams& rng,
+                                      uint32_t sweep0, int k, const RecordSlots& slots,
+                                      unsigned long long* rec_base, int n_tile_rows,
+                                      int tile_words, int grid, cudaStream_t s);
+size_t tiled32_smem_bytes(int L, int k, int n_tile_rows, int tile_words);
 cudaError_t launch_measure_bits(const BitsLattice& lat, unsigned long long* out2,
                                 cudaStream_t s);
 cudaError_t launch_unpack_bits(const BitsLattice& lat, int8_t* spins, cudaStream_t s);

@@ -39,6 +39,20 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// Same block function with the ten round keys given (k0 + r W0, k1 + r W1).
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t (&rk0)[10],
+                                             const uint32_t (&rk1)[10]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint32_t ctr_w(uint32_t tag, uint32_t colour, uint32_t block) {
   return (tag << 16) | (colour << 8) | block;
 }

@@ -218,6 +218,217 @@ __global__ void __launch_bounds__(256) k_tiled_bits(const uint32_t* __restrict__
     if (slots.slot[s] >= 0) block_add2(acc_anti[s], acc_ones[s], rec + 2 * (size_t)slots.slot[s]);
 }
 
+// Planes of Philox blocks b = B0 .. B1-1 for the undecided lanes of one word.
+// d1 / d0 = undecided lanes that test against t4 / t8; accepted lanes are added
+// to acc.  Stops early once no lane of the warp is undecided (warp vote), so
+// every lane of the warp must call it.
+template <int B0, int B1>
+__device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep, uint32_t colour,
+                                            const RngParams& rng, uint32_t& d1, uint32_t& d0,
+                                            uint32_t& acc) {
+#pragma unroll
+  for (int b = B0; b < B1; ++b) {
+    if (!__any_sync(0xffffffffu, (d1 | d0) != 0u)) break;
+    const uint4 r = philox10_rk(make_uint4(g, t, rep, ctr_w(kTagMet, colour, b)), rng.rk0, rng.rk1);
+    const uint32_t p[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * b + q;
+      const uint32_t m4 = 0u - ((rng.t4 >> (31 - k)) & 1u);
+      const uint32_t m8 = 0u - ((rng.t8 >> (31 - k)) & 1u);
+      const uint32_t tm = (d1 & m4) | (d0 & m8);  // undecided lanes whose threshold bit is 1
+      acc |= tm & ~p[q];                          // u bit 0 < T bit 1: accept
+      d1 &= ~(p[q] ^ m4);                         // equal bits: still undecided
+      d0 &= ~(p[q] ^ m8);
+    }
+  }
+}
+
+// Tiled sweep with one warp per 32-word tile row segment.  Same tiling, halo
+// and results as k_tiled_bits; differences are for speed only:
+//  * the inner 32*TWW words of a row are updated by TWW warps (lane = word), the
+//    two halo words per row by a separate short pass, so no integer division
+//    or modulo runs per word;
+//  * phase 1 evaluates the first two Philox blocks (8 planes) of every word;
+//    words with lanes still undecided (about 1 in 10) go to a shared-memory
+//    queue, and phase 2 finishes them with all lanes of a warp busy on queued
+//    words, instead of every warp waiting for its slowest word;
+//  * per-sweep observables are summed in shared memory, not registers.
+template <int K, int TWW>
+__global__ void __launch_bounds__(256, 4) k_tiled32_bits(const uint32_t* __restrict__ in,
+                                                         uint32_t* __restrict__ out, int L, int Wc,
+                                                         int n_ty, uint32_t t0, RngParams rng,
+                                                         RecordSlots slots,
+                                                         unsigned long long* __restrict__ rec) {
+  constexpr int H = 2 * K;
+  constexpr int TW = 32 * TWW;
+  constexpr int SP = TW + 8;
+  constexpr int QCAP = 512;
+  extern __shared__ uint4 smem4[];
+  __shared__ uint32_t q_pos[QCAP], q_d1[QCAP], q_d0[QCAP];
+  __shared__ int q_n[2];
+  __shared__ unsigned long long s_anti[K], s_ones[K];
+  uint32_t* S = reinterpret_cast<uint32_t*>(smem4);
+  const int Ty_max = (L + n_ty - 1) / n_ty;
+  const int SR = Ty_max + 2 * H;
+  uint32_t* S0 = S;
+  uint32_t* S1 = S + SR * SP;
+  const int n_tx = Wc / TW;
+  const int n_tiles = n_ty * n_tx;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid < K) {
+    s_anti[tid] = 0ull;
+    s_ones[tid] = 0ull;
+  }
+
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int ty = tile / n_tx, tx = tile - (tile / n_tx) * n_tx;
+    const int y0 = (int)((long long)ty * L / n_ty);
+    const int y1 = (int)((long long)(ty + 1) * L / n_ty);
+    const int Ty = y1 - y0;
+    const int w0 = tx * TW;
+    const int rows = Ty + 2 * H;
+    constexpr int QROW = SP / 4;
+    for (int i = tid; i < 2 * rows * QROW; i += blockDim.x) {
+      const int c = i / (rows * QROW);
+      const int rem = i - c * rows * QROW;
+      const int r = rem / QROW, q = rem - (rem / QROW) * QROW;
+      const int gy = wrap(y0 - H + r, L);
+      const int gw = wrap(w0 - 4 + 4 * q, Wc);
+      const uint4 v =
+          *reinterpret_cast<const uint4*>(in + (size_t)c * L * Wc + (size_t)gy * Wc + gw);
+      reinterpret_cast<uint4*>(S + c * SR * SP + r * SP)[q] = v;
+    }
+    if (tid == 0) q_n[0] = 0;
+    __syncthreads();
+    // global row of tile row r (no modulo: |y0 - H + r| < 2L since H <= 16 <= L)
+    auto grow = [&](int r) {
+      int gy = y0 - H + r;
+      gy += gy < 0 ? L : 0;
+      gy -= gy >= L ? L : 0;
+      return gy;
+    };
+    auto gcol = [&](int col) {
+      int gw = w0 - 4 + col;
+      gw += gw < 0 ? Wc : 0;
+      gw -= gw >= Wc ? Wc : 0;
+      return gw;
+    };
+#pragma unroll
+    for (int h = 0; h < 2 * K; ++h) {
+      const int c = h & 1;
+      const int sw = h >> 1;
+      const uint32_t t = t0 + (uint32_t)sw;
+      const int r_lo = h + 1;
+      const int nrows = rows - 2 * h - 2;
+      uint32_t* So = c ? S1 : S0;
+      const uint32_t* Sn = c ? S0 : S1;
+      int* qn = &q_n[h & 1];
+
+      // ---- phase 1: classes, planes 0..7, write, queue the undecided ----
+      auto phase1 = [&](int r, int col, bool active) {
+        const uint32_t s = So[r * SP + col];
+        const uint32_t up = Sn[(r - 1) * SP + col];
+        const uint32_t dn = Sn[(r + 1) * SP + col];
+        const uint32_t mid = Sn[r * SP + col];
+        const int o = (y0 + r + c) & 1;
+        const uint32_t side = o == 0 ? ((mid << 1) | (Sn[r * SP + col - 1] >> 31))
+                                     : ((mid >> 1) | (Sn[r * SP + col + 1] << 31));
+        const Classes k = classify(s, up, dn, mid, side);
+        const uint32_t valid = active ? 0xffffffffu : 0u;
+        uint32_t d1 = k.one & valid, d0 = k.zero & valid, acc = 0;
+        const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
+        lazy_planes<0, 2>(g, t, rng.replica, c, rng, d1, d0, acc);
+        bool ovf = false;
+        if (active) {
+          So[r * SP + col] = s ^ ((k.ge2 & valid) | acc);
+          if ((d1 | d0) != 0u) {
+            const int slot = atomicAdd(qn, 1);
+            if (slot < QCAP) {
+              q_pos[slot] = ((uint32_t)r << 8) | (uint32_t)col;
+              q_d1[slot] = d1;
+              q_d0[slot] = d0;
+            } else {
+              ovf = true;
+            }
+          }
+        }
+        // queue full (not expected at these tile sizes): finish in place
+        if (__any_sync(0xffffffffu, ovf)) {
+          uint32_t e1 = ovf ? d1 : 0u, e0 = ovf ? d0 : 0u, acc2 = 0;
+          lazy_planes<2, 8>(g, t, rng.replica, c, rng, e1, e0, acc2);
+          if (ovf) So[r * SP + col] ^= acc2;
+        }
+      };
+      for (int item = warp; item < nrows * TWW; item += nwarps) {
+        const int r = r_lo + item / TWW;
+        const int col = 4 + 32 * (item % TWW) + lane;
+        phase1(r, col, true);
+      }
+      for (int base = warp * 32; base < 2 * nrows; base += blockDim.x) {
+        const int idx = base + lane;
+        const bool active = idx < 2 * nrows;
+        const int r = r_lo + (active ? (idx >> 1) : 0);
+        const int col = (idx & 1) ? 4 + TW : 3;
+        phase1(r, col, active);
+      }
+      __syncthreads();
+
+      // ---- phase 2: finish the queued words, all lanes busy ----
+      const int n = min(*qn, QCAP);
+      if (tid == 0) q_n[(h + 1) & 1] = 0;
+      for (int base = warp * 32; base < n; base += blockDim.x) {
+        const int e = base + lane;
+        const bool act = e < n;
+        const uint32_t pos = act ? q_pos[e] : (3u | ((uint32_t)r_lo << 8));
+        uint32_t d1 = act ? q_d1[e] : 0u, d0 = act ? q_d0[e] : 0u, acc = 0;
+        const int r = (int)(pos >> 8), col = (int)(pos & 255u);
+        const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
+        lazy_planes<2, 8>(g, t, rng.replica, c, rng, d1, d0, acc);
+        if (act && acc) So[r * SP + col] ^= acc;
+      }
+      if (c == 1 && slots.slot[sw] >= 0) {
+        __syncthreads();
+        unsigned long long anti = 0, ones = 0;
+        for (int item = warp; item < Ty * TWW; item += nwarps) {
+          const int r = H + item / TWW;
+          const int col = 4 + 32 * (item % TWW) + lane;
+          const uint32_t ns = S1[r * SP + col];
+          const uint32_t up = S0[(r - 1) * SP + col];
+          const uint32_t dn = S0[(r + 1) * SP + col];
+          const uint32_t mid = S0[r * SP + col];
+          const int o = (y0 + r + 1) & 1;
+          const uint32_t side = o == 0 ? ((mid << 1) | (S0[r * SP + col - 1] >> 31))
+                                       : ((mid >> 1) | (S0[r * SP + col + 1] << 31));
+          anti += __popc(ns ^ up) + __popc(ns ^ dn) + __popc(ns ^ mid) + __popc(ns ^ side);
+          ones += __popc(ns) + __popc(mid);
+        }
+        anti = warp_sum_u64(anti);
+        ones = warp_sum_u64(ones);
+        if (lane == 0) {
+          atomicAdd(&s_anti[sw], anti);
+          atomicAdd(&s_ones[sw], ones);
+        }
+      }
+      __syncthreads();
+    }
+    constexpr int QIN = TW / 4;
+    for (int i = tid; i < 2 * Ty * QIN; i += blockDim.x) {
+      const int c = i / (Ty * QIN);
+      const int rem = i - c * Ty * QIN;
+      const int r = rem / QIN, q = rem - (rem / QIN) * QIN;
+      const uint4 v = reinterpret_cast<const uint4*>(S + c * SR * SP + (H + r) * SP + 4)[q];
+      *reinterpret_cast<uint4*>(out + (size_t)c * L * Wc + (size_t)(y0 + r) * Wc + w0 + 4 * q) = v;
+    }
+    __syncthreads();
+  }
+  if (tid < K && slots.slot[tid] >= 0) {
+    unsigned long long* dst = rec + 2 * (size_t)slots.slot[tid];
+    if (s_anti[tid]) atomicAdd(dst, s_anti[tid]);
+    if (s_ones[tid]) atomicAdd(dst + 1, s_ones[tid]);
+  }
+}
+
 // Observables of the current configuration: antiparallel bonds counted from
 // every colour-0 site to its four colour-1 neighbours, and up spins.
 __global__ void __launch_bounds__(256) k_measure_bits(const uint32_t* __restrict__ planes, int L,
@@ -344,6 +555,72 @@ cudaError_t launch_tiled_sweep_bits(const BitsLattice& in, uint32_t* out, const 
     case 8: return launch_tiled_k<8>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+size_t tiled32_smem_bytes(int L, int k, int n_tile_rows, int tile_words) {
+  const int Ty_max = (L + n_tile_rows - 1) / n_tile_rows;
+  return 2ull * (size_t)(Ty_max + 4 * k) * (size_t)(tile_words + 8) * sizeof(uint32_t);
+}
+
+template <int K, int TWW>
+static cudaError_t launch_tiled32_k(const BitsLattice& in, uint32_t* out, const RngParams& rng,
+                                    uint32_t sweep0, const RecordSlots& slots,
+                                    unsigned long long* rec, int n_ty, int grid, cudaStream_t s) {
+  const size_t smem = tiled32_smem_bytes(in.L, K, n_ty, 32 * TWW);
+  static size_t configured = 0;  // per instantiation
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_tiled32_bits<K, TWW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  const int n_tiles = n_ty * (in.Wc / (32 * TWW));
+  if (grid <= 0) {
+    static size_t occ_smem = 0;  // resident CTAs per SM, cached per shared-memory size
+    static int occ_grid = 0;
+    if (occ_smem != smem) {
+      int per_sm = 0, dev = 0, sms = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, k_tiled32_bits<K, TWW>, 256, smem);
+      if (e != cudaSuccess) return e;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      occ_grid = per_sm * sms;
+      occ_smem = smem;
+    }
+    grid = occ_grid;
+  }
+  if (grid > n_tiles) grid = n_tiles;
+  if (grid < 1) grid = 1;
+  k_tiled32_bits<K, TWW><<<grid, 256, smem, s>>>(in.planes, out, in.L, in.Wc, n_ty, sweep0, rng,
+                                                 slots, rec);
+  return cudaGetLastError();
+}
+
+template <int TWW>
+static cudaError_t launch_tiled32_w(const BitsLattice& in, uint32_t* out, const RngParams& rng,
+                                    uint32_t sweep0, int k, const RecordSlots& slots,
+                                    unsigned long long* rec, int n_ty, int grid, cudaStream_t s) {
+  switch (k) {
+    case 1: return launch_tiled32_k<1, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 2: return launch_tiled32_k<2, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 3: return launch_tiled32_k<3, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 4: return launch_tiled32_k<4, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 5: return launch_tiled32_k<5, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 6: return launch_tiled32_k<6, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 7: return launch_tiled32_k<7, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 8: return launch_tiled32_k<8, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_tiled32_sweep_bits(const BitsLattice& in, uint32_t* out, const RngParams& rng,
+                                      uint32_t sweep0, int k, const RecordSlots& slots,
+                                      unsigned long long* rec, int n_ty, int tile_words, int grid,
+                                      cudaStream_t s) {
+  if (tile_words == 32) return launch_tiled32_w<1>(in, out, rng, sweep0, k, slots, rec, n_ty, grid, s);
+  if (tile_words == 64) return launch_tiled32_w<2>(in, out, rng, sweep0, k, slots, rec, n_ty, grid, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_measure_bits(const BitsLattice& lat, unsigned long long* out2,

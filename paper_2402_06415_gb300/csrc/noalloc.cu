@@ -111,8 +111,7 @@ extern "C" int ising_sweep_bits_noalloc(const uint32_t* dev_in, uint32_t* dev_ou
     e = cudaMemsetAsync(rec, 0, (size_t)n_rec * 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return err(ISING_ECUDA, cudaGetErrorString(e));
   }
-  const ising::RngParams rng{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), replica, t4,
-                             t8};
+  const ising::RngParams rng = ising::make_rng(seed, replica, t4, t8);
   // Tile shape: 64-row strips, 32-word (2048-column) tiles where they divide.
   const int tile_rows = L / 64;
   const int tile_words = Wc % 32 == 0 ? 32 : (Wc % 16 == 0 ? 16 : (Wc % 8 == 0 ? 8 : 4));

@@ -74,6 +74,10 @@ CASES = [
     (BITS, TILED, (8, 7, 8), 512),
     (BITS, TILED, (2, 16, 16), 1024),
     (BITS, TILED, (5, 5, 4), 1024),
+    (BITS, TILED, (1, 19, 32), 2048),
+    (BITS, TILED, (2, 7, 32), 2048),
+    (BITS, TILED, (3, 20, 32), 2048),
+    (BITS, TILED, (8, 9, 32), 2048),
     (I8, RES, (), 4),
     (I8, RES, (), 10),
     (I8, RES, (), 64),
@@ -92,6 +96,16 @@ def test_sweeps_bit_exact(layout, kernel, kargs, L, beta):
     seed = 1000 + L
     ref, E_ref, M_ref = _oracle_run(L, beta, seed, n)
     got, E, M = _gpu_run(L, beta, seed, n, layout, kernel, kargs)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
+
+
+@pytest.mark.parametrize("kargs", [(2, 37, 64), (1, 152, 32), (4, 64, 32)])
+def test_tiled32_L4096(kargs):
+    """Warp-per-row tiled kernel with its compaction queue, 64- and 32-word tiles."""
+    L, beta, seed, n = 4096, BETA_C, 31, 7
+    ref, E_ref, M_ref = _oracle_run(L, beta, seed, n)
+    got, E, M = _gpu_run(L, beta, seed, n, BITS, TILED, kargs)
     assert np.array_equal(got, ref)
     assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
 
