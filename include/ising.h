@@ -257,6 +257,53 @@ int ising_batch_info(ising_batch* b, int* n_items, int* grid, int64_t* sweep);
 /* Free everything (NULL-safe; synchronises). */
 int ising_batch_destroy(ising_batch* b);
 
+/* ------------------------------------------------------------------------
+ * Learned block proposal (no counterpart in the paper; an extra exact move of
+ * the same chain).  A block pass draws an offset (ox, oy) in [0, block)^2 from
+ * Philox (tag BLK_OFFSET), tiles the lattice into block x block squares at that
+ * offset, and updates all squares of block-colour 0, then of colour 1 (colour =
+ * (bx + by) % 2; squares of one colour share no bond).  Each square's interior
+ * is resampled from a CNN conditioned on the four edges of the ring around it
+ * and accepted with the exact Metropolis-Hastings probability
+ * min(1, exp(-beta dE) q(old) / q(new)), q the quantised proposal density.
+ * Network: 3 x 3 convolutions 2 -> 32 -> 32 -> 1 channels, ReLU after the first
+ * two, zero padding on the (block+2)^2 frame; channel 0 = ring-edge spins,
+ * channel 1 = ring-edge mask.  BF16 weights, FP32 accumulation (tensor cores).
+ * Weight blob (10145 bf16, this order): W1[32][2][3][3], b1[32],
+ * W2[32][32][3][3], b2[32], W3[1][32][3][3], b3[1].
+ * ------------------------------------------------------------------------ */
+
+/* Load the BF16 weight blob (bytes = 2 * 10145) into the context.  Synchronises. */
+int ising_nn_load(ising_ctx* ctx, const void* bf16_weights, size_t bytes);
+
+/* n_passes block passes with squares of side `block` (2, 4, 8 or 16; L must be
+ * a multiple of 2 * block; packed layout).  Async. */
+int ising_block_pass(ising_ctx* ctx, int n_passes, int block);
+
+/* Squares proposed and accepted by this context's block passes (synchronises). */
+int ising_block_stats(ising_ctx* ctx, int64_t* proposed, int64_t* accepted);
+
+/* Trainer: FP32 master weights, Adam state and BF16 inference copies of the
+ * same network.  Windows are int8 spins of (block+2)^2 sites, row-major: the
+ * ring around a block (corners ignored) and its interior (the training target).
+ * Loss = mean over windows of sum_i BCE(logit_i, (s_i + 1) / 2). */
+typedef struct ising_nn ising_nn;
+int ising_nn_param_count(void);
+int ising_nn_create(ising_nn** out, int block, int channels, void* stream);
+int ising_nn_set_params(ising_nn* nn, const float* host_params, int count);
+int ising_nn_get_params(ising_nn* nn, float* host_params, int count);
+/* BF16 blob of the current weights, for ising_nn_load (bytes = 2 * 10145). */
+int ising_nn_export(ising_nn* nn, void* host_bf16, size_t bytes);
+/* Inference logits (BF16 tensor-core path) of count windows on the device:
+ * dev_windows [count][(block+2)^2] int8 -> dev_logits [count][block^2] float. */
+int ising_nn_logits(ising_nn* nn, const int8_t* dev_windows, int count, float* dev_logits);
+/* FP32 loss and gradients (host arrays; grads may be NULL).  Synchronises. */
+int ising_nn_loss_grad(ising_nn* nn, const int8_t* dev_windows, int count, float* loss,
+                       float* host_grads);
+/* One Adam step (lr, betas 0.9 / 0.999, eps 1e-8) on one minibatch. */
+int ising_nn_train_step(ising_nn* nn, const int8_t* dev_windows, int count, float lr, float* loss);
+int ising_nn_destroy(ising_nn* nn);
+
 /* Free everything the context owns.  NULL-safe.  Synchronises the stream. */
 int ising_destroy(ising_ctx* ctx);
 

@@ -89,6 +89,18 @@ _PROTOS = [
     ("ising_batch_get_spins", _i, [_p, _i, _i, _p]),
     ("ising_batch_info", _i, [_p, _p, _p, _p]),
     ("ising_batch_destroy", _i, [_p]),
+    ("ising_nn_load", _i, [_p, _p, ctypes.c_size_t]),
+    ("ising_block_pass", _i, [_p, _i, _i]),
+    ("ising_block_stats", _i, [_p, _p, _p]),
+    ("ising_nn_param_count", _i, []),
+    ("ising_nn_create", _i, [ctypes.POINTER(_p), _i, _i, _p]),
+    ("ising_nn_set_params", _i, [_p, _p, _i]),
+    ("ising_nn_get_params", _i, [_p, _p, _i]),
+    ("ising_nn_export", _i, [_p, _p, ctypes.c_size_t]),
+    ("ising_nn_logits", _i, [_p, _p, _i, _p]),
+    ("ising_nn_loss_grad", _i, [_p, _p, _i, _p, _p]),
+    ("ising_nn_train_step", _i, [_p, _p, _i, ctypes.c_float, _p]),
+    ("ising_nn_destroy", _i, [_p]),
     ("ising_destroy", _i, [_p]),
     ("ising_last_error", ctypes.c_char_p, []),
 ]
@@ -488,3 +500,91 @@ class Batch:
 
     def spins(self, ladder, replica):
         return ising_batch_get_spins(self.h, ladder, replica, self.Ls[ladder])
+
+
+# ---------------------------------------------------------------------------
+# learned block proposal
+# ---------------------------------------------------------------------------
+NN_CHANNELS = 32
+NN_SHAPES = [("W1", (32, 2, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3)), ("b2", (32,)),
+             ("W3", (1, 32, 3, 3)), ("b3", (1,))]
+
+
+def nn_flatten(params: dict) -> np.ndarray:
+    """Parameter dict (W1, b1, W2, b2, W3, b3) -> flat float32 vector (C-ABI order)."""
+    return np.concatenate([np.asarray(params[k], dtype=np.float32).reshape(-1)
+                           for k, _ in NN_SHAPES]).astype(np.float32)
+
+
+def nn_unflatten(v) -> dict:
+    out, o = {}, 0
+    for k, shp in NN_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(v[o:o + n]).reshape(shp)
+        o += n
+    return out
+
+
+def ising_nn_load(ctx: int, blob: np.ndarray) -> None:
+    b = np.ascontiguousarray(blob)
+    _check(lib().ising_nn_load(ctx, _ptr(b), b.nbytes))
+
+
+def ising_block_pass(ctx: int, n_passes: int, block: int = 16) -> None:
+    _check(lib().ising_block_pass(ctx, int(n_passes), int(block)))
+
+
+def ising_block_stats(ctx: int):
+    p, a = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ising_block_stats(ctx, ctypes.byref(p), ctypes.byref(a)))
+    return int(p.value), int(a.value)
+
+
+def ising_nn_param_count() -> int:
+    return int(lib().ising_nn_param_count())
+
+
+def ising_nn_create(block: int = 16, channels: int = NN_CHANNELS, stream=None) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().ising_nn_create(ctypes.byref(out), int(block), int(channels), _stream_ptr(stream)))
+    return out.value
+
+
+def ising_nn_set_params(nn: int, flat: np.ndarray) -> None:
+    v = np.ascontiguousarray(flat, dtype=np.float32)
+    _check(lib().ising_nn_set_params(nn, _ptr(v), v.size))
+
+
+def ising_nn_get_params(nn: int) -> np.ndarray:
+    v = np.zeros(ising_nn_param_count(), dtype=np.float32)
+    _check(lib().ising_nn_get_params(nn, _ptr(v), v.size))
+    return v
+
+
+def ising_nn_export(nn: int) -> np.ndarray:
+    blob = np.zeros(ising_nn_param_count(), dtype=np.uint16)
+    _check(lib().ising_nn_export(nn, _ptr(blob), blob.nbytes))
+    return blob
+
+
+def ising_nn_logits(nn: int, dev_windows, count: int, dev_logits) -> None:
+    _check(lib().ising_nn_logits(nn, _ptr(dev_windows), int(count), _ptr(dev_logits)))
+
+
+def ising_nn_loss_grad(nn: int, dev_windows, count: int, want_grads: bool = True):
+    loss = ctypes.c_float()
+    g = np.zeros(ising_nn_param_count(), dtype=np.float32) if want_grads else None
+    _check(lib().ising_nn_loss_grad(nn, _ptr(dev_windows), int(count), ctypes.byref(loss),
+                                    _ptr(g) if g is not None else ctypes.c_void_p(0)))
+    return float(loss.value), g
+
+
+def ising_nn_train_step(nn: int, dev_windows, count: int, lr: float) -> float:
+    loss = ctypes.c_float()
+    _check(lib().ising_nn_train_step(nn, _ptr(dev_windows), int(count), float(lr),
+                                     ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def ising_nn_destroy(nn: int) -> None:
+    _check(lib().ising_nn_destroy(nn))

@@ -85,6 +85,10 @@ struct ising_ctx {
   int64_t rec_count = 0;
   unsigned long long* meas = nullptr;  // [2]
   int kernel = ISING_KERNEL_HALF, k = 1, tile_rows = 1, tile_words = 4, grid = 0, block = 0;
+  __nv_bfloat16* nn_w = nullptr;    // BF16 weights of the block proposal
+  __nv_bfloat16* nn_w2t = nullptr;
+  unsigned long long* blk_stats = nullptr;  // [2] proposed, accepted
+  int64_t block_passes = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
@@ -119,6 +123,11 @@ void free_all(ising_ctx* c) {
   cudaFree(c->spins);
   cudaFree(c->rec);
   cudaFree(c->meas);
+  cudaFree(c->nn_w);
+  cudaFree(c->nn_w2t);
+  cudaFree(c->blk_stats);
+  c->nn_w = c->nn_w2t = nullptr;
+  c->blk_stats = nullptr;
   c->bits[0] = c->bits[1] = nullptr;
   c->spins = nullptr;
   c->rec = nullptr;
@@ -733,6 +742,54 @@ int ising_kernel_time(ising_ctx* c, double* ms, int64_t* launches) {
   }
   *ms = total;
   *launches = (int64_t)(c->ev_used / 2);
+  return ok();
+}
+
+int ising_nn_load(ising_ctx* c, const void* bf16_weights, size_t bytes) {
+  if (int st = check_ctx(c)) return st;
+  if (!bf16_weights || bytes != nn_blob_bytes())
+    return fail(ISING_EINVAL, "weights blob must be %zu bytes of bf16", nn_blob_bytes());
+  if (!c->nn_w) {
+    cudaError_t e = nn_alloc_weights(&c->nn_w, &c->nn_w2t);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->blk_stats, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->blk_stats, 0, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ISING_ENOMEM, "block-proposal weights: %s", cudaGetErrorString(e));
+    }
+  }
+  CUDA_TRY(nn_load_blob(c->nn_w, c->nn_w2t, bf16_weights, c->stream));
+  return ok();
+}
+
+int ising_block_pass(ising_ctx* c, int n_passes, int block) {
+  if (int st = check_ctx(c)) return st;
+  if (!c->nn_w) return fail(ISING_EINVAL, "no network loaded (ising_nn_load)");
+  if (c->layout != ISING_LAYOUT_BITS) return fail(ISING_EINVAL, "block passes need the packed layout");
+  if (block != 2 && block != 4 && block != 8 && block != 16)
+    return fail(ISING_EINVAL, "block must be 2, 4, 8 or 16");
+  if (c->L % (2 * block) != 0) return fail(ISING_EINVAL, "L must be a multiple of 2 x block");
+  if (n_passes < 0) return fail(ISING_EINVAL, "n_passes must be >= 0");
+  const RngParams rng = c->rng();
+  for (int k = 0; k < n_passes; ++k) {
+    for (int col = 0; col < 2; ++col) {
+      Timed tm(c);
+      cudaError_t e = nn_block_pass(c->bits[c->cur], c->L, c->Wc, block, (uint32_t)c->block_passes,
+                                    col, rng, c->beta, c->nn_w, c->nn_w2t, c->blk_stats, c->stream);
+      if (int st = launch_result(c, e, "block pass")) return st;
+    }
+    ++c->block_passes;
+  }
+  return ok();
+}
+
+int ising_block_stats(ising_ctx* c, int64_t* proposed, int64_t* accepted) {
+  if (int st = check_ctx(c)) return st;
+  unsigned long long h[2] = {0, 0};
+  if (c->blk_stats)
+    if (int st = to_host_sync(c, h, c->blk_stats, sizeof(h))) return st;
+  if (proposed) *proposed = (int64_t)h[0];
+  if (accepted) *accepted = (int64_t)h[1];
   return ok();
 }
 

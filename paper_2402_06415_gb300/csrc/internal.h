@@ -71,6 +71,20 @@ cudaError_t launch_measure_bits(const BitsLattice& lat, unsigned long long* out2
 cudaError_t launch_unpack_bits(const BitsLattice& lat, int8_t* spins, cudaStream_t s);
 cudaError_t launch_pack_bits(const BitsLattice& lat, const int8_t* spins, cudaStream_t s);
 
+// ---- learned block proposal (nn.cu) ----
+}  // namespace ising
+#include <cuda_bf16.h>
+namespace ising {
+cudaError_t nn_alloc_weights(__nv_bfloat16** wbf, __nv_bfloat16** w2t);
+cudaError_t nn_load_blob(__nv_bfloat16* wbf, __nv_bfloat16* w2t, const void* host_blob,
+                         cudaStream_t s);
+size_t nn_blob_bytes();
+// One colour of one block pass: every block of that colour (at the pass's
+// Philox-drawn offset) gets one exact MH block update, in place.
+cudaError_t nn_block_pass(uint32_t* planes, int L, int Wc, int B, uint32_t pass, int colour,
+                          const RngParams& rng, double beta, const __nv_bfloat16* wbf,
+                          const __nv_bfloat16* w2t, unsigned long long* stats, cudaStream_t s);
+
 // Sets the message returned by ising_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
