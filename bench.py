@@ -179,6 +179,27 @@ def dist_env():
     return ws, rank, local
 
 
+def job_value(local_ms: float, flips_per_rank: float, dist=None, device=None):
+    """Whole-job throughput over ranks that each run their own replica: the
+    slowest rank's time bounds the job; value = all ranks' flips / that time.
+    Returns (value in flips/ns, max time in ms)."""
+    ws = 1
+    t_max = float(local_ms)
+    if dist is not None and dist.is_initialized():
+        import torch
+
+        ws = dist.get_world_size()
+        t = torch.tensor([t_max], dtype=torch.float64, device=device or "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return flips_per_rank * ws / (t_max * 1e6), t_max
+
+
+def replica_of_rank(rank: int) -> int:
+    """Replica id (Philox stream) of the lattice a rank runs."""
+    return rank
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -231,7 +252,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     L = L_BENCH
     lat = ising.Lattice(L, BETAS[0], ising.ISING_LAYOUT_BITS, stream=stream)
-    ising.ising_set_replica(lat.ctx, rank)
+    ising.ising_set_replica(lat.ctx, replica_of_rank(rank))
     cfg = configure_kernel(lat, tune=not args.no_tune)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -267,13 +288,9 @@ def run_ours(args):
     launches = ising.ising_launch_count(lat.ctx) - launches0
     step_ms = [a.elapsed_time(b) for (a, b) in evs]
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    flips = float(L) * L * SWEEPS_PER_STEP * args.steps * ws
-    value = flips / (total_ms * 1e6)
+    flips_rank = float(L) * L * SWEEPS_PER_STEP * args.steps
+    value, total_ms = job_value(sum(step_ms), flips_rank, dist, "cuda")
+    flips = flips_rank * ws
     # sanity: the chain is alive (records present, energies in range)
     E, M = lat.series(SWEEPS_PER_STEP // MEASURE_EVERY)
     assert np.all(np.abs(E) <= 2 * L * L) and len(E) == SWEEPS_PER_STEP // MEASURE_EVERY
@@ -304,12 +321,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_times.append(t1 - t0)
-    e2e_s = sum(e2e_times)
-    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_s = float(t.item())
-    e2e_value = flips / (e2e_s * 1e9)
+    e2e_value, _ = job_value(1e3 * sum(e2e_times), flips_rank, dist, "cuda")
     h2d = 2 * L * Wc * 4
     d2h = 2 * L * Wc * 4 + n_rec * 16
 
@@ -381,7 +393,14 @@ def run_batch(args):
     b = ising.Batch(Ls, betas, pt, stream=stream, seed=SEED)
     if args.batch_kernel:
         wpi, thr = (int(v) for v in args.batch_kernel.split(","))
-        ising.ising_batch_set_kernel(b.h, wpi, thr, 0)
+    elif not args.no_tune:
+        from paper_2402_06415_gb300 import autotune
+
+        best = autotune.tune_batch(Ls, betas, pt)["config"]
+        wpi, thr = best["words_per_item"], best["threads"]
+    else:
+        wpi, thr = 512, 256
+    ising.ising_batch_set_kernel(b.h, wpi, thr, 0)
     ising.ising_batch_capture(b.h, sweeps)
     for _ in range(args.warmup):
         b.run(sweeps)
@@ -413,13 +432,90 @@ def run_batch(args):
                                "L per ladder from {16..128}, PT every 10 sweeps, one persistent "
                                "launch per step replayed from a CUDA graph",
                    "sweeps_per_step": sweeps, "replica_sites": sites, "items": info["items"],
-                   "grid": info["grid"], "status": st, "device_sweeps": sw},
+                   "grid": info["grid"], "status": st, "device_sweeps": sw,
+                   "words_per_item": wpi, "threads": thr},
         "pt_accept_rate_by_pair": [round(x, 4) for x in rate],
         "gpu_launches": args.steps, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
+    return 0
+
+
+def run_learned(args):
+    """Learned 16x16 block proposal at beta_c on L = 256 against the plain sweep:
+    train the CNN on plain-sweep windows (L in {64, 128, 256}), then run chains of
+    (1 sweep + 1 block pass) and of plain sweeps; report acceptance, tau_int of
+    |M| and E, and independent samples per second of each."""
+    import numpy as np
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import learned, stats
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    beta, L, block = 0.4406868, 256, 16
+    t0 = time.perf_counter()
+    wins = learned.generate_windows([64, 128, 256], beta, args.train_windows // 3, block, seed=7,
+                                    thermalise=2000, thin=20, per_config=64)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with learned.Trainer(block, seed=8) as tr:
+        losses = tr.fit(wins, epochs=args.train_epochs, batch=512, lr=2e-3, seed=9)
+        blob = tr.blob()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n = args.chain_sweeps
+    res = {}
+    stream = torch.cuda.current_stream()
+    for mode in ("plain", "learned"):
+        taus_m, taus_e, ms_tot, acc = [], [], 0.0, [0, 0]
+        for c in range(args.chains):
+            with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream,
+                               seed=100 + c) as lat:
+                ising.ising_nn_load(lat.ctx, blob)
+                every = 1 if mode == "learned" else 0
+                ising.ising_sweep_blocks(lat.ctx, args.thermalise, 0, block, every)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ising.ising_sweep_blocks(lat.ctx, n, 1, block, every)
+                e1.record(stream)
+                e1.synchronize()
+                ms_tot += e0.elapsed_time(e1)
+                E, M = lat.series(n)
+                taus_m.append(stats.tau_int(np.abs(M).astype(float)))
+                taus_e.append(stats.tau_int(E.astype(float)))
+                p_, a_ = ising.ising_block_stats(lat.ctx)
+                acc[0] += p_
+                acc[1] += a_
+        sweeps_per_s = args.chains * n / (ms_tot / 1e3)
+        tm, te = float(np.mean(taus_m)), float(np.mean(taus_e))
+        res[mode] = {"sweeps_per_s": sweeps_per_s, "tau_int_absM": tm, "tau_int_E": te,
+                     "indep_samples_per_s_absM": sweeps_per_s / (2 * tm),
+                     "indep_samples_per_s_E": sweeps_per_s / (2 * te),
+                     "block_acceptance": (acc[1] / acc[0]) if acc[0] else None,
+                     "run_over_tau_absM": n / tm}
+    gain_m = res["learned"]["indep_samples_per_s_absM"] / res["plain"]["indep_samples_per_s_absM"]
+    gain_e = res["learned"]["indep_samples_per_s_E"] / res["plain"]["indep_samples_per_s_E"]
+    line = {
+        "metric": METRIC, "value": res["learned"]["indep_samples_per_s_absM"],
+        "unit": "independent |M| samples/s (learned chain, L=256, beta_c)", "n_gpus": 1,
+        "steps": args.chains, "warmup": args.thermalise, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "learned 16x16 block proposal, L=256 at beta_c, 1 block pass per "
+                               "sweep, vs plain sweep on the same GPU",
+                   "train_windows": int(len(wins)), "train_epochs": args.train_epochs,
+                   "chain_sweeps": n, "chains": args.chains},
+        "plain": res["plain"], "learned": res["learned"],
+        "gain_indep_samples_absM": gain_m, "gain_indep_samples_E": gain_e,
+        "train": {"loss_first": float(np.mean(losses[:5])), "loss_last": float(np.mean(losses[-5:])),
+                  "data_s": t_data, "train_s": t_train, "steps": len(losses)},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -433,7 +529,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the fixed kernel shape instead of the autotuner's choice")
-    ap.add_argument("--workload", choices=["plain", "batch"], default="plain",
+    ap.add_argument("--train-windows", type=int, default=100000)
+    ap.add_argument("--train-epochs", type=int, default=4)
+    ap.add_argument("--chain-sweeps", type=int, default=60000)
+    ap.add_argument("--chains", type=int, default=2)
+    ap.add_argument("--thermalise", type=int, default=5000)
+    ap.add_argument("--workload", choices=["plain", "batch", "learned"], default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
     ap.add_argument("--batch-kernel", default="",
@@ -448,6 +549,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -191,7 +191,7 @@ int ising_sweep_bits_noalloc(const uint32_t* dev_in, uint32_t* dev_out, int L, d
  * whose MC runs one chain per lattice; the sweep each replica runs is the
  * paper's checkerboard sweep, Results A / Supplementary MC steps 1-3).
  * n_ladders ladders of n_beta replicas each; ladder l has lattice size L[l]
- * (even, 4..256) and replica i of ladder l uses Philox replica id
+ * (even, 4..1024) and replica i of ladder l uses Philox replica id
  * l * n_beta + i.  betas (ascending, > 0) are the temperature slots shared by
  * all ladders.  Every sweep runs each replica at the beta of its slot; after
  * every sweep t with (t + 1) % pt_every == 0 each ladder performs exchange step
@@ -251,6 +251,14 @@ int ising_batch_series(ising_batch* b, int n_steps, int32_t* E, int32_t* M, int1
 /* int8 spins (L*L, row-major) of replica i of ladder l.  Synchronises. */
 int ising_batch_get_spins(ising_batch* b, int ladder, int replica, int8_t* host_out);
 
+/* Learned block proposal on every replica of the batch (the same move as
+ * ising_block_pass, per replica at the beta of its current slot, Philox replica
+ * id = its batch replica id).  Load the BF16 blob first; then each pass updates
+ * all squares of colour 0, then colour 1, of every replica.  Async. */
+int ising_batch_nn_load(ising_batch* b, const void* bf16_weights, size_t bytes);
+int ising_batch_block_pass(ising_batch* b, int n_passes, int block);
+int ising_batch_block_stats(ising_batch* b, int64_t* proposed, int64_t* accepted);
+
 /* Work items, CTAs used, host-side sweep counter. */
 int ising_batch_info(ising_batch* b, int* n_items, int* grid, int64_t* sweep);
 
@@ -279,6 +287,11 @@ int ising_nn_load(ising_ctx* ctx, const void* bf16_weights, size_t bytes);
 /* n_passes block passes with squares of side `block` (2, 4, 8 or 16; L must be
  * a multiple of 2 * block; packed layout).  Async. */
 int ising_block_pass(ising_ctx* ctx, int n_passes, int block);
+
+/* Interleaved schedule: n_sweeps plain sweeps (records as in ising_sweep); after
+ * every sweep t with (t + 1) % block_every == 0 one block pass with squares of
+ * side `block` (block_every = 0: plain sweeps only).  Async. */
+int ising_sweep_blocks(ising_ctx* ctx, int n_sweeps, int measure_every, int block, int block_every);
 
 /* Squares proposed and accepted by this context's block passes (synchronises). */
 int ising_block_stats(ising_ctx* ctx, int64_t* proposed, int64_t* accepted);

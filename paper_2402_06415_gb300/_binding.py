@@ -88,10 +88,14 @@ _PROTOS = [
     ("ising_batch_series", _i, [_p, _i, _p, _p, _p]),
     ("ising_batch_get_spins", _i, [_p, _i, _i, _p]),
     ("ising_batch_info", _i, [_p, _p, _p, _p]),
+    ("ising_batch_nn_load", _i, [_p, _p, ctypes.c_size_t]),
+    ("ising_batch_block_pass", _i, [_p, _i, _i]),
+    ("ising_batch_block_stats", _i, [_p, _p, _p]),
     ("ising_batch_destroy", _i, [_p]),
     ("ising_nn_load", _i, [_p, _p, ctypes.c_size_t]),
     ("ising_block_pass", _i, [_p, _i, _i]),
     ("ising_block_stats", _i, [_p, _p, _p]),
+    ("ising_sweep_blocks", _i, [_p, _i, _i, _i, _i]),
     ("ising_nn_param_count", _i, []),
     ("ising_nn_create", _i, [ctypes.POINTER(_p), _i, _i, _p]),
     ("ising_nn_set_params", _i, [_p, _p, _i]),
@@ -452,6 +456,21 @@ def ising_batch_info(b: int):
     return {"items": int(n.value), "grid": int(g.value), "sweep": int(sw.value)}
 
 
+def ising_batch_nn_load(b: int, blob: np.ndarray) -> None:
+    v = np.ascontiguousarray(blob)
+    _check(lib().ising_batch_nn_load(b, _ptr(v), v.nbytes))
+
+
+def ising_batch_block_pass(b: int, n_passes: int, block: int = 16) -> None:
+    _check(lib().ising_batch_block_pass(b, int(n_passes), int(block)))
+
+
+def ising_batch_block_stats(b: int):
+    p, a = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ising_batch_block_stats(b, ctypes.byref(p), ctypes.byref(a)))
+    return int(p.value), int(a.value)
+
+
 def ising_batch_destroy(b: int) -> None:
     _check(lib().ising_batch_destroy(b))
 
@@ -532,6 +551,12 @@ def ising_nn_load(ctx: int, blob: np.ndarray) -> None:
 
 def ising_block_pass(ctx: int, n_passes: int, block: int = 16) -> None:
     _check(lib().ising_block_pass(ctx, int(n_passes), int(block)))
+
+
+def ising_sweep_blocks(ctx: int, n_sweeps: int, measure_every: int = 0, block: int = 16,
+                       block_every: int = 1) -> None:
+    _check(lib().ising_sweep_blocks(ctx, int(n_sweeps), int(measure_every), int(block),
+                                    int(block_every)))
 
 
 def ising_block_stats(ctx: int):

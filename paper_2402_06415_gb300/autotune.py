@@ -116,3 +116,59 @@ def tune(L: int, beta: float = 0.4406868, sweeps: int = 24, reps: int = 3,
         with open(path, "w") as f:
             json.dump(cache, f, indent=1)
     return res
+
+
+def tune_batch(Ls, betas, pt_every: int, sweeps: int = 100, reps: int = 2,
+               cands: list[tuple[int, int]] | None = None, use_cache: bool = True,
+               verbose: bool = False) -> dict:
+    """Work decomposition (words per item, threads per CTA) of the batched
+    persistent kernel; cached like tune()."""
+    import numpy as np
+    import torch
+
+    key = "batch|%s|%d|nL=%d|Lsum=%d|nb=%d|pt=%d" % (
+        torch.cuda.get_device_properties(torch.cuda.current_device()).name,
+        torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count,
+        len(Ls), int(np.sum(np.asarray(Ls) ** 2)), len(betas), pt_every)
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            return cache[key]
+    cands = cands or [(w, t) for w in (128, 256, 512, 1024, 2048) for t in (128, 256)]
+    table = []
+    st = torch.cuda.current_stream()
+    with B.Batch(Ls, betas, pt_every, stream=st, seed=1) as b:
+        for (w, t) in cands:
+            try:
+                B.ising_batch_set_kernel(b.h, w, t, 0)
+            except B.IsingError:
+                continue
+            b.run(pt_every)  # warm-up
+            best = 0.0
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                b.run(sweeps)
+                e1.record(st)
+                e1.synchronize()
+                sites = sum(L * L for L in Ls) * len(betas)
+                best = max(best, sites * sweeps / (e0.elapsed_time(e1) * 1e6))
+            table.append({"words_per_item": w, "threads": t, "flips_per_ns": best})
+            if verbose:
+                print(table[-1], flush=True)
+    table.sort(key=lambda r: -r["flips_per_ns"])
+    res = {"config": {"words_per_item": table[0]["words_per_item"], "threads": table[0]["threads"]},
+           "flips_per_ns": table[0]["flips_per_ns"], "table": table}
+    if use_cache:
+        cache[key] = res
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    return res

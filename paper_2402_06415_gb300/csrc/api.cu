@@ -783,6 +783,18 @@ int ising_block_pass(ising_ctx* c, int n_passes, int block) {
   return ok();
 }
 
+int ising_sweep_blocks(ising_ctx* c, int n_sweeps, int measure_every, int block, int block_every) {
+  if (int st = check_ctx(c)) return st;
+  if (n_sweeps < 0 || block_every < 0) return fail(ISING_EINVAL, "negative count");
+  if (block_every == 0) return ising_sweep(c, n_sweeps, measure_every);
+  for (int k = 0; k < n_sweeps; ++k) {
+    if (int st = ising_sweep(c, 1, measure_every)) return st;
+    if ((c->sweep % block_every) == 0)
+      if (int st = ising_block_pass(c, 1, block)) return st;
+  }
+  return ok();
+}
+
 int ising_block_stats(ising_ctx* c, int64_t* proposed, int64_t* accepted) {
   if (int st = check_ctx(c)) return st;
   unsigned long long h[2] = {0, 0};

@@ -313,6 +313,14 @@ struct ising_batch {
   int *d_cta_first = nullptr, *d_cta_items = nullptr;
   BatchCounters* d_ctr = nullptr;
   int n_items = 0;
+  // learned block proposal on every replica
+  __nv_bfloat16 *nn_w = nullptr, *nn_w2t = nullptr;
+  float* d_beta_slot = nullptr;
+  long long* d_unit0 = nullptr;
+  int unit_B = 0;
+  long long unit_total = 0;
+  unsigned long long* d_blk_stats = nullptr;
+  int64_t block_passes = 0;
   // captured graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -355,7 +363,7 @@ void bfree(ising_batch* b) {
   void* ptrs[] = {b->spins, b->d_off, b->d_L, b->d_t4, b->d_t8, b->d_q, b->d_perm, b->d_slot,
                   b->d_E, b->d_M, b->d_acc, b->d_att, b->d_serE, b->d_serM, b->d_serS,
                   b->d_item_l, b->d_item_i0, b->d_item_nr, b->d_cta_first, b->d_cta_items,
-                  b->d_ctr};
+                  b->d_ctr, b->nn_w, b->nn_w2t, b->d_beta_slot, b->d_unit0, b->d_blk_stats};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -497,8 +505,8 @@ int ising_batch_create(ising_batch** out, int n_ladders, const int* L, int n_bet
   if (n_beta > 4096 || n_ladders > (1 << 20)) return bfail(ISING_EINVAL, "too many replicas");
   if (pt_every < 1) return bfail(ISING_EINVAL, "pt_every must be >= 1");
   for (int l = 0; l < n_ladders; ++l)
-    if (L[l] < 4 || L[l] > 256 || (L[l] & 1))
-      return bfail(ISING_EINVAL, "ladder %d: L must be even and in [4, 256] (got %d)", l, L[l]);
+    if (L[l] < 4 || L[l] > 1024 || (L[l] & 1))
+      return bfail(ISING_EINVAL, "ladder %d: L must be even and in [4, 1024] (got %d)", l, L[l]);
   for (int a = 0; a < n_beta; ++a) {
     if (!std::isfinite(betas[a]) || betas[a] <= 0)
       return bfail(ISING_EINVAL, "betas must be finite and > 0");
@@ -761,6 +769,77 @@ int ising_batch_info(ising_batch* b, int* n_items, int* grid, int64_t* sweep) {
   if (n_items) *n_items = b->n_items;
   if (grid) *grid = b->grid_used;
   if (sweep) *sweep = b->sweep;
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_batch_nn_load(ising_batch* b, const void* bf16_weights, size_t bytes) {
+  if (int st = check_b(b)) return st;
+  if (!bf16_weights || bytes != nn_blob_bytes())
+    return bfail(ISING_EINVAL, "weights blob must be %zu bytes of bf16", nn_blob_bytes());
+  if (!b->nn_w) {
+    cudaError_t e = nn_alloc_weights(&b->nn_w, &b->nn_w2t);
+    if (!e) e = cudaMalloc((void**)&b->d_beta_slot, (size_t)b->n_beta * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&b->d_blk_stats, 2 * sizeof(unsigned long long));
+    if (!e) e = cudaMemset(b->d_blk_stats, 0, 2 * sizeof(unsigned long long));
+    if (!e) {
+      std::vector<float> bf(b->betas.begin(), b->betas.end());
+      e = cudaMemcpy(b->d_beta_slot, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (e) {
+      cudaGetLastError();
+      return bfail(ISING_ENOMEM, "batch block-proposal buffers: %s", cudaGetErrorString(e));
+    }
+  }
+  BTRY(nn_load_blob(b->nn_w, b->nn_w2t, bf16_weights, b->stream));
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_batch_block_pass(ising_batch* b, int n_passes, int block) {
+  if (int st = check_b(b)) return st;
+  if (!b->nn_w) return bfail(ISING_EINVAL, "no network loaded (ising_batch_nn_load)");
+  if (block != 2 && block != 4 && block != 8 && block != 16)
+    return bfail(ISING_EINVAL, "block must be 2, 4, 8 or 16");
+  for (int l = 0; l < b->n_ladders; ++l)
+    if (b->L[l] % (2 * block) != 0)
+      return bfail(ISING_EINVAL, "ladder %d: L = %d is not a multiple of 2 x block", l, b->L[l]);
+  if (n_passes < 0) return bfail(ISING_EINVAL, "n_passes must be >= 0");
+  if (b->unit_B != block) {
+    std::vector<long long> u0(b->n_rep + 1, 0);
+    for (int r = 0; r < b->n_rep; ++r) {
+      const long long nbx = b->L[r / b->n_beta] / block;
+      u0[r + 1] = u0[r] + nbx * nbx / 2;
+    }
+    cudaFree(b->d_unit0);
+    b->d_unit0 = nullptr;
+    if (int st = balloc(&b->d_unit0, u0.size())) return st;
+    BTRY(cudaMemcpy(b->d_unit0, u0.data(), u0.size() * 8, cudaMemcpyHostToDevice));
+    b->unit_B = block;
+    b->unit_total = u0[b->n_rep];
+  }
+  const RngParams rng = make_rng(b->seed, 0, 0, 0);
+  for (int k = 0; k < n_passes; ++k) {
+    for (int col = 0; col < 2; ++col)
+      BTRY(nn_batch_block_pass(b->spins, b->d_off, b->d_L, b->d_slot, b->d_beta_slot, b->d_unit0,
+                               b->unit_total, b->n_rep, b->n_beta, block, col,
+                               (uint32_t)b->block_passes, rng, b->nn_w, b->nn_w2t,
+                               b->d_blk_stats, b->stream));
+    ++b->block_passes;
+  }
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_batch_block_stats(ising_batch* b, int64_t* proposed, int64_t* accepted) {
+  if (int st = check_b(b)) return st;
+  unsigned long long h[2] = {0, 0};
+  if (b->d_blk_stats) {
+    BTRY(cudaMemcpyAsync(h, b->d_blk_stats, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    BTRY(cudaStreamSynchronize(b->stream));
+  }
+  if (proposed) *proposed = (int64_t)h[0];
+  if (accepted) *accepted = (int64_t)h[1];
   set_last_error("");
   return ISING_OK;
 }

@@ -85,6 +85,14 @@ cudaError_t nn_block_pass(uint32_t* planes, int L, int Wc, int B, uint32_t pass,
                           const RngParams& rng, double beta, const __nv_bfloat16* wbf,
                           const __nv_bfloat16* w2t, unsigned long long* stats, cudaStream_t s);
 
+// One colour of one block pass over every replica of a batch (see nn.cu).
+cudaError_t nn_batch_block_pass(uint32_t* spins, const long long* off, const int* lad_L,
+                                const int* slot_of, const float* beta_of_slot,
+                                const long long* unit0, long long total_units, int n_rep,
+                                int n_beta, int B, int colour, uint32_t pass, const RngParams& rng,
+                                const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
+                                unsigned long long* stats, cudaStream_t s);
+
 // Sets the message returned by ising_last_error() on the calling thread.
 void set_last_error(const char* msg);
 

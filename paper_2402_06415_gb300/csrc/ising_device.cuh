@@ -88,7 +88,9 @@ __device__ __forceinline__ void compare_block(uint4 r, int b, uint32_t t4, uint3
     const int k = 4 * b + q;                       // plane index
     const uint32_t m4 = 0u - ((t4 >> (31 - k)) & 1u);  // all-ones iff T4 bit set
     const uint32_t m8 = 0u - ((t8 >> (31 - k)) & 1u);
-    const uint32_t tm = (one & m4) | (zero & m8);  // per-lane threshold bit
+    // per-lane threshold bit: T4's for class `one`, T8's otherwise (lanes of
+    // neither class are never in D); one three-input logic op
+    const uint32_t tm = (one & m4) | (~one & m8);
     acc |= D & tm & ~p[q];
     D &= ~(tm ^ p[q]);
   }

@@ -218,17 +218,17 @@ __global__ void __launch_bounds__(256) k_tiled_bits(const uint32_t* __restrict__
     if (slots.slot[s] >= 0) block_add2(acc_anti[s], acc_ones[s], rec + 2 * (size_t)slots.slot[s]);
 }
 
-// Planes of Philox blocks b = B0 .. B1-1 for the undecided lanes of one word.
-// d1 / d0 = undecided lanes that test against t4 / t8; accepted lanes are added
-// to acc.  Stops early once no lane of the warp is undecided (warp vote), so
-// every lane of the warp must call it.
+// Planes of Philox blocks b = B0 .. B1-1 for the undecided lanes D of one
+// word; cls marks the lanes that test against t4 (the others test against t8).
+// Accepted lanes are added to acc.  Stops early once no lane of the warp is
+// undecided (warp vote), so every lane of the warp must call it.
 template <int B0, int B1>
 __device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep, uint32_t colour,
-                                            const RngParams& rng, uint32_t& d1, uint32_t& d0,
+                                            const RngParams& rng, uint32_t& D, uint32_t cls,
                                             uint32_t& acc) {
 #pragma unroll
   for (int b = B0; b < B1; ++b) {
-    if (!__any_sync(0xffffffffu, (d1 | d0) != 0u)) break;
+    if (!__any_sync(0xffffffffu, D != 0u)) break;
     const uint4 r = philox10_rk(make_uint4(g, t, rep, ctr_w(kTagMet, colour, b)), rng.rk0, rng.rk1);
     const uint32_t p[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -236,10 +236,9 @@ __device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep
       const int k = 4 * b + q;
       const uint32_t m4 = 0u - ((rng.t4 >> (31 - k)) & 1u);
       const uint32_t m8 = 0u - ((rng.t8 >> (31 - k)) & 1u);
-      const uint32_t tm = (d1 & m4) | (d0 & m8);  // undecided lanes whose threshold bit is 1
-      acc |= tm & ~p[q];                          // u bit 0 < T bit 1: accept
-      d1 &= ~(p[q] ^ m4);                         // equal bits: still undecided
-      d0 &= ~(p[q] ^ m8);
+      const uint32_t tm = (cls & m4) | (~cls & m8);  // lane's threshold bit
+      acc |= D & tm & ~p[q];                          // u bit 0 < T bit 1: accept
+      D &= ~(tm ^ p[q]);                              // equal bits: still undecided
     }
   }
 }
@@ -265,7 +264,7 @@ __global__ void __launch_bounds__(256, 4) k_tiled32_bits(const uint32_t* __restr
   constexpr int SP = TW + 8;
   constexpr int QCAP = 512;
   extern __shared__ uint4 smem4[];
-  __shared__ uint32_t q_pos[QCAP], q_d1[QCAP], q_d0[QCAP];
+  __shared__ uint32_t q_pos[QCAP], q_d[QCAP], q_cls[QCAP];
   __shared__ int q_n[2];
   __shared__ unsigned long long s_anti[K], s_ones[K];
   uint32_t* S = reinterpret_cast<uint32_t*>(smem4);
@@ -336,18 +335,19 @@ __global__ void __launch_bounds__(256, 4) k_tiled32_bits(const uint32_t* __restr
                                      : ((mid >> 1) | (Sn[r * SP + col + 1] << 31));
         const Classes k = classify(s, up, dn, mid, side);
         const uint32_t valid = active ? 0xffffffffu : 0u;
-        uint32_t d1 = k.one & valid, d0 = k.zero & valid, acc = 0;
+        uint32_t D = (k.one | k.zero) & valid, acc = 0;
+        const uint32_t cls = k.one;
         const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
-        lazy_planes<0, 2>(g, t, rng.replica, c, rng, d1, d0, acc);
+        lazy_planes<0, 2>(g, t, rng.replica, c, rng, D, cls, acc);
         bool ovf = false;
         if (active) {
           So[r * SP + col] = s ^ ((k.ge2 & valid) | acc);
-          if ((d1 | d0) != 0u) {
+          if (D != 0u) {
             const int slot = atomicAdd(qn, 1);
             if (slot < QCAP) {
               q_pos[slot] = ((uint32_t)r << 8) | (uint32_t)col;
-              q_d1[slot] = d1;
-              q_d0[slot] = d0;
+              q_d[slot] = D;
+              q_cls[slot] = cls;
             } else {
               ovf = true;
             }
@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(256, 4) k_tiled32_bits(const uint32_t* __restr
         }
         // queue full (not expected at these tile sizes): finish in place
         if (__any_sync(0xffffffffu, ovf)) {
-          uint32_t e1 = ovf ? d1 : 0u, e0 = ovf ? d0 : 0u, acc2 = 0;
-          lazy_planes<2, 8>(g, t, rng.replica, c, rng, e1, e0, acc2);
+          uint32_t e = ovf ? D : 0u, acc2 = 0;
+          lazy_planes<2, 8>(g, t, rng.replica, c, rng, e, cls, acc2);
           if (ovf) So[r * SP + col] ^= acc2;
         }
       };
@@ -381,10 +381,11 @@ __global__ void __launch_bounds__(256, 4) k_tiled32_bits(const uint32_t* __restr
         const int e = base + lane;
         const bool act = e < n;
         const uint32_t pos = act ? q_pos[e] : (3u | ((uint32_t)r_lo << 8));
-        uint32_t d1 = act ? q_d1[e] : 0u, d0 = act ? q_d0[e] : 0u, acc = 0;
+        uint32_t D = act ? q_d[e] : 0u, acc = 0;
+        const uint32_t cls = act ? q_cls[e] : 0u;
         const int r = (int)(pos >> 8), col = (int)(pos & 255u);
         const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
-        lazy_planes<2, 8>(g, t, rng.replica, c, rng, d1, d0, acc);
+        lazy_planes<2, 8>(g, t, rng.replica, c, rng, D, cls, acc);
         if (act && acc) So[r * SP + col] ^= acc;
       }
       if (c == 1 && slots.slot[sw] >= 0) {

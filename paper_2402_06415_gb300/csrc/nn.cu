@@ -15,7 +15,9 @@
 // the same integers P_i, so the chain is exact up to FP32 rounding of the
 // acceptance probability.
 //
-// Inference keeps BF16 weights and BF16 activations with FP32 accumulation:
+// Inference keeps BF16 weights and FP32 accumulation; the first-layer
+// activations (the tensor-core A operand) are a BF16 hi + lo pair (two MMAs per
+// step into the same accumulator), the second-layer ones FP32:
 // layer 2 (K = 9 C = 288) runs on the tensor cores as an implicit GEMM over
 // frame positions (mma.sync m16n8k16, A gathered by ldmatrix straight from the
 // zero-padded activation grid); layers 1 and 3 (K = 18 and 288 with one
@@ -51,8 +53,11 @@ constexpr int kThreads = 256;
 __host__ __device__ constexpr int frame_of(int B) { return B + 2; }
 
 struct InferSmem {
+  // layer-1 activations as a BF16 pair hi + lo (hi = bf16(h), lo = bf16(h - hi)):
+  // the tensor-core A operand with ~16 mantissa bits
   __nv_bfloat16 h1[(kMaxB + 4) * (kMaxB + 4) * kCP];
-  __nv_bfloat16 h2[(kMaxB + 4) * (kMaxB + 4) * kCP];
+  __nv_bfloat16 h1lo[(kMaxB + 4) * (kMaxB + 4) * kCP];
+  float h2[(kMaxB + 4) * (kMaxB + 4) * kC];            // FP32: layer-3 input
   __nv_bfloat16 w2t[kC * kK2P];
   float w1[kOffB1 + kC];   // W1 then b1
   float w3[kC * 9 + 1];    // W3 then b3
@@ -85,8 +90,9 @@ __device__ void load_weights(InferSmem& S, const __nv_bfloat16* __restrict__ w,
   const __nv_bfloat16 z = __float2bfloat16(0.f);
   for (int i = threadIdx.x; i < FP * FP * kCP; i += blockDim.x) {
     S.h1[i] = z;
-    S.h2[i] = z;
+    S.h1lo[i] = z;
   }
+  for (int i = threadIdx.x; i < FP * FP * kC; i += blockDim.x) S.h2[i] = 0.f;
 }
 
 // Layer 1 on the CUDA cores: h1 = relu(conv(frame)) on the F x F frame.
@@ -105,7 +111,10 @@ __device__ void layer1(InferSmem& S, int B) {
         const float s = (float)S.win[yy * F + xx];
         z += S.w1[(c * 2 + 0) * 9 + dy * 3 + dx] * s + S.w1[(c * 2 + 1) * 9 + dy * 3 + dx];
       }
-    S.h1[((fy + 1) * FP + fx + 1) * kCP + c] = __float2bfloat16(fmaxf(z, 0.f));
+    const float h = fmaxf(z, 0.f);
+    const __nv_bfloat16 hi = __float2bfloat16(h);
+    S.h1[((fy + 1) * FP + fx + 1) * kCP + c] = hi;
+    S.h1lo[((fy + 1) * FP + fx + 1) * kCP + c] = __float2bfloat16(h - __bfloat162float(hi));
   }
 }
 
@@ -134,11 +143,14 @@ __device__ void layer2(InferSmem& S, int B) {
     for (int kc = 0; kc < 18; ++kc) {
       const int tap = kc >> 1, ci0 = (kc & 1) * 16;
       const int dy = tap / 3, dx = tap - (tap / 3) * 3;
-      const __nv_bfloat16* arow = &S.h1[((py + dy) * FP + px + dx) * kCP + ci0 + acol];
-      uint32_t a0, a1, a2, a3;
+      const int aoff = ((py + dy) * FP + px + dx) * kCP + ci0 + acol;
+      uint32_t a0, a1, a2, a3, l0, l1, l2, l3;
       asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                    : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
-                   : "r"(smem_addr(arow)));
+                   : "r"(smem_addr(&S.h1[aoff])));
+      asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                   : "=r"(l0), "=r"(l1), "=r"(l2), "=r"(l3)
+                   : "r"(smem_addr(&S.h1lo[aoff])));
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         const __nv_bfloat16* brow =
@@ -152,6 +164,11 @@ __device__ void layer2(InferSmem& S, int B) {
             "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
             : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+            "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+            : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+            : "r"(l0), "r"(l1), "r"(l2), "r"(l3), "r"(b0), "r"(b1));
       }
     }
     const int g = lane >> 2, t2 = (lane & 3) * 2;
@@ -160,12 +177,12 @@ __device__ void layer2(InferSmem& S, int B) {
       const int pp = mt * 16 + g + half * 8;
       if (pp >= M) continue;
       const int fy = pp / F, fx = pp - (pp / F) * F;
-      __nv_bfloat16* dst = &S.h2[((fy + 1) * FP + fx + 1) * kCP];
+      float* dst = &S.h2[((fy + 1) * FP + fx + 1) * kC];
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         const int c = nt * 8 + t2;
-        dst[c] = __float2bfloat16(fmaxf(acc[nt][half * 2 + 0] + S.b2[c], 0.f));
-        dst[c + 1] = __float2bfloat16(fmaxf(acc[nt][half * 2 + 1] + S.b2[c + 1], 0.f));
+        dst[c] = fmaxf(acc[nt][half * 2 + 0] + S.b2[c], 0.f);
+        dst[c + 1] = fmaxf(acc[nt][half * 2 + 1] + S.b2[c + 1], 0.f);
       }
     }
   }
@@ -180,9 +197,9 @@ __device__ void layer3(InferSmem& S, int B) {
     float z = S.w3[kC * 9];
     for (int dy = 0; dy < 3; ++dy)
       for (int dx = 0; dx < 3; ++dx) {
-        const __nv_bfloat16* h = &S.h2[((fy + dy) * FP + fx + dx) * kCP];
+        const float* h = &S.h2[((fy + dy) * FP + fx + dx) * kC];
 #pragma unroll 8
-        for (int c = 0; c < kC; ++c) z += S.w3[c * 9 + dy * 3 + dx] * bf(h[c]);
+        for (int c = 0; c < kC; ++c) z += S.w3[c * 9 + dy * 3 + dx] * h[c];
       }
     S.logit[i] = z;
   }
@@ -216,11 +233,109 @@ __device__ __forceinline__ int get_spin(const uint32_t* planes, int L, int Wc, i
   return ((w >> (j & 31)) & 1u) ? 1 : -1;
 }
 
-__device__ void block_offset(const PassParams& P, int& ox, int& oy) {
-  const uint4 r = philox10_rk(make_uint4(0u, P.pass, P.rng.replica, ctr_w(kTagBlkOffset, 0, 0)),
-                              P.rng.rk0, P.rng.rk1);
-  ox = (int)(r.x % (uint32_t)P.B);
-  oy = (int)(r.y % (uint32_t)P.B);
+__device__ void block_offset(uint32_t pass, uint32_t replica, const RngParams& rng, int B, int& ox,
+                             int& oy) {
+  const uint4 r = philox10_rk(make_uint4(0u, pass, replica, ctr_w(kTagBlkOffset, 0, 0)), rng.rk0,
+                              rng.rk1);
+  ox = (int)(r.x % (uint32_t)B);
+  oy = (int)(r.y % (uint32_t)B);
+}
+
+// One exact block MH update of square (bx, by) of a lattice (whole CTA).
+__device__ void process_block(InferSmem& S, uint32_t* planes, int L, int Wc, int B, int colour,
+                              int ox, int oy, int bx, int by, uint32_t pass, uint32_t replica,
+                              const RngParams& rng, float beta, unsigned long long* stats) {
+  const int F = frame_of(B);
+  const int nbx = L / B;
+  const int x0 = ox + bx * B, y0 = oy + by * B;  // interior origin (mod L)
+  const uint32_t gid = (uint32_t)(by * nbx + bx);
+  for (int i = threadIdx.x; i < F * F; i += blockDim.x) {
+    const int fy = i / F, fx = i - (i / F) * F;
+    int y = y0 - 1 + fy, x = x0 - 1 + fx;
+    y = (y % L + L) % L;
+    x = (x % L + L) % L;
+    S.win[i] = (int8_t)get_spin(planes, L, Wc, y, x);
+  }
+  __syncthreads();
+  layer1(S, B);
+  __syncthreads();
+  layer2(S, B);
+  __syncthreads();
+  layer3(S, B);
+  __syncthreads();
+  // proposal draw, log q terms and local energy terms
+  float lq = 0.f;
+  int de = 0;
+  const int i = threadIdx.x;
+  int old_s = 0, new_s = 0;
+  if (i < B * B) {
+    const int iy = i / B, ix = i - (i / B) * B;
+    const uint32_t Pq = quantise_p(S.logit[i]);
+    const uint4 r = philox10_rk(
+        make_uint4(gid, pass, replica, ctr_w(kTagBlkSample, colour, i >> 2)), rng.rk0, rng.rk1);
+    const uint32_t u = (i & 3) == 0 ? r.x : ((i & 3) == 1 ? r.y : ((i & 3) == 2 ? r.z : r.w));
+    new_s = u < Pq ? 1 : -1;
+    old_s = S.win[(iy + 1) * F + ix + 1];
+    S.nw[i] = (int8_t)new_s;
+    lq = log2_q_term(Pq, old_s) - log2_q_term(Pq, new_s);
+  }
+  __syncthreads();
+  if (i < B * B) {
+    const int iy = i / B, ix = i - (i / B) * B;
+    const int fy = iy + 1, fx = ix + 1;
+    // bonds to the right and down (interior or boundary), plus left / up
+    // bonds to the boundary: every bond touching the interior once
+    const int o_r = S.win[fy * F + fx + 1], o_d = S.win[(fy + 1) * F + fx];
+    const int n_r = ix + 1 < B ? S.nw[i + 1] : o_r;
+    const int n_d = iy + 1 < B ? S.nw[i + B] : o_d;
+    int e_old = -old_s * (o_r + o_d), e_new = -new_s * (n_r + n_d);
+    if (ix == 0) {
+      const int l = S.win[fy * F + fx - 1];
+      e_old -= old_s * l;
+      e_new -= new_s * l;
+    }
+    if (iy == 0) {
+      const int u = S.win[(fy - 1) * F + fx];
+      e_old -= old_s * u;
+      e_new -= new_s * u;
+    }
+    de = e_new - e_old;
+  }
+  float lqs = lq;
+  int des = de;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lqs += __shfl_xor_sync(0xffffffffu, lqs, o);
+    des += __shfl_xor_sync(0xffffffffu, des, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    S.red_lq[threadIdx.x >> 5] = lqs;
+    S.red_de[threadIdx.x >> 5] = des;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sl = 0.f;
+    int sd = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      sl += S.red_lq[k];
+      sd += S.red_de[k];
+    }
+    const float log_alpha = -beta * (float)sd + 0.69314718f * sl;
+    const uint4 r = philox10_rk(make_uint4(gid, pass, replica, ctr_w(kTagBlkAccept, colour, 0)),
+                                rng.rk0, rng.rk1);
+    const float ua = (float)(r.x >> 8) * (1.0f / 16777216.0f);
+    S.accept = (log_alpha >= 0.f || ua < expf(log_alpha)) ? 1 : 0;
+    atomicAdd(&stats[0], 1ull);
+    if (S.accept) atomicAdd(&stats[1], 1ull);
+  }
+  __syncthreads();
+  if (S.accept && i < B * B && new_s != old_s) {
+    const int iy = i / B, ix = i - (i / B) * B;
+    const int y = (y0 + iy) % L, x = (x0 + ix) % L;
+    const int c = (x + y) & 1, j = x >> 1;
+    atomicXor(&planes[(size_t)c * L * Wc + (size_t)y * Wc + (j >> 5)], 1u << (j & 31));
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads) k_nn_block_pass(PassParams P,
@@ -228,108 +343,63 @@ __global__ void __launch_bounds__(kThreads) k_nn_block_pass(PassParams P,
                                                            const __nv_bfloat16* __restrict__ w2t) {
   extern __shared__ uint4 smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
-  const int B = P.B, F = frame_of(B), L = P.L;
+  const int B = P.B, L = P.L;
   const int nbx = L / B, half = nbx / 2;
-  const int n_blocks = nbx * half;  // blocks of this colour
+  const int n_blocks = nbx * half;  // squares of this colour
   int ox, oy;
-  block_offset(P, ox, oy);
+  block_offset(P.pass, P.rng.replica, P.rng, B, ox, oy);
   load_weights(S, w, w2t, B);
   __syncthreads();
   for (int blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     const int by = blk / half, bx = 2 * (blk - by * half) + ((by + P.colour) & 1);
-    const int x0 = ox + bx * B, y0 = oy + by * B;  // interior origin (mod L)
-    const uint32_t gid = (uint32_t)(by * nbx + bx);
-    for (int i = threadIdx.x; i < F * F; i += blockDim.x) {
-      const int fy = i / F, fx = i - (i / F) * F;
-      int y = y0 - 1 + fy, x = x0 - 1 + fx;
-      y = (y % L + L) % L;
-      x = (x % L + L) % L;
-      S.win[i] = (int8_t)get_spin(P.planes, L, P.Wc, y, x);
+    process_block(S, P.planes, L, P.Wc, B, P.colour, ox, oy, bx, by, P.pass, P.rng.replica, P.rng,
+                  P.beta, P.stats);
+  }
+}
+
+// The same pass over every replica of a batch: replica r has its packed
+// lattice at spins + off[r], size L of its ladder, the beta of its current
+// temperature slot, Philox replica id r.  Work unit u (squares of this colour,
+// all replicas) maps to (r, square) through the prefix sums unit0[r].
+struct BatchPassParams {
+  uint32_t* spins;
+  const long long* off;
+  const int* lad_L;
+  const int* slot_of;
+  const float* beta_of_slot;
+  const long long* unit0;  // [n_rep + 1]
+  int n_rep, n_beta, B, colour;
+  uint32_t pass;
+  RngParams rng;           // key and round keys; replica set per unit
+  unsigned long long* stats;
+};
+
+__global__ void __launch_bounds__(kThreads) k_nn_batch_block_pass(BatchPassParams P,
+                                                                 const __nv_bfloat16* __restrict__ w,
+                                                                 const __nv_bfloat16* __restrict__ w2t) {
+  extern __shared__ uint4 smem_raw[];
+  InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
+  const int B = P.B;
+  load_weights(S, w, w2t, B);
+  __syncthreads();
+  const long long total = P.unit0[P.n_rep];
+  for (long long u = blockIdx.x; u < total; u += gridDim.x) {
+    int lo = 0, hi = P.n_rep;  // unit0[lo] <= u < unit0[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (P.unit0[mid] <= u) lo = mid; else hi = mid;
     }
-    __syncthreads();
-    layer1(S, B);
-    __syncthreads();
-    layer2(S, B);
-    __syncthreads();
-    layer3(S, B);
-    __syncthreads();
-    // proposal draw, log q terms and local energy terms
-    float lq = 0.f;
-    int de = 0;
-    const int i = threadIdx.x;
-    int old_s = 0, new_s = 0;
-    uint32_t Pq = 0;
-    if (i < B * B) {
-      const int iy = i / B, ix = i - (i / B) * B;
-      Pq = quantise_p(S.logit[i]);
-      const uint4 r = philox10_rk(
-          make_uint4(gid, P.pass, P.rng.replica, ctr_w(kTagBlkSample, P.colour, i >> 2)),
-          P.rng.rk0, P.rng.rk1);
-      const uint32_t u = (i & 3) == 0 ? r.x : ((i & 3) == 1 ? r.y : ((i & 3) == 2 ? r.z : r.w));
-      new_s = u < Pq ? 1 : -1;
-      old_s = S.win[(iy + 1) * F + ix + 1];
-      S.nw[i] = (int8_t)new_s;
-      lq = log2_q_term(Pq, old_s) - log2_q_term(Pq, new_s);
-    }
-    __syncthreads();
-    if (i < B * B) {
-      const int iy = i / B, ix = i - (i / B) * B;
-      const int fy = iy + 1, fx = ix + 1;
-      // bonds to the right and down (interior or boundary), plus left / up
-      // bonds to the boundary: every bond touching the interior once
-      const int o_r = S.win[fy * F + fx + 1], o_d = S.win[(fy + 1) * F + fx];
-      const int n_r = ix + 1 < B ? S.nw[i + 1] : o_r;
-      const int n_d = iy + 1 < B ? S.nw[i + B] : o_d;
-      int e_old = -old_s * (o_r + o_d), e_new = -new_s * (n_r + n_d);
-      if (ix == 0) {
-        const int l = S.win[fy * F + fx - 1];
-        e_old -= old_s * l;
-        e_new -= new_s * l;
-      }
-      if (iy == 0) {
-        const int u = S.win[(fy - 1) * F + fx];
-        e_old -= old_s * u;
-        e_new -= new_s * u;
-      }
-      de = e_new - e_old;
-    }
-    // block reductions
-    float lqs = lq;
-    int des = de;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lqs += __shfl_xor_sync(0xffffffffu, lqs, o);
-      des += __shfl_xor_sync(0xffffffffu, des, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      S.red_lq[threadIdx.x >> 5] = lqs;
-      S.red_de[threadIdx.x >> 5] = des;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float sl = 0.f;
-      int sd = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        sl += S.red_lq[k];
-        sd += S.red_de[k];
-      }
-      const float log_alpha = -P.beta * (float)sd + 0.69314718f * sl;
-      const uint4 r = philox10_rk(
-          make_uint4(gid, P.pass, P.rng.replica, ctr_w(kTagBlkAccept, P.colour, 0)), P.rng.rk0,
-          P.rng.rk1);
-      const float ua = (float)(r.x >> 8) * (1.0f / 16777216.0f);
-      S.accept = (log_alpha >= 0.f || ua < expf(log_alpha)) ? 1 : 0;
-      atomicAdd(&P.stats[0], 1ull);
-      if (S.accept) atomicAdd(&P.stats[1], 1ull);
-    }
-    __syncthreads();
-    if (S.accept && i < B * B && new_s != old_s) {
-      const int iy = i / B, ix = i - (i / B) * B;
-      const int y = (y0 + iy) % L, x = (x0 + ix) % L;
-      const int c = (x + y) & 1, j = x >> 1;
-      atomicXor(&P.planes[(size_t)c * L * P.Wc + (size_t)y * P.Wc + (j >> 5)], 1u << (j & 31));
-    }
-    __syncthreads();
+    const int r = lo;
+    const int L = P.lad_L[r / P.n_beta];
+    const int Wc = (L / 2 + 31) / 32;
+    const int nbx = L / B, half = nbx / 2;
+    const int blk = (int)(u - P.unit0[r]);
+    const int by = blk / half, bx = 2 * (blk - by * half) + ((by + P.colour) & 1);
+    int ox, oy;
+    block_offset(P.pass, (uint32_t)r, P.rng, B, ox, oy);
+    const float beta = P.beta_of_slot[P.slot_of[r]];
+    process_block(S, P.spins + P.off[r], L, Wc, B, P.colour, ox, oy, bx, by, P.pass, (uint32_t)r,
+                  P.rng, beta, P.stats);
   }
 }
 
@@ -638,6 +708,39 @@ cudaError_t nn_block_pass(uint32_t* planes, int L, int Wc, int B, uint32_t pass,
   const int n_blocks = (L / B) * (L / B) / 2;
   const int grid = std::max(1, std::min(n_blocks, 2 * sms_of_current()));
   k_nn_block_pass<<<grid, kThreads, infer_smem(), s>>>(P, wbf, w2t);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_batch_block_pass(uint32_t* spins, const long long* off, const int* lad_L,
+                                const int* slot_of, const float* beta_of_slot,
+                                const long long* unit0, long long total_units, int n_rep,
+                                int n_beta, int B, int colour, uint32_t pass, const RngParams& rng,
+                                const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
+                                unsigned long long* stats, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_nn_batch_block_pass,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)infer_smem());
+    if (e) return e;
+    attr = true;
+  }
+  BatchPassParams P;
+  P.spins = spins;
+  P.off = off;
+  P.lad_L = lad_L;
+  P.slot_of = slot_of;
+  P.beta_of_slot = beta_of_slot;
+  P.unit0 = unit0;
+  P.n_rep = n_rep;
+  P.n_beta = n_beta;
+  P.B = B;
+  P.colour = colour;
+  P.pass = pass;
+  P.rng = rng;
+  P.stats = stats;
+  const long long g = std::min<long long>(total_units, 2LL * sms_of_current());
+  k_nn_batch_block_pass<<<(int)std::max<long long>(g, 1), kThreads, infer_smem(), s>>>(P, wbf, w2t);
   return cudaGetLastError();
 }
 

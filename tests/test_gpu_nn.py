@@ -1,0 +1,174 @@
+"""Learned block proposal on the GPU against the CPU reference.
+
+* Logits of the BF16 tensor-core inference match the float64 reference with
+  the same (bf16-rounded) weights to 1e-2 relative (floor 1 on the scale).
+* FP32 training loss and gradients match the float64 reference.
+* The block MH chain is exact: block passes alone (2 x 2 blocks, random
+  untrained network) on a 4 x 4 lattice reproduce exact <E> and <M^2>
+  within 3 sigma; with 16 x 16 blocks on L = 64 the chain (sweeps + passes)
+  reproduces the plain chain's energy within 3 sigma.
+* Training on plain-sweep configurations lowers the loss and raises the block
+  acceptance over the untrained network.
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn, exact
+import paper_2402_06415_gb300 as ising
+from paper_2402_06415_gb300 import learned, stats
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ising.lib()
+    return t
+
+
+def _windows(L, n, block, seed, beta=0.44):
+    rng = np.random.default_rng(seed)
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, seed=seed) as lat:
+        lat.sweep(50, 0)
+        s = lat.spins()
+    return learned.extract_windows(s, n, block, rng)
+
+
+def _frames(wins, block):
+    F = block + 2
+    mask = np.zeros((F, F))
+    mask[0, 1:-1] = mask[-1, 1:-1] = mask[1:-1, 0] = mask[1:-1, -1] = 1.0
+    return np.stack([np.stack([w * mask, mask]) for w in wins.astype(np.float64)])
+
+
+@pytest.mark.parametrize("block", [16, 4, 2])
+def test_logits_match_fp32_reference(torch, block):
+    p32 = learned.init_params(seed=3, scale=2.0)
+    for k in p32:  # non-zero biases
+        if k.startswith("b"):
+            p32[k] = (0.1 * np.random.default_rng(4).standard_normal(p32[k].shape)).astype(np.float32)
+    wins = _windows(64, 40, block, seed=5)
+    with learned.Trainer(block, params=p32) as tr:
+        d = torch.from_numpy(wins).cuda()
+        out = torch.zeros((len(wins), block, block), dtype=torch.float32, device="cuda")
+        ising.ising_nn_logits(tr.h, d, len(wins), out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+    pref = {k: cnn.bf16_round(v.astype(np.float64)) for k, v in p32.items()}
+    want = cnn.forward(pref, _frames(wins, block))
+    err = np.abs(got - want) / np.maximum(np.abs(want), 1.0)
+    assert err.max() < 1e-2, err.max()
+    assert np.abs(want).max() > 1.0  # the logits are not trivially small
+
+
+def test_loss_and_gradients_match_reference(torch):
+    block = 4
+    p32 = learned.init_params(seed=6)
+    wins = _windows(32, 24, block, seed=7)
+    with learned.Trainer(block, params=p32) as tr:
+        d = torch.from_numpy(wins).cuda()
+        loss, g = ising.ising_nn_loss_grad(tr.h, d, len(wins))
+    p64 = {k: v.astype(np.float64) for k, v in p32.items()}
+    F = block + 2
+    want_loss, want_g = cnn.loss_and_grads(p64, _frames(wins, block),
+                                           wins[:, 1:F - 1, 1:F - 1].astype(np.float64))
+    assert abs(loss - want_loss) < 1e-4 * abs(want_loss)
+    G = ising.nn_unflatten(g)
+    for k in want_g:
+        num = np.linalg.norm(G[k] - want_g[k])
+        den = np.linalg.norm(want_g[k]) + 1e-12
+        assert num / den < 1e-4, (k, num / den)
+
+
+def test_block_mh_exact_on_4x4(torch):
+    """Block passes only (2 x 2 blocks at random offsets) must sample the
+    Boltzmann distribution of the 4 x 4 lattice."""
+    L, block, beta, n = 4, 2, 0.44, 12000
+    ex = exact.averages(L, beta)
+    # moderate random weights: saturated proposal probabilities would make the
+    # (still exact) block-only chain mix too slowly to test in a few seconds
+    with learned.Trainer(block, params=learned.init_params(seed=9, scale=1.0)) as tr:
+        blob = tr.blob()
+    Es, M2 = [], []
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, seed=11) as lat:
+        ising.ising_nn_load(lat.ctx, blob)
+        for _ in range(n):
+            ising.ising_block_pass(lat.ctx, 1, block)
+            E, M = lat.measure()
+            Es.append(E)
+            M2.append(M * M)
+        prop, acc = ising.ising_block_stats(lat.ctx)
+    e, de = stats.mean_and_error(Es[200:])
+    m, dm = stats.mean_and_error(M2[200:])
+    assert abs(e - ex["E"]) < 3 * de, (e, de, ex["E"])
+    assert abs(m - ex["M2"]) < 3 * dm, (m, dm, ex["M2"])
+    assert prop == n * 4 * 2 // 2 and 0 < acc < prop  # 2 colours x 2 blocks each
+
+
+def test_block_chain_keeps_plain_energy_L64(torch):
+    L, block, beta = 64, 16, 0.40
+    with learned.Trainer(block, params=learned.init_params(seed=12)) as tr:
+        blob = tr.blob()
+    res = {}
+    for mode in ("plain", "learned"):
+        Es = []
+        for seed in (21, 22, 23, 24):
+            with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, seed=seed) as lat:
+                if mode == "learned":
+                    ising.ising_nn_load(lat.ctx, blob)
+                every = 1 if mode == "learned" else 0
+                ising.ising_sweep_blocks(lat.ctx, 200, 0, block, every)
+                ising.ising_sweep_blocks(lat.ctx, 1500, 1, block, every)
+                E, _ = lat.series(1500)
+                Es.append(stats.mean_and_error(E / (L * L)))
+        res[mode] = stats.combine_runs([a for a, _ in Es], [b for _, b in Es])
+    (a, da), (b, db) = res["plain"], res["learned"]
+    assert abs(a - b) < 3 * np.hypot(da, db), res
+
+
+def test_training_lowers_loss_and_raises_acceptance(torch):
+    block, beta = 4, 0.3
+    wins = learned.generate_windows([64], beta, 8192, block, seed=31, thermalise=300, thin=5)
+    with learned.Trainer(block, seed=32) as tr:
+        blob0 = tr.blob()
+        losses = tr.fit(wins, epochs=3, batch=256, lr=3e-3, seed=33)
+        blob1 = tr.blob()
+    assert np.mean(losses[-5:]) < 0.9 * np.mean(losses[:5])
+    rates = []
+    for blob in (blob0, blob1):
+        with ising.Lattice(64, beta, ising.ISING_LAYOUT_BITS, seed=34) as lat:
+            ising.ising_nn_load(lat.ctx, blob)
+            lat.sweep(300, 0)
+            ising.ising_block_pass(lat.ctx, 200, block)
+            p, a = ising.ising_block_stats(lat.ctx)
+            rates.append(a / p)
+    assert rates[1] > rates[0], rates
+
+
+def test_batch_block_pass_equals_single_lattice_pass(torch):
+    """The batched block pass on replica r equals the single-lattice pass with
+    replica id r at that replica's beta, bit for bit."""
+    Ls, betas, block, seed = [32, 64], np.array([0.38, 0.42, 0.46]), 4, 5
+    with learned.Trainer(block, params=learned.init_params(seed=13)) as tr:
+        blob = tr.blob()
+    with ising.Batch(Ls, betas, 1000, seed=seed) as b:
+        ising.ising_batch_nn_load(b.h, blob)
+        ising.ising_batch_block_pass(b.h, 3, block)
+        got = {(l, i): b.spins(l, i) for l in range(2) for i in range(3)}
+        pb, ab = ising.ising_batch_block_stats(b.h)
+    tot_p = tot_a = 0
+    for l, L in enumerate(Ls):
+        for i in range(3):
+            with ising.Lattice(L, betas[i], ising.ISING_LAYOUT_BITS) as lat:
+                ising.ising_set_replica(lat.ctx, l * 3 + i)
+                lat.seed(seed)
+                ising.ising_nn_load(lat.ctx, blob)
+                ising.ising_block_pass(lat.ctx, 3, block)
+                assert np.array_equal(lat.spins(), got[(l, i)]), (l, i)
+                p_, a_ = ising.ising_block_stats(lat.ctx)
+                tot_p += p_
+                tot_a += a_
+    assert (pb, ab) == (tot_p, tot_a) and ab > 0

@@ -6,7 +6,9 @@
 * The quantised proposal density sums to one over all interior configurations.
 * The block energy change equals the difference of full-lattice energies.
 * The block Metropolis-Hastings kernel satisfies detailed balance exactly on a
-  4 x 4 lattice with a 2 x 2 block (enumeration), for a random network.
+  4 x 4 lattice with a 2 x 2 block (enumeration), for a random network, and a
+  chain of block moves alone (random offsets, two square colours) reproduces
+  the exact <E> within 3 sigma.
 """
 import itertools
 
@@ -126,3 +128,27 @@ def test_block_mh_detailed_balance_4x4():
             assert abs(lhs - rhs) <= 1e-12 * max(lhs, rhs, 1e-300)
             checked += 1
     assert checked > 500
+
+
+def test_block_chain_matches_enumeration_4x4():
+    from oracle import init as orc_init
+    from paper_2402_06415_gb300 import stats
+
+    L, B, beta = 4, 2, 0.44
+    p = {k: cnn.bf16_round(v) for k, v in cnn.init_params(C=32, seed=9).items()}
+    rng = np.random.default_rng(0)
+    s = orc_init(L, 11)
+    Es = []
+    for _ in range(5000):
+        ox, oy = rng.integers(0, B, 2)
+        for col in (0, 1):
+            for by in range(L // B):
+                for bx in range(L // B):
+                    if (bx + by) % 2 == col:
+                        u = rng.integers(0, 2 ** 32, (B, B), dtype=np.uint64)
+                        cnn.block_mh(s, (ox + bx * B) % L, (oy + by * B) % L, B, p, beta, u,
+                                     rng.random())
+        Es.append(exact.energy(s))
+    e, de = stats.mean_and_error(Es[200:])
+    want = exact.averages(L, beta)["E"]
+    assert abs(e - want) < 3 * de, (e, de, want)
