@@ -498,6 +498,30 @@ def run_learned(args):
                      "indep_samples_per_s_E": sweeps_per_s / (2 * te),
                      "block_acceptance": (acc[1] / acc[0]) if acc[0] else None,
                      "run_over_tau_absM": n / tm}
+    # acceptance of networks trained per block size (same data recipe, smaller set)
+    scan = []
+    for Bs in args.scan_blocks:
+        if Bs == block:
+            bl, tr_loss = blob, float(np.mean(losses[-5:]))
+        else:
+            w_s = learned.generate_windows([64, 128, 256], beta, 10000, Bs, seed=11, thermalise=2000,
+                                           thin=20, per_config=64)
+            with learned.Trainer(Bs, seed=12) as tr2:
+                ls = tr2.fit(w_s, epochs=3, batch=512, lr=2e-3, seed=13)
+                bl, tr_loss = tr2.blob(), float(np.mean(ls[-5:]))
+        with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=300) as lat:
+            ising.ising_nn_load(lat.ctx, bl)
+            ising.ising_sweep(lat.ctx, args.thermalise, 0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ising.ising_sweep_blocks(lat.ctx, args.scan_sweeps, 0, Bs, 1)
+            e1.record(stream)
+            e1.synchronize()
+            p_, a_ = ising.ising_block_stats(lat.ctx)
+        scan.append({"block": Bs, "train_loss_per_site": tr_loss / (Bs * Bs),
+                     "acceptance": a_ / max(p_, 1), "proposed": p_,
+                     "sweeps_per_s": args.scan_sweeps / (e0.elapsed_time(e1) / 1e3)})
     gain_m = res["learned"]["indep_samples_per_s_absM"] / res["plain"]["indep_samples_per_s_absM"]
     gain_e = res["learned"]["indep_samples_per_s_E"] / res["plain"]["indep_samples_per_s_E"]
     line = {
@@ -509,11 +533,70 @@ def run_learned(args):
                                "sweep, vs plain sweep on the same GPU",
                    "train_windows": int(len(wins)), "train_epochs": args.train_epochs,
                    "chain_sweeps": n, "chains": args.chains},
-        "plain": res["plain"], "learned": res["learned"],
+        "plain": res["plain"], "learned": res["learned"], "acceptance_by_block": scan,
         "gain_indep_samples_absM": gain_m, "gain_indep_samples_E": gain_e,
         "train": {"loss_first": float(np.mean(losses[:5])), "loss_last": float(np.mean(losses[-5:])),
                   "data_s": t_data, "train_s": t_train, "steps": len(losses)},
     }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch_learned(args):
+    """1024 replicas at L = 512 (32 ladders x 32 betas in [0.42, 0.46]): block
+    passes (16 x 16) every 5 sweeps on every replica plus exchanges every 10,
+    against the same batch without block passes; a bounded number of sweeps."""
+    import numpy as np
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import learned, workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    Ls = [512] * 32
+    betas = workloads.batch_betas(32, 0.42, 0.46)
+    block, every, pt = 16, 5, 10
+    wins = learned.generate_windows([64, 128, 256], 0.4406868, 30000, block, seed=7,
+                                    thermalise=2000, thin=20, per_config=64)
+    with learned.Trainer(block, seed=8) as tr:
+        tr.fit(wins, epochs=3, batch=512, lr=2e-3, seed=9)
+        blob = tr.blob()
+    stream = torch.cuda.current_stream()
+    out = {}
+    n = args.sweeps
+    for mode in ("plain", "learned"):
+        with ising.Batch(Ls, betas, pt, stream=stream, seed=SEED) as b:
+            ising.ising_batch_nn_load(b.h, blob)
+            b.run(20)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n // every):
+                b.run(every)
+                if mode == "learned":
+                    ising.ising_batch_block_pass(b.h, 1, block)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            st, sw = ising.ising_batch_status(b.h)
+            p_, a_ = ising.ising_batch_block_stats(b.h)
+            acc, att = b.swap_counts()
+        sites = 512 * 512 * 1024
+        out[mode] = {"ms": ms, "sweeps": (n // every) * every,
+                     "flips_per_ns": sites * (n // every) * every / (ms * 1e6),
+                     "block_acceptance": (a_ / p_) if p_ else None, "squares_proposed": p_,
+                     "pt_accept": float(acc[:, :-1].sum() / max(att[:, :-1].sum(), 1)),
+                     "status": st}
+    line = {"metric": METRIC, "value": out["learned"]["flips_per_ns"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16",
+            "config": {"workload": "batched + learned: 1024 replicas L=512, 32 betas in "
+                                   "[0.42,0.46], 16x16 block pass every 5 sweeps, PT every 10",
+                       "sweeps": n},
+            "plain": out["plain"], "learned": out["learned"],
+            "cost_ratio_per_sweep": out["learned"]["ms"] / out["plain"]["ms"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -534,7 +617,10 @@ def main(argv=None):
     ap.add_argument("--chain-sweeps", type=int, default=60000)
     ap.add_argument("--chains", type=int, default=2)
     ap.add_argument("--thermalise", type=int, default=5000)
-    ap.add_argument("--workload", choices=["plain", "batch", "learned"], default="plain",
+    ap.add_argument("--scan-blocks", type=int, nargs="*", default=[2, 4, 8, 16])
+    ap.add_argument("--scan-sweeps", type=int, default=3000)
+    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned"],
+                    default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
     ap.add_argument("--batch-kernel", default="",
@@ -551,6 +637,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "batch_learned":
+        return run_batch_learned(args)
     return run_ours(args)
 
 

@@ -259,6 +259,13 @@ int ising_batch_nn_load(ising_batch* b, const void* bf16_weights, size_t bytes);
 int ising_batch_block_pass(ising_batch* b, int n_passes, int block);
 int ising_batch_block_stats(ising_batch* b, int64_t* proposed, int64_t* accepted);
 
+/* Failure-path self test (no counterpart in the paper): launches one kernel
+ * that waits, with the same bounded spin as the batch grid barrier, on a device
+ * flag that nothing sets.  The wait gives up after timeout_s (0 < t <= 10) of
+ * SM clock cycles; the call then returns ISING_ETIMEOUT with *device_status = 1,
+ * and the CUDA context stays usable.  Synchronises. */
+int ising_selftest_wait(double timeout_s, int* device_status);
+
 /* Work items, CTAs used, host-side sweep counter. */
 int ising_batch_info(ising_batch* b, int* n_items, int* grid, int64_t* sweep);
 

@@ -92,6 +92,7 @@ _PROTOS = [
     ("ising_batch_block_pass", _i, [_p, _i, _i]),
     ("ising_batch_block_stats", _i, [_p, _p, _p]),
     ("ising_batch_destroy", _i, [_p]),
+    ("ising_selftest_wait", _i, [_d, _p]),
     ("ising_nn_load", _i, [_p, _p, ctypes.c_size_t]),
     ("ising_block_pass", _i, [_p, _i, _i]),
     ("ising_block_stats", _i, [_p, _p, _p]),
@@ -469,6 +470,13 @@ def ising_batch_block_stats(b: int):
     p, a = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().ising_batch_block_stats(b, ctypes.byref(p), ctypes.byref(a)))
     return int(p.value), int(a.value)
+
+
+def ising_selftest_wait(timeout_s: float) -> int:
+    """Runs the bounded-wait self test; raises IsingError(ETIMEOUT) as designed."""
+    st = ctypes.c_int()
+    _check(lib().ising_selftest_wait(float(timeout_s), ctypes.byref(st)))
+    return int(st.value)
 
 
 def ising_batch_destroy(b: int) -> None:

@@ -85,15 +85,8 @@ __device__ bool grid_barrier(const BatchDev& d) {
       atomicExch(&d.ctr->bar_count, 0u);
       __threadfence();
       atomicAdd(&d.ctr->bar_gen, 1u);
-    } else {
-      const long long start = clock64();
-      while (*gen == g) {
-        if (clock64() - start > d.spin_limit) {
-          atomicExch(&d.ctr->status, 1);
-          break;
-        }
-        __nanosleep(128);
-      }
+    } else if (!bounded_wait_while_eq(gen, g, d.spin_limit)) {
+      atomicExch(&d.ctr->status, 1);
     }
     __threadfence();
   }
@@ -262,6 +255,13 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev d, int n_sweeps) {
     d.ctr->sweep = sweep0 + (uint32_t)n_sweeps;
     d.ctr->launches += 1;
   }
+}
+
+// Waits on a word nothing writes, with the same bounded spin as the grid
+// barrier; records 1 in *status when the budget runs out.
+__global__ void k_wait_selftest(const unsigned int* never_set, long long limit, int* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    if (!bounded_wait_while_eq(never_set, 0u, limit)) *status = 1;
 }
 
 __global__ void k_batch_init(uint32_t* spins, const long long* off, const int* lad_L, int n_beta,
@@ -840,6 +840,36 @@ int ising_batch_block_stats(ising_batch* b, int64_t* proposed, int64_t* accepted
   }
   if (proposed) *proposed = (int64_t)h[0];
   if (accepted) *accepted = (int64_t)h[1];
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_selftest_wait(double timeout_s, int* device_status) {
+  if (!(timeout_s > 0.0 && timeout_s <= 10.0)) return bfail(ISING_EINVAL, "timeout must be in (0, 10] s");
+  int dev = 0, khz = 0;
+  BTRY(cudaGetDevice(&dev));
+  BTRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  const long long limit = (long long)(timeout_s * (double)khz * 1000.0);
+  unsigned int* flag = nullptr;
+  int* st = nullptr;
+  if (int e = balloc(&flag, 1)) return e;
+  if (int e = balloc(&st, 1)) {
+    cudaFree(flag);
+    return e;
+  }
+  cudaError_t e = cudaMemset(flag, 0, sizeof(unsigned int));
+  if (!e) e = cudaMemset(st, 0, sizeof(int));
+  if (!e) {
+    k_wait_selftest<<<1, 32>>>(flag, limit, st);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (!e) e = cudaMemcpy(&h, st, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(flag);
+  cudaFree(st);
+  if (e) return bfail(ISING_ECUDA, "self-test: %s", cudaGetErrorString(e));
+  if (device_status) *device_status = h;
+  if (h == 1) return bfail(ISING_ETIMEOUT, "bounded device wait ran out after %.3f s", timeout_s);
   set_last_error("");
   return ISING_OK;
 }

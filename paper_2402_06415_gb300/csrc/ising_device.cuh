@@ -140,6 +140,19 @@ __device__ __forceinline__ uint32_t side_word(const Row& row, int w, int Wc, int
   }
 }
 
+// Spins while *word == value, for at most `limit` clock64 cycles.  Returns
+// true when the word changed, false when the budget ran out (the caller then
+// records an error status and returns instead of waiting forever).
+__device__ __forceinline__ bool bounded_wait_while_eq(const volatile unsigned int* word,
+                                                      unsigned int value, long long limit) {
+  const long long start = clock64();
+  while (*word == value) {
+    if (clock64() - start > limit) return false;
+    __nanosleep(128);
+  }
+  return true;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -265,3 +265,19 @@ def test_full_size_L16384_first_sweeps():
         got = lat.spins()
     assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
     assert np.array_equal(got, ref)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait on a flag nothing sets gives up after its budget and
+    reports ETIMEOUT; the context keeps working afterwards."""
+    import time
+
+    t0 = time.perf_counter()
+    with pytest.raises(ising.IsingError) as e:
+        ising.ising_selftest_wait(0.2)
+    dt = time.perf_counter() - t0
+    assert e.value.status == ising.ISING_ETIMEOUT
+    assert 0.05 < dt < 5.0
+    ref, E_ref, _ = _oracle_run(64, BETA_C, 3, 4)
+    got, E, _ = _gpu_run(64, BETA_C, 3, 4, BITS, HALF)
+    assert np.array_equal(got, ref) and np.array_equal(E, E_ref)
