@@ -481,6 +481,7 @@ int ising_get_state(ising_ctx* c, uint64_t* seed, uint32_t* replica, int64_t* sw
 
 int ising_sweep(ising_ctx* c, int n_sweeps, int measure_every) {
   if (int st = check_ctx(c)) return st;
+  NvtxRange nvtx("ising_sweep");
   if (n_sweeps < 0) return fail(ISING_EINVAL, "n_sweeps must be >= 0");
   if (measure_every < 0) return fail(ISING_EINVAL, "measure_every must be >= 0");
   if (c->sweep + n_sweeps >= ((int64_t)1 << 32))
@@ -764,6 +765,7 @@ int ising_nn_load(ising_ctx* c, const void* bf16_weights, size_t bytes) {
 
 int ising_block_pass(ising_ctx* c, int n_passes, int block) {
   if (int st = check_ctx(c)) return st;
+  NvtxRange nvtx("ising_block_pass");
   if (!c->nn_w) return fail(ISING_EINVAL, "no network loaded (ising_nn_load)");
   if (c->layout != ISING_LAYOUT_BITS) return fail(ISING_EINVAL, "block passes need the packed layout");
   if (block != 2 && block != 4 && block != 8 && block != 16)

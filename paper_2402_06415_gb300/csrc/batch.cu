@@ -644,6 +644,7 @@ int ising_batch_set_series(ising_batch* b, int capacity) {
 
 int ising_batch_run(ising_batch* b, int n_sweeps) {
   if (int st = check_b(b)) return st;
+  NvtxRange nvtx("ising_batch_run");
   if (n_sweeps < 0) return bfail(ISING_EINVAL, "n_sweeps must be >= 0");
   if (b->sweep + n_sweeps >= ((int64_t)1 << 32)) return bfail(ISING_EINVAL, "sweep counter overflow");
   if (n_sweeps == 0) return ISING_OK;
@@ -798,6 +799,7 @@ int ising_batch_nn_load(ising_batch* b, const void* bf16_weights, size_t bytes) 
 
 int ising_batch_block_pass(ising_batch* b, int n_passes, int block) {
   if (int st = check_b(b)) return st;
+  NvtxRange nvtx("ising_batch_block_pass");
   if (!b->nn_w) return bfail(ISING_EINVAL, "no network loaded (ising_batch_nn_load)");
   if (block != 2 && block != 4 && block != 8 && block != 16)
     return bfail(ISING_EINVAL, "block must be 2, 4, 8 or 16");

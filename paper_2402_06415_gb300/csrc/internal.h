@@ -2,10 +2,18 @@
 // Every launcher enqueues on `stream` and returns the launch status.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 
 namespace ising {
+
+// NVTX range for the lifetime of the object (profiler timelines; a no-op when
+// no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Per-sweep record slots for one launch that covers up to kMaxSweepsPerLaunch
 // sweeps: slot[s] >= 0 is the index (in units of 2 x u64: anti-bond count,

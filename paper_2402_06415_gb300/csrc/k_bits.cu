@@ -243,6 +243,36 @@ __device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep
   }
 }
 
+// lazy_planes for two independent words at once (one warp vote for both; two
+// Philox chains in flight per thread).
+template <int B0, int B1>
+__device__ __forceinline__ void lazy_planes2(uint32_t ga, uint32_t gb, uint32_t t, uint32_t rep,
+                                             uint32_t colour, const RngParams& rng, uint32_t& Da,
+                                             uint32_t clsa, uint32_t& acca, uint32_t& Db,
+                                             uint32_t clsb, uint32_t& accb) {
+#pragma unroll
+  for (int b = B0; b < B1; ++b) {
+    if (!__any_sync(0xffffffffu, (Da | Db) != 0u)) break;
+    const uint32_t cw = ctr_w(kTagMet, colour, b);
+    const uint4 ra = philox10_rk(make_uint4(ga, t, rep, cw), rng.rk0, rng.rk1);
+    const uint4 rb = philox10_rk(make_uint4(gb, t, rep, cw), rng.rk0, rng.rk1);
+    const uint32_t pa[4] = {ra.x, ra.y, ra.z, ra.w};
+    const uint32_t pb[4] = {rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * b + q;
+      const uint32_t m4 = 0u - ((rng.t4 >> (31 - k)) & 1u);
+      const uint32_t m8 = 0u - ((rng.t8 >> (31 - k)) & 1u);
+      const uint32_t ta = (clsa & m4) | (~clsa & m8);
+      const uint32_t tb = (clsb & m4) | (~clsb & m8);
+      acca |= Da & ta & ~pa[q];
+      accb |= Db & tb & ~pb[q];
+      Da &= ~(ta ^ pa[q]);
+      Db &= ~(tb ^ pb[q]);
+    }
+  }
+}
+
 // Tiled sweep with one warp per 32-word tile row segment.  Same tiling, halo
 // and results as k_tiled_bits; differences are for speed only:
 //  * the inner 32*TWW words of a row are updated by TWW warps (lane = word), the
@@ -254,7 +284,7 @@ __device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep
 //    words, instead of every warp waiting for its slowest word;
 //  * per-sweep observables are summed in shared memory, not registers.
 template <int K, int TWW>
-__global__ void __launch_bounds__(256, 4) k_tiled32_bits(const uint32_t* __restrict__ in,
+__global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restrict__ in,
                                                          uint32_t* __restrict__ out, int L, int Wc,
                                                          int n_ty, uint32_t t0, RngParams rng,
                                                          RecordSlots slots,
@@ -360,10 +390,63 @@ __global__ void __launch_bounds__(256, 4) k_tiled32_bits(const uint32_t* __restr
           if (ovf) So[r * SP + col] ^= acc2;
         }
       };
-      for (int item = warp; item < nrows * TWW; item += nwarps) {
-        const int r = r_lo + item / TWW;
+      // queue a word whose lanes are still undecided after phase 1 (returns
+      // false if the queue is full; the caller then finishes it in place)
+      auto enqueue = [&](int r, int col, uint32_t D, uint32_t cls) {
+        const int slot = atomicAdd(qn, 1);
+        if (slot >= QCAP) return false;
+        q_pos[slot] = ((uint32_t)r << 8) | (uint32_t)col;
+        q_d[slot] = D;
+        q_cls[slot] = cls;
+        return true;
+      };
+      // inner words of two adjacent rows (r, r+1) per thread: the two words
+      // share the other colour's rows r and r+1 as neighbours
+      auto phase1_pair = [&](int r, int col) {
+        const uint32_t sa = So[r * SP + col];
+        const uint32_t sb = So[(r + 1) * SP + col];
+        const uint32_t u0 = Sn[(r - 1) * SP + col];
+        const uint32_t m0 = Sn[r * SP + col];
+        const uint32_t m1 = Sn[(r + 1) * SP + col];
+        const uint32_t d1 = Sn[(r + 2) * SP + col];
+        const int oa = (y0 + r + c) & 1;  // row r+1 has the other offset
+        uint32_t side_a, side_b;
+        if (oa == 0) {
+          side_a = (m0 << 1) | (Sn[r * SP + col - 1] >> 31);
+          side_b = (m1 >> 1) | (Sn[(r + 1) * SP + col + 1] << 31);
+        } else {
+          side_a = (m0 >> 1) | (Sn[r * SP + col + 1] << 31);
+          side_b = (m1 << 1) | (Sn[(r + 1) * SP + col - 1] >> 31);
+        }
+        const Classes ka = classify(sa, u0, m1, m0, side_a);
+        const Classes kb = classify(sb, m0, d1, m1, side_b);
+        uint32_t Da = ka.one | ka.zero, Db = kb.one | kb.zero, acca = 0, accb = 0;
+        const int gya = grow(r);
+        const int gyb = gya + 1 == L ? 0 : gya + 1;
+        const uint32_t gw = (uint32_t)(w0 + col - 4);  // inner column: no wrap
+        const uint32_t ga = (uint32_t)gya * (uint32_t)Wc + gw;
+        const uint32_t gb = (uint32_t)gyb * (uint32_t)Wc + gw;
+        lazy_planes2<0, 2>(ga, gb, t, rng.replica, c, rng, Da, ka.one, acca, Db, kb.one, accb);
+        So[r * SP + col] = sa ^ (ka.ge2 | acca);
+        So[(r + 1) * SP + col] = sb ^ (kb.ge2 | accb);
+        const bool ovfa = Da != 0u && !enqueue(r, col, Da, ka.one);
+        const bool ovfb = Db != 0u && !enqueue(r + 1, col, Db, kb.one);
+        if (__any_sync(0xffffffffu, ovfa || ovfb)) {  // queue full: finish in place
+          uint32_t ea = ovfa ? Da : 0u, eb = ovfb ? Db : 0u, xa = 0, xb = 0;
+          lazy_planes2<2, 8>(ga, gb, t, rng.replica, c, rng, ea, ka.one, xa, eb, kb.one, xb);
+          if (ovfa) So[r * SP + col] ^= xa;
+          if (ovfb) So[(r + 1) * SP + col] ^= xb;
+        }
+      };
+      const int npairs = nrows >> 1;
+      for (int item = warp; item < npairs * TWW; item += nwarps) {
+        const int r = r_lo + 2 * (item / TWW);
         const int col = 4 + 32 * (item % TWW) + lane;
-        phase1(r, col, true);
+        phase1_pair(r, col);
+      }
+      if (nrows & 1) {  // odd row count: the last row alone
+        for (int item = warp; item < TWW; item += nwarps)
+          phase1(r_lo + nrows - 1, 4 + 32 * item + lane, true);
       }
       for (int base = warp * 32; base < 2 * nrows; base += blockDim.x) {
         const int idx = base + lane;
