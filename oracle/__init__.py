@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "xy_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -33,11 +34,11 @@ BETA_C = float(np.log(1.0 + np.sqrt(2.0)) / 2.0)
 def build(force: bool = False) -> str:
     """Compile ``ising_oracle.c`` with gcc into ``liboracle.so``."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -81,6 +82,26 @@ def lib() -> ctypes.CDLL:
         L.orc_n_anti_all.restype = None
         L.orc_pt_step.argtypes = [i32, p, u64, u32, u32, p, p, p, p]
         L.orc_pt_step.restype = None
+        L.orc_xy_sincos_d.argtypes = [dbl, p, p]
+        L.orc_xy_sincos_d.restype = None
+        L.orc_xy_exp_d.argtypes = [dbl]
+        L.orc_xy_exp_d.restype = dbl
+        L.orc_xy_sincos_f.argtypes = [ctypes.c_float, p, p]
+        L.orc_xy_sincos_f.restype = None
+        L.orc_xy_exp_f.argtypes = [ctypes.c_float]
+        L.orc_xy_exp_f.restype = ctypes.c_float
+        L.orc_xy_init_d.argtypes = [i32, u64, u32, p]
+        L.orc_xy_init_d.restype = None
+        L.orc_xy_init_f.argtypes = [i32, u64, u32, p]
+        L.orc_xy_init_f.restype = None
+        L.orc_xy_sweep_d.argtypes = [i32, dbl, u64, u32, u32, p]
+        L.orc_xy_sweep_d.restype = i64
+        L.orc_xy_sweep_f.argtypes = [i32, ctypes.c_float, u64, u32, u32, p]
+        L.orc_xy_sweep_f.restype = i64
+        L.orc_xy_observables_d.argtypes = [i32, p, p, p, p]
+        L.orc_xy_observables_d.restype = None
+        L.orc_xy_observables_f.argtypes = [i32, p, p, p, p]
+        L.orc_xy_observables_f.restype = None
         _lib = L
     return _lib
 
@@ -244,3 +265,48 @@ def run_ladders(Ls, betas, seed: int, n_sweeps: int, pt_every: int, ladder_ids=N
     if record:
         return spins, perm, E, M, acc, att, series
     return spins, perm, E, M, acc, att
+
+
+# ---------------------------------------------------------------------------
+# 2D XY model (the paper's Monte Carlo workload)
+# ---------------------------------------------------------------------------
+
+def xy_sincos(x: float, precision: int = 64):
+    s, c = (ctypes.c_double(), ctypes.c_double()) if precision == 64 else (ctypes.c_float(), ctypes.c_float())
+    f = lib().orc_xy_sincos_d if precision == 64 else lib().orc_xy_sincos_f
+    f(x, ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def xy_exp(x: float, precision: int = 64) -> float:
+    return (lib().orc_xy_exp_d if precision == 64 else lib().orc_xy_exp_f)(x)
+
+
+def xy_init(L: int, seed: int, replica: int = 0, precision: int = 64) -> np.ndarray:
+    """Seeded random start: unit vectors (cos, sin) as an (L, L, 2) array."""
+    dt = np.float64 if precision == 64 else np.float32
+    u = np.zeros((L, L, 2), dtype=dt)
+    (lib().orc_xy_init_d if precision == 64 else lib().orc_xy_init_f)(L, seed, replica, _ptr(u))
+    return u
+
+
+def xy_observables(u: np.ndarray):
+    """(E, Mx, My) in double: E = -sum_x u_x . (u_{x+e1} + u_{x+e2})."""
+    E, Mx, My = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    f = lib().orc_xy_observables_d if u.dtype == np.float64 else lib().orc_xy_observables_f
+    f(u.shape[0], _ptr(u), ctypes.byref(E), ctypes.byref(Mx), ctypes.byref(My))
+    return E.value, Mx.value, My.value
+
+
+def xy_sweep(u: np.ndarray, beta: float, seed: int, n_sweeps: int, t0: int = 0, replica: int = 0,
+             record: bool = True):
+    """n_sweeps sweeps in place; returns (accepted per sweep, E per sweep)."""
+    L = u.shape[0]
+    f = lib().orc_xy_sweep_d if u.dtype == np.float64 else lib().orc_xy_sweep_f
+    acc = np.zeros(n_sweeps, dtype=np.int64)
+    E = np.zeros(n_sweeps)
+    for k in range(n_sweeps):
+        acc[k] = f(L, beta, seed, replica, t0 + k, _ptr(u))
+        if record:
+            E[k] = xy_observables(u)[0]
+    return acc, E
