@@ -324,6 +324,32 @@ int ising_nn_loss_grad(ising_nn* nn, const int8_t* dev_windows, int count, float
 int ising_nn_train_step(ising_nn* nn, const int8_t* dev_windows, int count, float lr, float* loss);
 int ising_nn_destroy(ising_nn* nn);
 
+/* ------------------------------------------------------------------------
+ * 2D XY model: the paper's own Monte Carlo workload (Eq. 1; Supplementary
+ * "Detail of the MC calculation for the XY model"; checkerboard of Fig. 2).
+ * Spins are unit vectors u = (cos theta, sin theta).  Per site: theta' = 2 pi U1,
+ * p = U2 (24-bit uniforms from Philox), dE = -(u' - u) . h, h = sum of the four
+ * neighbour vectors (Eq. S1 with its sign corrected), accept iff dE <= 0 or
+ * p < exp(-beta dE).  precision: 64 (double, as in the paper) or 32 (float).
+ * cos/sin/exp are the library's own Taylor/Cody-Waite routines, so the chain is
+ * reproducible bit for bit.  L even, 2..32768.  Records (every measure_every
+ * sweeps) hold E = -sum_bonds u.u' and the magnetisation vector, in double.
+ * ------------------------------------------------------------------------ */
+typedef struct ising_xy ising_xy;
+int ising_xy_create(ising_xy** out, int L, double beta, int precision, void* stream);
+/* Seeded random start (uniform angles); sweep counter 0; clears records. */
+int ising_xy_seed(ising_xy* x, uint64_t seed);
+/* n_sweeps sweeps (async). */
+int ising_xy_sweep(ising_xy* x, int n_sweeps, int measure_every);
+/* Last n records (oldest first): E, Mx, My (host arrays; any may be NULL). */
+int ising_xy_series(ising_xy* x, double* E, double* Mx, double* My, int n);
+/* Spins as host [L][L][2] doubles (cos, sin), row-major y*L + x. */
+int ising_xy_get_spins(ising_xy* x, double* host_uv);
+int ising_xy_set_spins(ising_xy* x, const double* host_uv);
+/* Accepted updates since the last seed (synchronises). */
+int ising_xy_accepted(ising_xy* x, int64_t* accepted);
+int ising_xy_destroy(ising_xy* x);
+
 /* Free everything the context owns.  NULL-safe.  Synchronises the stream. */
 int ising_destroy(ising_ctx* ctx);
 

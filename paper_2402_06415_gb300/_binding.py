@@ -106,6 +106,14 @@ _PROTOS = [
     ("ising_nn_loss_grad", _i, [_p, _p, _i, _p, _p]),
     ("ising_nn_train_step", _i, [_p, _p, _i, ctypes.c_float, _p]),
     ("ising_nn_destroy", _i, [_p]),
+    ("ising_xy_create", _i, [ctypes.POINTER(_p), _i, _d, _i, _p]),
+    ("ising_xy_seed", _i, [_p, _u64]),
+    ("ising_xy_sweep", _i, [_p, _i, _i]),
+    ("ising_xy_series", _i, [_p, _p, _p, _p, _i]),
+    ("ising_xy_get_spins", _i, [_p, _p]),
+    ("ising_xy_set_spins", _i, [_p, _p]),
+    ("ising_xy_accepted", _i, [_p, _p]),
+    ("ising_xy_destroy", _i, [_p]),
     ("ising_destroy", _i, [_p]),
     ("ising_last_error", ctypes.c_char_p, []),
 ]
@@ -621,3 +629,62 @@ def ising_nn_train_step(nn: int, dev_windows, count: int, lr: float) -> float:
 
 def ising_nn_destroy(nn: int) -> None:
     _check(lib().ising_nn_destroy(nn))
+
+
+# ---------------------------------------------------------------------------
+# 2D XY model
+# ---------------------------------------------------------------------------
+
+class XY:
+    """Owning wrapper of an ising_xy context (unit-vector spins)."""
+
+    def __init__(self, L: int, beta: float, precision: int = 64, stream=None, seed=None):
+        self.L = int(L)
+        out = ctypes.c_void_p()
+        _check(lib().ising_xy_create(ctypes.byref(out), self.L, float(beta), int(precision),
+                                     _stream_ptr(stream)))
+        self.h = out.value
+        if seed is not None:
+            self.seed(seed)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().ising_xy_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seed(self, seed: int):
+        _check(lib().ising_xy_seed(self.h, int(seed)))
+
+    def sweep(self, n: int, measure_every: int = 0):
+        _check(lib().ising_xy_sweep(self.h, int(n), int(measure_every)))
+
+    def series(self, n: int):
+        E, Mx, My = (np.zeros(max(n, 1)) for _ in range(3))
+        _check(lib().ising_xy_series(self.h, _ptr(E), _ptr(Mx), _ptr(My), int(n)))
+        return E[:n], Mx[:n], My[:n]
+
+    def spins(self) -> np.ndarray:
+        u = np.zeros((self.L, self.L, 2))
+        _check(lib().ising_xy_get_spins(self.h, _ptr(u)))
+        return u
+
+    def set_spins(self, u: np.ndarray):
+        v = np.ascontiguousarray(u, dtype=np.float64)
+        _check(lib().ising_xy_set_spins(self.h, _ptr(v)))
+
+    def accepted(self) -> int:
+        a = ctypes.c_int64()
+        _check(lib().ising_xy_accepted(self.h, ctypes.byref(a)))
+        return int(a.value)
