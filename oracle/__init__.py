@@ -82,6 +82,10 @@ def lib() -> ctypes.CDLL:
         L.orc_n_anti_all.restype = None
         L.orc_pt_step.argtypes = [i32, p, u64, u32, u32, p, p, p, p]
         L.orc_pt_step.restype = None
+        L.orc_sw_threshold.argtypes = [dbl]
+        L.orc_sw_threshold.restype = u32
+        L.orc_sw_step.argtypes = [i32, dbl, u64, u32, u32, p, p]
+        L.orc_sw_step.restype = i64
         L.orc_xy_sincos_d.argtypes = [dbl, p, p]
         L.orc_xy_sincos_d.restype = None
         L.orc_xy_exp_d.argtypes = [dbl]
@@ -310,3 +314,26 @@ def xy_sweep(u: np.ndarray, beta: float, seed: int, n_sweeps: int, t0: int = 0, 
         if record:
             E[k] = xy_observables(u)[0]
     return acc, E
+
+
+# ---------------------------------------------------------------------------
+# Swendsen-Wang cluster update
+# ---------------------------------------------------------------------------
+
+def sw_threshold(beta: float) -> int:
+    return int(lib().orc_sw_threshold(float(beta)))
+
+
+def sw_steps(s: np.ndarray, beta: float, seed: int, n_steps: int, step0: int = 0,
+             replica: int = 0):
+    """n Swendsen-Wang steps in place; returns (E, M, clusters) after each step."""
+    assert s.dtype == np.int8 and s.flags["C_CONTIGUOUS"]
+    L = s.shape[0]
+    parent = np.zeros(L * L, dtype=np.uint32)
+    E = np.zeros(n_steps, dtype=np.int64)
+    M = np.zeros(n_steps, dtype=np.int64)
+    C = np.zeros(n_steps, dtype=np.int64)
+    for k in range(n_steps):
+        C[k] = lib().orc_sw_step(L, float(beta), seed, replica, step0 + k, _ptr(s), _ptr(parent))
+        E[k], M[k] = energy_mag(s)
+    return E, M, C

@@ -295,3 +295,62 @@ void orc_pt_step(int n_beta, const double *betas, uint64_t seed, uint32_t ladder
         }
     }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Swendsen-Wang cluster update (Swendsen & Wang, PRL 58, 86 (1987)); the  */
+/* paper names cluster updates as the next step beyond its single-site MC. */
+/* One step: every bond between equal spins is activated with probability  */
+/* p = 1 - exp(-2 beta), i.e. iff u < floor(p 2^32), u = word (b & 3) of    */
+/* Philox(b >> 2, step, r, SW_BOND << 16) for bond b = 2 (y L + x) + dir    */
+/* (dir 0: to x+1, 1: to y+1); clusters = connected components of active   */
+/* bonds; each cluster flips iff bit 31 of word (m & 3) of                  */
+/* Philox(m >> 2, step, r, SW_FLIP << 16), m = its smallest site index.     */
+/* ---------------------------------------------------------------------- */
+enum { ORC_TAG_SW_BOND = 10, ORC_TAG_SW_FLIP = 11 };
+
+uint32_t orc_sw_threshold(double beta)
+{
+    double p = 1.0 - exp(-2.0 * beta);
+    double t = floor(p * 4294967296.0);
+    if (t >= 4294967295.0) return 0xffffffffu;
+    if (t <= 0.0) return 0u;
+    return (uint32_t)t;
+}
+
+static uint32_t sw_find(uint32_t *parent, uint32_t a)
+{
+    while (parent[a] != a) a = parent[a];
+    return a;
+}
+
+/* One SW step in place; parent is scratch of L*L entries.  Returns the
+ * number of clusters. */
+long long orc_sw_step(int L, double beta, uint64_t seed, uint32_t r, uint32_t step, int8_t *s,
+                      uint32_t *parent)
+{
+    const uint32_t N = (uint32_t)L * (uint32_t)L;
+    const uint32_t thr = orc_sw_threshold(beta);
+    for (uint32_t i = 0; i < N; ++i) parent[i] = i;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x)
+            for (int dir = 0; dir < 2; ++dir) {
+                int xn = dir == 0 ? (x + 1) % L : x, yn = dir == 0 ? y : (y + 1) % L;
+                uint32_t a = (uint32_t)(y * L + x), b = (uint32_t)(yn * L + xn);
+                if (s[a] != s[b]) continue;
+                uint32_t bond = 2 * a + (uint32_t)dir, o[4];
+                orc_block(seed, bond >> 2, step, r, ORC_TAG_SW_BOND, 0, 0, o);
+                if (o[bond & 3] >= thr) continue;
+                uint32_t ra = sw_find(parent, a), rb = sw_find(parent, b);
+                if (ra == rb) continue;
+                if (ra < rb) parent[rb] = ra; else parent[ra] = rb;  /* root = smallest index */
+            }
+    long long clusters = 0;
+    for (uint32_t i = 0; i < N; ++i) {
+        uint32_t m = sw_find(parent, i);
+        if (m == i) ++clusters;
+        uint32_t o[4];
+        orc_block(seed, m >> 2, step, r, ORC_TAG_SW_FLIP, 0, 0, o);
+        if (o[m & 3] >> 31) s[i] = (int8_t)-s[i];
+    }
+    return clusters;
+}
