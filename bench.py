@@ -602,6 +602,138 @@ def run_batch_learned(args):
     return 0
 
 
+def run_xy(args):
+    """The paper's own MC experiment on the XY model (Results C, Fig. 4a): time
+    per MC step at T = 0.85 for L = 8 .. 128 over 10^4 steps, in FP64 (the
+    paper's precision) and FP32, next to the CPU oracle (1 core, FP64); plus
+    site-update throughput on a large lattice."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2402_06415_gb300 as ising
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    beta = 1.0 / 0.85
+    stream = torch.cuda.current_stream()
+    rows = []
+    for L in (8, 16, 32, 64, 128):
+        row = {"L": L}
+        for prec in (64, 32):
+            with ising.XY(L, beta, prec, stream=stream, seed=1) as x:
+                x.sweep(200)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x.sweep(args.xy_steps)
+                e1.record(stream)
+                e1.synchronize()
+                row["gpu_us_per_step_fp%d" % prec] = 1e3 * e0.elapsed_time(e1) / args.xy_steps
+                if prec == 64:
+                    x.sweep(1, 1)
+                    E, _, _ = x.series(1)
+                    row["energy_per_site_fp64"] = float(E[-1]) / (L * L)
+        u = oracle.xy_init(L, 1)
+        n_cpu = max(20, 20000 // L)
+        t0 = time.perf_counter()
+        oracle.xy_sweep(u, beta, 1, n_cpu, record=False)
+        row["cpu_us_per_step_fp64"] = 1e6 * (time.perf_counter() - t0) / n_cpu
+        rows.append(row)
+    thr = {}
+    for prec in (64, 32):
+        with ising.XY(4096, beta, prec, stream=stream, seed=2) as x:
+            x.sweep(5)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x.sweep(50)
+            e1.record(stream)
+            e1.synchronize()
+            thr["fp%d" % prec] = 4096 * 4096 * 50 / (e0.elapsed_time(e1) * 1e6)
+    line = {"metric": "XY-model MC time per step (the paper's Fig. 4a experiment)",
+            "value": thr["fp64"], "unit": "site updates/ns (L=4096, FP64)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "2D XY model, checkerboard Metropolis, T=0.85, 10^4 steps "
+                                   "per size", "steps": args.xy_steps},
+            "per_size": rows, "throughput_L4096": thr,
+            "paper_context": "FPGA (XC7K325T, pipelined, FP64): 42.36 us per step at L=32 "
+                             "(Tab. S3); 16.5x a Xeon Gold 6230 core at L=128"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sw(args):
+    """Swendsen-Wang cluster steps against single-site Metropolis at beta_c:
+    independent |M| and E samples per second at L = 128 and 256 (tau_int from
+    the recorded series; SW alone at L = 1024), plus site throughput of one
+    cluster step at L = 4096 and 16384."""
+    import numpy as np
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import stats
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    beta = 0.4406868
+    stream = torch.cuda.current_stream()
+
+    def chain(L, mode, n, therm):
+        with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=500 + L) as lat:
+            step = lat.sweep if mode == "metropolis" else lat.sw_step
+            step(therm)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(n, 1)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            E, M = lat.series(n)
+        tm = stats.tau_int(np.abs(M).astype(float))
+        te = stats.tau_int(E.astype(float))
+        per_s = n / (ms / 1e3)
+        return {"steps": n, "steps_per_s": per_s, "tau_int_absM": tm, "tau_int_E": te,
+                "indep_samples_per_s_absM": per_s / (2 * tm),
+                "indep_samples_per_s_E": per_s / (2 * te), "run_over_tau_absM": n / tm,
+                "energy_per_site": float(np.mean(E)) / (L * L)}
+
+    rows = []
+    for L in (128, 256):
+        met = chain(L, "metropolis", args.chain_sweeps, args.thermalise)
+        sw = chain(L, "sw", args.sw_steps, 200)
+        rows.append({"L": L, "metropolis": met, "sw": sw,
+                     "gain_indep_samples_absM": sw["indep_samples_per_s_absM"]
+                     / met["indep_samples_per_s_absM"]})
+    # Metropolis needs runs of ~10^3 tau_int(|M|) ~ L^2.2 sweeps beyond L = 256
+    rows.append({"L": 1024, "sw": chain(1024, "sw", args.sw_steps, 200)})
+    thr = {}
+    for L in (4096, 16384):
+        with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=9) as lat:
+            lat.sw_step(3)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.sw_step(10)
+            e1.record(stream)
+            e1.synchronize()
+            thr["L%d" % L] = {"ms_per_step": e0.elapsed_time(e1) / 10,
+                              "site_updates_per_ns": L * L * 10 / (e0.elapsed_time(e1) * 1e6)}
+    line = {"metric": "independent samples/s at beta_c, Swendsen-Wang vs Metropolis",
+            "value": rows[1]["sw"]["indep_samples_per_s_absM"],
+            "unit": "independent |M| samples/s (SW, L=256, beta_c)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u32",
+            "config": {"workload": "2D Ising at beta_c: Swendsen-Wang cluster steps vs "
+                                   "checkerboard Metropolis sweeps, L in {128, 256} (SW also 1024)",
+                       "sw_steps": args.sw_steps, "metropolis_sweeps": args.chain_sweeps},
+            "per_size": rows, "sw_throughput": thr}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     global SWEEPS_PER_STEP
     ap = argparse.ArgumentParser()
@@ -619,7 +751,9 @@ def main(argv=None):
     ap.add_argument("--thermalise", type=int, default=5000)
     ap.add_argument("--scan-blocks", type=int, nargs="*", default=[2, 4, 8, 16])
     ap.add_argument("--scan-sweeps", type=int, default=3000)
-    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned"],
+    ap.add_argument("--xy-steps", type=int, default=10000)
+    ap.add_argument("--sw-steps", type=int, default=20000)
+    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw"],
                     default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
@@ -639,6 +773,10 @@ def main(argv=None):
         return run_learned(args)
     if args.workload == "batch_learned":
         return run_batch_learned(args)
+    if args.workload == "xy":
+        return run_xy(args)
+    if args.workload == "sw":
+        return run_sw(args)
     return run_ours(args)
 
 
