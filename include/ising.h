@@ -300,6 +300,19 @@ int ising_block_pass(ising_ctx* ctx, int n_passes, int block);
  * side `block` (block_every = 0: plain sweeps only).  Async. */
 int ising_sweep_blocks(ising_ctx* ctx, int n_sweeps, int measure_every, int block, int block_every);
 
+/* Swendsen-Wang cluster steps on the packed lattice (no counterpart in the
+ * paper beyond its pointer to cluster methods; Swendsen & Wang 1987).  Step n:
+ * bonds between equal spins are active iff u < floor((1 - exp(-2 beta)) 2^32),
+ * u = word (b & 3) of Philox(b >> 2, n, replica, SW_BOND << 16) for bond
+ * b = 2 (y L + x) + dir (dir 0: to x+1, 1: to y+1); each connected cluster flips
+ * iff bit 31 of word (m & 3) of Philox(m >> 2, n, replica, SW_FLIP << 16), m its
+ * smallest site index.  Records E, M after every step n with
+ * (n + 1) % measure_every == 0 into the same record ring as ising_sweep.  The
+ * step counter n is separate from the sweep counter and starts at 0.  Allocates
+ * 5 bytes per site of scratch on first use; L = 65536 (2^32 sites) is
+ * rejected with ISING_EINVAL.  Async. */
+int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);
+
 /* Squares proposed and accepted by this context's block passes (synchronises). */
 int ising_block_stats(ising_ctx* ctx, int64_t* proposed, int64_t* accepted);
 

@@ -97,6 +97,7 @@ _PROTOS = [
     ("ising_block_pass", _i, [_p, _i, _i]),
     ("ising_block_stats", _i, [_p, _p, _p]),
     ("ising_sweep_blocks", _i, [_p, _i, _i, _i, _i]),
+    ("ising_sw_step", _i, [_p, _i, _i]),
     ("ising_nn_param_count", _i, []),
     ("ising_nn_create", _i, [ctypes.POINTER(_p), _i, _i, _p]),
     ("ising_nn_set_params", _i, [_p, _p, _i]),
@@ -365,6 +366,10 @@ class Lattice:
     def sweep(self, n: int, measure_every: int = 0):
         ising_sweep(self.ctx, n, measure_every)
 
+    def sw_step(self, n: int, measure_every: int = 0):
+        """n Swendsen-Wang cluster steps (packed layout only)."""
+        ising_sw_step(self.ctx, n, measure_every)
+
     def measure(self):
         return ising_measure(self.ctx)
 
@@ -573,6 +578,10 @@ def ising_sweep_blocks(ctx: int, n_sweeps: int, measure_every: int = 0, block: i
                        block_every: int = 1) -> None:
     _check(lib().ising_sweep_blocks(ctx, int(n_sweeps), int(measure_every), int(block),
                                     int(block_every)))
+
+
+def ising_sw_step(ctx: int, n_steps: int, measure_every: int = 0) -> None:
+    _check(lib().ising_sw_step(ctx, int(n_steps), int(measure_every)))
 
 
 def ising_block_stats(ctx: int):

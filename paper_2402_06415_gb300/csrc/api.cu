@@ -89,6 +89,9 @@ struct ising_ctx {
   __nv_bfloat16* nn_w2t = nullptr;
   unsigned long long* blk_stats = nullptr;  // [2] proposed, accepted
   int64_t block_passes = 0;
+  uint32_t* sw_parent = nullptr;  // Swendsen-Wang scratch
+  uint8_t* sw_flip = nullptr;
+  int64_t sw_steps = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
@@ -126,6 +129,10 @@ void free_all(ising_ctx* c) {
   cudaFree(c->nn_w);
   cudaFree(c->nn_w2t);
   cudaFree(c->blk_stats);
+  cudaFree(c->sw_parent);
+  cudaFree(c->sw_flip);
+  c->sw_parent = nullptr;
+  c->sw_flip = nullptr;
   c->nn_w = c->nn_w2t = nullptr;
   c->blk_stats = nullptr;
   c->bits[0] = c->bits[1] = nullptr;
@@ -793,6 +800,44 @@ int ising_sweep_blocks(ising_ctx* c, int n_sweeps, int measure_every, int block,
     if (int st = ising_sweep(c, 1, measure_every)) return st;
     if ((c->sweep % block_every) == 0)
       if (int st = ising_block_pass(c, 1, block)) return st;
+  }
+  return ok();
+}
+
+int ising_sw_step(ising_ctx* c, int n_steps, int measure_every) {
+  if (int st = check_ctx(c)) return st;
+  if (c->layout != ISING_LAYOUT_BITS) return fail(ISING_EINVAL, "cluster steps need the packed layout");
+  if (n_steps < 0 || measure_every < 0) return fail(ISING_EINVAL, "negative count");
+  if (c->sw_steps + n_steps >= ((int64_t)1 << 32)) return fail(ISING_EINVAL, "step counter overflow");
+  if ((int64_t)c->L * c->L >= ((int64_t)1 << 32)) return fail(ISING_EINVAL, "lattice too large");
+  NvtxRange nvtx("ising_sw_step");
+  if (!c->sw_parent) {
+    void* p = nullptr;
+    if (int st = dev_alloc(&p, (size_t)c->N() * sizeof(uint32_t))) return st;
+    c->sw_parent = (uint32_t*)p;
+    if (int st = dev_alloc(&p, (size_t)c->N())) return st;
+    c->sw_flip = (uint8_t*)p;
+  }
+  const double pb = 1.0 - std::exp(-2.0 * c->beta);
+  const double tf = std::floor(pb * 4294967296.0);
+  const uint32_t thr = tf >= 4294967295.0 ? 0xffffffffu : (tf <= 0.0 ? 0u : (uint32_t)tf);
+  const RngParams rng = c->rng();
+  for (int k = 0; k < n_steps; ++k) {
+    const int64_t t = c->sw_steps;
+    Timed tm(c);
+    cudaError_t e = launch_sw_step(c->lat(c->cur), (uint32_t)t, thr, rng, c->sw_parent, c->sw_flip,
+                                   c->stream);
+    if (int st = launch_result(c, e, "cluster step")) return st;
+    c->launches += 3;
+    if (measure_every > 0 && (t + 1) % measure_every == 0) {
+      const int64_t slot = c->rec_count % kRecCap;
+      if (int st = zero_records(c, c->rec_count, 1)) return st;
+      if (int st = launch_result(c, launch_measure_bits(c->lat(c->cur), c->rec + 2 * slot, c->stream),
+                                 "measure"))
+        return st;
+      ++c->rec_count;
+    }
+    ++c->sw_steps;
   }
   return ok();
 }

@@ -101,6 +101,11 @@ cudaError_t nn_batch_block_pass(uint32_t* spins, const long long* off, const int
                                 const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
                                 unsigned long long* stats, cudaStream_t s);
 
+// One Swendsen-Wang step on a packed lattice (sw.cu); parent: L*L uint32 and
+// flip: L*L bytes of scratch.
+cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
+                           const RngParams& rng, uint32_t* parent, uint8_t* flip, cudaStream_t s);
+
 // Sets the message returned by ising_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
