@@ -40,6 +40,16 @@ __device__ __forceinline__ uint32_t find_root(uint32_t* parent, uint32_t a) {
   }
 }
 
+// Read-only walk for the roots pass: a halving store there could overwrite, with
+// a mere ancestor, the root that the site's own thread has just stored.
+__device__ __forceinline__ uint32_t find_root_ro(const uint32_t* parent, uint32_t a) {
+  while (true) {
+    const uint32_t p = __ldcg(&parent[a]);
+    if (p == a) return a;
+    a = p;
+  }
+}
+
 __device__ __forceinline__ void unite(uint32_t* parent, uint32_t a, uint32_t b) {
   while (true) {
     a = find_root(parent, a);
@@ -91,12 +101,13 @@ __global__ void __launch_bounds__(256) k_sw_bonds(const uint32_t* __restrict__ p
   }
 }
 
-// Roots decide their flip; every site records its root.
+// Roots decide their flip; every site records its root (only the site's own
+// thread writes parent[i] here, so afterwards parent[i] is i's root).
 __global__ void k_sw_roots(uint32_t* __restrict__ parent, long long N, uint32_t step,
                            RngParams rng, uint8_t* __restrict__ flip) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    const uint32_t m = find_root(parent, (uint32_t)i);
+    const uint32_t m = find_root_ro(parent, (uint32_t)i);
     parent[i] = m;  // compress: every site now points at its root
     if (m == (uint32_t)i) {
       const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16),
