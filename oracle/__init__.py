@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference arm of ``bench.py`` may import this package.  The
 product path (``paper_2402_06415_gb300``) never imports it; the two share no
 code.  What the oracle computes, and which passage of arXiv 2402.06415 each
-part follows, is stated in ``ising_oracle.c`` (sweep, Philox, counter map),
+part follows, is stated in ``ising_oracle.c`` (sweep, Philox, counter map,
+Swendsen-Wang), ``xy_oracle.c`` (XY model), ``quad_oracle.c`` (four-sublattice
+lattices),
 ``closed_forms.py`` (Onsager / Yang / Kaufman) and ``exact.py`` (brute force).
 
 The C part is compiled by :func:`build` (plain gcc, no CUDA) into
@@ -20,7 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "xy_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "xy_oracle.c"), os.path.join(_HERE, "quad_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -86,6 +88,22 @@ def lib() -> ctypes.CDLL:
         L.orc_sw_threshold.restype = u32
         L.orc_sw_step.argtypes = [i32, dbl, u64, u32, u32, p, p]
         L.orc_sw_step.restype = i64
+        L.orc_quad_neighbours.argtypes = [i32, i32, i32, i32, i32, p]
+        L.orc_quad_neighbours.restype = i32
+        L.orc_quad_threshold.argtypes = [i32, dbl, dbl, dbl, i32, i32, p]
+        L.orc_quad_threshold.restype = u32
+        L.orc_quad_init.argtypes = [i32, u64, u32, p]
+        L.orc_quad_init.restype = None
+        L.orc_quad_uniform.argtypes = [i32, u64, u32, u32, i32, i32, i32]
+        L.orc_quad_uniform.restype = u32
+        L.orc_quad_anti.argtypes = [i32, i32, p, i32, i32, i32, p, p]
+        L.orc_quad_anti.restype = None
+        L.orc_quad_observables.argtypes = [i32, i32, p, p, p, p]
+        L.orc_quad_observables.restype = None
+        L.orc_quad_quarter.argtypes = [i32, i32, dbl, dbl, dbl, u64, u32, u32, i32, p]
+        L.orc_quad_quarter.restype = None
+        L.orc_quad_sweep.argtypes = [i32, i32, dbl, dbl, dbl, u64, u32, u32, i32, i32, p, p, p, p]
+        L.orc_quad_sweep.restype = i32
         L.orc_xy_sincos_d.argtypes = [dbl, p, p]
         L.orc_xy_sincos_d.restype = None
         L.orc_xy_exp_d.argtypes = [dbl]
@@ -337,3 +355,83 @@ def sw_steps(s: np.ndarray, beta: float, seed: int, n_steps: int, step0: int = 0
         C[k] = lib().orc_sw_step(L, float(beta), seed, replica, step0 + k, _ptr(s), _ptr(parent))
         E[k], M[k] = energy_mag(s)
     return E, M, C
+
+
+# ---------------------------------------------------------------------------
+# four-sublattice lattices: square NN (+ NNN) and square-octagon
+# ---------------------------------------------------------------------------
+
+QUAD_SQUARE = 0
+QUAD_SQOCT = 1
+
+
+def quad_neighbours(lattice: int, Lc: int, q: int, X: int, Y: int):
+    """[(q', X', Y', type)] of site (q, X, Y); type 1 = J1 bond, 2 = J2 bond."""
+    out = np.zeros(32, dtype=np.int32)
+    n = lib().orc_quad_neighbours(lattice, Lc, q, X, Y, _ptr(out))
+    return [tuple(int(v) for v in out[4 * k:4 * k + 4]) for k in range(n)]
+
+
+def quad_threshold(lattice: int, beta: float, J1: float, J2: float, a1: int, a2: int):
+    """(threshold, always) of the class with a1 / a2 antiparallel J1 / J2 neighbours."""
+    al = ctypes.c_int()
+    t = lib().orc_quad_threshold(lattice, float(beta), float(J1), float(J2), a1, a2,
+                                 ctypes.byref(al))
+    return int(t), bool(al.value)
+
+
+def quad_init(Lc: int, seed: int, replica: int = 0) -> np.ndarray:
+    """Seeded random start, int8 +-1 as s[q][Y][X]."""
+    s = np.zeros((4, Lc, Lc), dtype=np.int8)
+    lib().orc_quad_init(Lc, seed, replica, _ptr(s))
+    return s
+
+
+def quad_uniform(Lc: int, seed: int, replica: int, t: int, q: int, X: int, Y: int) -> int:
+    return int(lib().orc_quad_uniform(Lc, seed, replica, t, q, X, Y))
+
+
+def quad_anti(lattice: int, s: np.ndarray, q: int, X: int, Y: int):
+    a1, a2 = ctypes.c_int(), ctypes.c_int()
+    lib().orc_quad_anti(lattice, s.shape[1], _ptr(s), q, X, Y, ctypes.byref(a1), ctypes.byref(a2))
+    return a1.value, a2.value
+
+
+def quad_observables(lattice: int, s: np.ndarray):
+    """(B1, B2, M): J1-bond sum, J2-bond sum of s s', magnetisation."""
+    b1, b2, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib().orc_quad_observables(lattice, s.shape[1], _ptr(s), ctypes.byref(b1), ctypes.byref(b2),
+                               ctypes.byref(m))
+    return int(b1.value), int(b2.value), int(m.value)
+
+
+def quad_quarter(lattice: int, s: np.ndarray, beta: float, J1: float, J2: float, seed: int,
+                 t: int, q: int, replica: int = 0) -> None:
+    lib().orc_quad_quarter(lattice, s.shape[1], float(beta), float(J1), float(J2), seed, replica,
+                           t, q, _ptr(s))
+
+
+def quad_sweep(lattice: int, s: np.ndarray, beta: float, J1: float, J2: float, seed: int,
+               n_sweeps: int, t0: int = 0, replica: int = 0, measure_every: int = 1):
+    """n sweeps in place (sublattices 0..3); returns (B1, B2, M) records as int64
+    arrays.  Energy: E = -J1 B1 - J2 B2."""
+    assert s.dtype == np.int8 and s.flags["C_CONTIGUOUS"] and s.shape[0] == 4
+    Lc = s.shape[1]
+    n_rec = sum(1 for t in range(t0, t0 + n_sweeps) if (t + 1) % measure_every == 0)
+    B1 = np.zeros(max(n_rec, 1), dtype=np.int64)
+    B2 = np.zeros(max(n_rec, 1), dtype=np.int64)
+    M = np.zeros(max(n_rec, 1), dtype=np.int64)
+    got = lib().orc_quad_sweep(lattice, Lc, float(beta), float(J1), float(J2), seed, replica, t0,
+                               n_sweeps, measure_every, _ptr(s), _ptr(B1), _ptr(B2), _ptr(M))
+    if got < 0:
+        raise ValueError("bad arguments")
+    return B1[:got], B2[:got], M[:got]
+
+
+def quad_square_image(s: np.ndarray) -> np.ndarray:
+    """s[q][Y][X] of the SQUARE lattice as the L x L image, site (2X + i, 2Y + j)."""
+    Lc = s.shape[1]
+    img = np.zeros((2 * Lc, 2 * Lc), dtype=s.dtype)
+    for q in range(4):
+        img[(q >> 1)::2, (q & 1)::2] = s[q]
+    return img
