@@ -734,6 +734,71 @@ def run_sw(args):
     return 0
 
 
+def run_quad(args):
+    """The paper's quadripartition workloads (Fig. 5b/5d) for the Ising model:
+    time per sweep on the square-octagon lattice (J1 = J2 = 1) and on the square
+    lattice with J2 = 0 and with next-nearest neighbours (J2 = 0.5), N = 16 ..
+    4096 sites, next to the CPU oracle; plus site-update throughput at 8192^2
+    cells (2.7e8 sites)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2402_06415_gb300 as ising
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    beta = 0.4406868
+    stream = torch.cuda.current_stream()
+    models = [("square_octagon", ising.ISING_QUAD_SQOCT, 1.0, 1.0),
+              ("square_nn", ising.ISING_QUAD_SQUARE, 1.0, 0.0),
+              ("square_nn_nnn", ising.ISING_QUAD_SQUARE, 1.0, 0.5)]
+    per_size, thr = [], {}
+    launches = 0
+    for name, lat, J1, J2 in models:
+        for Lc in (2, 4, 6, 8, 16, 32):
+            with ising.Quad(lat, Lc, beta, J1, J2, stream=stream, seed=1) as x:
+                x.sweep(200)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x.sweep(args.quad_sweeps)
+                e1.record(stream)
+                e1.synchronize()
+                us = 1e3 * e0.elapsed_time(e1) / args.quad_sweeps
+            s = oracle.quad_init(Lc, 1)
+            n_cpu = max(20, 40000 // (4 * Lc * Lc))
+            t0 = time.perf_counter()
+            oracle.quad_sweep(lat, s, beta, J1, J2, 1, n_cpu, measure_every=n_cpu)
+            cpu_us = 1e6 * (time.perf_counter() - t0) / n_cpu
+            per_size.append({"lattice": name, "N": 4 * Lc * Lc, "gpu_us_per_sweep": us,
+                             "oracle_us_per_sweep": cpu_us})
+        Lc = 8192
+        with ising.Quad(lat, Lc, beta, J1, J2, stream=stream, seed=2) as x:
+            x.sweep(3)
+            c0 = x.launch_count()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x.sweep(20)
+            e1.record(stream)
+            e1.synchronize()
+            launches += x.launch_count() - c0
+            ms = e0.elapsed_time(e1)
+        thr[name] = {"ms_per_sweep": ms / 20, "site_updates_per_ns": 4 * Lc * Lc * 20 / (ms * 1e6)}
+    line = {"metric": "quadripartite Ising sweeps (the paper's Fig. 5b/5d workloads)",
+            "value": thr["square_octagon"]["site_updates_per_ns"],
+            "unit": "site updates/ns (square-octagon, 8192^2 cells, beta=0.4406868)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u32",
+            "config": {"workload": "Ising on square-octagon and square (NN, NN+NNN) lattices, "
+                                   "four-sublattice Metropolis sweep",
+                       "small_sweeps": args.quad_sweeps, "beta": beta},
+            "gpu_launches": launches, "per_size": per_size, "throughput_8192": thr}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     global SWEEPS_PER_STEP
     ap = argparse.ArgumentParser()
@@ -753,7 +818,8 @@ def main(argv=None):
     ap.add_argument("--scan-sweeps", type=int, default=3000)
     ap.add_argument("--xy-steps", type=int, default=10000)
     ap.add_argument("--sw-steps", type=int, default=20000)
-    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw"],
+    ap.add_argument("--quad-sweeps", type=int, default=2000)
+    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw", "quad"],
                     default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
@@ -777,6 +843,8 @@ def main(argv=None):
         return run_xy(args)
     if args.workload == "sw":
         return run_sw(args)
+    if args.workload == "quad":
+        return run_quad(args)
     return run_ours(args)
 
 

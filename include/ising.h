@@ -363,6 +363,46 @@ int ising_xy_set_spins(ising_xy* x, const double* host_uv);
 int ising_xy_accepted(ising_xy* x, int64_t* accepted);
 int ising_xy_destroy(ising_xy* x);
 
+/* ------------------------------------------------------------------------
+ * Ising model on lattices with a four-site unit cell, swept by sublattice
+ * (the paper's quadripartition: Results "optimising the partition", Fig. 5b/5d,
+ * Supplementary Fig. S4a-c).  Lc x Lc periodic cells, 4 Lc^2 sites, spins as
+ * s[q][Y][X] (q the sublattice).
+ *   ISING_QUAD_SQUARE: square lattice of side 2 Lc, site (2X + i, 2Y + j) in
+ *     sublattice q = i + 2j; J1 on nearest, J2 on diagonal (next-nearest)
+ *     neighbours (J2 = 0: the plain square lattice).
+ *   ISING_QUAD_SQOCT: square-octagon (4.8.8) lattice; cell sites A, B, C, D
+ *     (q = 0..3) joined A-B-C-D-A by J1 bonds, octagon bonds J2 between
+ *     B(X, Y)-D(X+1, Y) and A(X, Y)-C(X, Y+1).
+ * A sweep updates sublattice 0, 1, 2, 3; a site with a1 (a2) antiparallel J1
+ * (J2) neighbours out of z1 (z2) flips iff dE = 2 J1 (z1 - 2 a1) +
+ * 2 J2 (z2 - 2 a2) <= 0 or u < floor(exp(-beta dE) 2^32), u from Philox planes
+ * P_{4m+k} = word k of Philox(g, t, replica, QUAD_MET << 16 | q << 8 | m),
+ * g = Y ceil(Lc/32) + (X >> 5), u = sum_k bit_{X & 31}(P_k) 2^(31-k).  Start:
+ * s = +1 iff bit X & 31 of word 0 of Philox(g, 0, replica, QUAD_INIT << 16 |
+ * q << 8).  Records after sweep t with (t + 1) % measure_every == 0:
+ * B1 = sum over J1 bonds of s s', B2 likewise for J2, M = sum s; the energy is
+ * -J1 B1 - J2 B2.  Lc in [2, 16384]; beta > 0; finite couplings.
+ * ------------------------------------------------------------------------ */
+enum { ISING_QUAD_SQUARE = 0, ISING_QUAD_SQOCT = 1 };
+typedef struct ising_quad ising_quad;
+int ising_quad_create(ising_quad** out, int lattice, int Lc, double beta, double J1, double J2,
+                      void* cuda_stream);
+/* Seeded random start; sweep counter 0; clears records. */
+int ising_quad_seed(ising_quad* x, uint64_t seed);
+/* Replica id of the counter map; re-seeds with the current seed. */
+int ising_quad_set_replica(ising_quad* x, uint32_t replica);
+/* n_sweeps sweeps (async). */
+int ising_quad_sweep(ising_quad* x, int n_sweeps, int measure_every);
+/* Last n records, oldest first (host arrays; any may be NULL).  Synchronises. */
+int ising_quad_series(ising_quad* x, int64_t* B1, int64_t* B2, int64_t* M, int n);
+/* Spins as host int8 [4][Lc][Lc] (+1 / -1).  Synchronise. */
+int ising_quad_get_spins(ising_quad* x, int8_t* host_out);
+int ising_quad_set_spins(ising_quad* x, const int8_t* host_in);
+/* Kernels this context has launched. */
+int ising_quad_launch_count(ising_quad* x, int64_t* count);
+int ising_quad_destroy(ising_quad* x);
+
 /* Free everything the context owns.  NULL-safe.  Synchronises the stream. */
 int ising_destroy(ising_ctx* ctx);
 

@@ -115,6 +115,15 @@ _PROTOS = [
     ("ising_xy_set_spins", _i, [_p, _p]),
     ("ising_xy_accepted", _i, [_p, _p]),
     ("ising_xy_destroy", _i, [_p]),
+    ("ising_quad_create", _i, [ctypes.POINTER(_p), _i, _i, _d, _d, _d, _p]),
+    ("ising_quad_seed", _i, [_p, _u64]),
+    ("ising_quad_set_replica", _i, [_p, ctypes.c_uint32]),
+    ("ising_quad_sweep", _i, [_p, _i, _i]),
+    ("ising_quad_series", _i, [_p, _p, _p, _p, _i]),
+    ("ising_quad_get_spins", _i, [_p, _p]),
+    ("ising_quad_set_spins", _i, [_p, _p]),
+    ("ising_quad_launch_count", _i, [_p, _p]),
+    ("ising_quad_destroy", _i, [_p]),
     ("ising_destroy", _i, [_p]),
     ("ising_last_error", ctypes.c_char_p, []),
 ]
@@ -697,3 +706,74 @@ class XY:
         a = ctypes.c_int64()
         _check(lib().ising_xy_accepted(self.h, ctypes.byref(a)))
         return int(a.value)
+
+
+# ---------------------------------------------------------------------------
+# four-sublattice lattices (square NN + NNN, square-octagon)
+# ---------------------------------------------------------------------------
+
+ISING_QUAD_SQUARE = 0
+ISING_QUAD_SQOCT = 1
+
+
+class Quad:
+    """Owning wrapper of an ising_quad context; spins as s[q][Y][X]."""
+
+    def __init__(self, lattice: int, Lc: int, beta: float, J1: float = 1.0, J2: float = 0.0,
+                 stream=None, seed=None, replica: int = 0):
+        self.Lc = int(Lc)
+        self.lattice = int(lattice)
+        self.J1, self.J2 = float(J1), float(J2)
+        out = ctypes.c_void_p()
+        _check(lib().ising_quad_create(ctypes.byref(out), self.lattice, self.Lc, float(beta),
+                                       self.J1, self.J2, _stream_ptr(stream)))
+        self.h = out.value
+        if replica:
+            _check(lib().ising_quad_set_replica(self.h, int(replica)))
+        if seed is not None:
+            self.seed(seed)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().ising_quad_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seed(self, seed: int):
+        _check(lib().ising_quad_seed(self.h, int(seed)))
+
+    def sweep(self, n: int, measure_every: int = 0):
+        _check(lib().ising_quad_sweep(self.h, int(n), int(measure_every)))
+
+    def series(self, n: int):
+        """(B1, B2, M) of the last n records; energy = -J1 B1 - J2 B2."""
+        B1, B2, M = (np.zeros(max(n, 1), dtype=np.int64) for _ in range(3))
+        _check(lib().ising_quad_series(self.h, _ptr(B1), _ptr(B2), _ptr(M), int(n)))
+        return B1[:n], B2[:n], M[:n]
+
+    def spins(self) -> np.ndarray:
+        s = np.zeros((4, self.Lc, self.Lc), dtype=np.int8)
+        _check(lib().ising_quad_get_spins(self.h, _ptr(s)))
+        return s
+
+    def set_spins(self, s: np.ndarray):
+        v = np.ascontiguousarray(s, dtype=np.int8)
+        if v.shape != (4, self.Lc, self.Lc):
+            raise ValueError("spins must have shape (4, Lc, Lc)")
+        _check(lib().ising_quad_set_spins(self.h, _ptr(v)))
+
+    def launch_count(self) -> int:
+        c = ctypes.c_int64()
+        _check(lib().ising_quad_launch_count(self.h, ctypes.byref(c)))
+        return int(c.value)
