@@ -5,8 +5,8 @@ CPU-baseline / reference arm of ``bench.py`` may import this package.  The
 product path (``paper_2402_06415_gb300``) never imports it; the two share no
 code.  What the oracle computes, and which passage of arXiv 2402.06415 each
 part follows, is stated in ``ising_oracle.c`` (sweep, Philox, counter map,
-Swendsen-Wang), ``xy_oracle.c`` (XY model), ``quad_oracle.c`` (four-sublattice
-lattices),
+Swendsen-Wang), ``xy_oracle.c`` (XY model), ``xyfix_oracle.c`` (fixed-point XY
+for the precision study), ``quad_oracle.c`` (four-sublattice lattices),
 ``closed_forms.py`` (Onsager / Yang / Kaufman) and ``exact.py`` (brute force).
 
 The C part is compiled by :func:`build` (plain gcc, no CUDA) into
@@ -22,7 +22,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "xy_oracle.c"), os.path.join(_HERE, "quad_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "xy_oracle.c"), os.path.join(_HERE, "quad_oracle.c"),
+         os.path.join(_HERE, "xyfix_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -104,6 +105,20 @@ def lib() -> ctypes.CDLL:
         L.orc_quad_quarter.restype = None
         L.orc_quad_sweep.argtypes = [i32, i32, dbl, dbl, dbl, u64, u32, u32, i32, i32, p, p, p, p]
         L.orc_quad_sweep.restype = i32
+        L.orc_xyfix_K.argtypes = [i32]
+        L.orc_xyfix_K.restype = ctypes.c_int32
+        L.orc_xyfix_trig.argtypes = [i32, ctypes.c_int32, p, p]
+        L.orc_xyfix_trig.restype = None
+        L.orc_xyfix_accept.argtypes = [i32, dbl, ctypes.c_int32]
+        L.orc_xyfix_accept.restype = u32
+        L.orc_xyfix_dE.argtypes = [i32, ctypes.c_int32, ctypes.c_int32, i64, i64]
+        L.orc_xyfix_dE.restype = i64
+        L.orc_xyfix_init.argtypes = [i32, i32, u64, u32, p]
+        L.orc_xyfix_init.restype = None
+        L.orc_xyfix_sweep.argtypes = [i32, i32, dbl, u64, u32, u32, p]
+        L.orc_xyfix_sweep.restype = i64
+        L.orc_xyfix_observables.argtypes = [i32, i32, p, p, p, p]
+        L.orc_xyfix_observables.restype = None
         L.orc_xy_sincos_d.argtypes = [dbl, p, p]
         L.orc_xy_sincos_d.restype = None
         L.orc_xy_exp_d.argtypes = [dbl]
@@ -435,3 +450,55 @@ def quad_square_image(s: np.ndarray) -> np.ndarray:
     for q in range(4):
         img[(q >> 1)::2, (q & 1)::2] = s[q]
     return img
+
+
+# ---------------------------------------------------------------------------
+# fixed-point XY model (operand-precision study)
+# ---------------------------------------------------------------------------
+
+def xyfix_K(F: int) -> int:
+    """Number of grid angles k 2^-F in [0, 2 pi)."""
+    return int(lib().orc_xyfix_K(F))
+
+
+def xyfix_trig(F: int, k: int):
+    c, s = ctypes.c_int32(), ctypes.c_int32()
+    lib().orc_xyfix_trig(F, k, ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+def xyfix_accept(F: int, beta: float, e: int) -> int:
+    return int(lib().orc_xyfix_accept(F, float(beta), int(e)))
+
+
+def xyfix_dE(F: int, k: int, k2: int, hx: int, hy: int) -> int:
+    return int(lib().orc_xyfix_dE(F, k, k2, hx, hy))
+
+
+def xyfix_init(L: int, F: int, seed: int, replica: int = 0) -> np.ndarray:
+    """Seeded random start: angle indices k as an (L, L) int32 array."""
+    k = np.zeros((L, L), dtype=np.int32)
+    lib().orc_xyfix_init(L, F, seed, replica, _ptr(k))
+    return k
+
+
+def xyfix_observables(k: np.ndarray, F: int):
+    """(E2, Mx, My) integers: energy = -E2 2^-2F, magnetisation (Mx, My) 2^-F."""
+    e, mx, my = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib().orc_xyfix_observables(k.shape[0], F, _ptr(k), ctypes.byref(e), ctypes.byref(mx),
+                                ctypes.byref(my))
+    return int(e.value), int(mx.value), int(my.value)
+
+
+def xyfix_sweep(k: np.ndarray, F: int, beta: float, seed: int, n_sweeps: int, t0: int = 0,
+                replica: int = 0, record: bool = True):
+    """n sweeps in place; returns (accepted per sweep, E2 per sweep)."""
+    assert k.dtype == np.int32 and k.flags["C_CONTIGUOUS"]
+    L = k.shape[0]
+    acc = np.zeros(n_sweeps, dtype=np.int64)
+    E2 = np.zeros(n_sweeps, dtype=np.int64)
+    for i in range(n_sweeps):
+        acc[i] = lib().orc_xyfix_sweep(L, F, float(beta), seed, replica, t0 + i, _ptr(k))
+        if record:
+            E2[i] = xyfix_observables(k, F)[0]
+    return acc, E2
