@@ -109,13 +109,13 @@ def lib() -> ctypes.CDLL:
         L.orc_xyfix_K.restype = ctypes.c_int32
         L.orc_xyfix_trig.argtypes = [i32, ctypes.c_int32, p, p]
         L.orc_xyfix_trig.restype = None
-        L.orc_xyfix_accept.argtypes = [i32, dbl, ctypes.c_int32]
+        L.orc_xyfix_accept.argtypes = [i32, dbl, ctypes.c_int32, i32]
         L.orc_xyfix_accept.restype = u32
         L.orc_xyfix_dE.argtypes = [i32, ctypes.c_int32, ctypes.c_int32, i64, i64]
         L.orc_xyfix_dE.restype = i64
         L.orc_xyfix_init.argtypes = [i32, i32, u64, u32, p]
         L.orc_xyfix_init.restype = None
-        L.orc_xyfix_sweep.argtypes = [i32, i32, dbl, u64, u32, u32, p]
+        L.orc_xyfix_sweep.argtypes = [i32, i32, i32, dbl, u64, u32, u32, p]
         L.orc_xyfix_sweep.restype = i64
         L.orc_xyfix_observables.argtypes = [i32, i32, p, p, p, p]
         L.orc_xyfix_observables.restype = None
@@ -467,8 +467,9 @@ def xyfix_trig(F: int, k: int):
     return c.value, s.value
 
 
-def xyfix_accept(F: int, beta: float, e: int) -> int:
-    return int(lib().orc_xyfix_accept(F, float(beta), int(e)))
+def xyfix_accept(F: int, beta: float, e: int, qp: bool = False) -> int:
+    """Threshold for dE = e 2^-F; qp: the probability truncated to F bits first."""
+    return int(lib().orc_xyfix_accept(F, float(beta), int(e), int(bool(qp))))
 
 
 def xyfix_dE(F: int, k: int, k2: int, hx: int, hy: int) -> int:
@@ -491,14 +492,15 @@ def xyfix_observables(k: np.ndarray, F: int):
 
 
 def xyfix_sweep(k: np.ndarray, F: int, beta: float, seed: int, n_sweeps: int, t0: int = 0,
-                replica: int = 0, record: bool = True):
-    """n sweeps in place; returns (accepted per sweep, E2 per sweep)."""
+                replica: int = 0, record: bool = True, qp: bool = False):
+    """n sweeps in place; returns (accepted per sweep, E2 per sweep).  qp: the
+    acceptance probability is truncated to F fractional bits."""
     assert k.dtype == np.int32 and k.flags["C_CONTIGUOUS"]
     L = k.shape[0]
     acc = np.zeros(n_sweeps, dtype=np.int64)
     E2 = np.zeros(n_sweeps, dtype=np.int64)
     for i in range(n_sweeps):
-        acc[i] = lib().orc_xyfix_sweep(L, F, float(beta), seed, replica, t0 + i, _ptr(k))
+        acc[i] = lib().orc_xyfix_sweep(L, F, int(bool(qp)), float(beta), seed, replica, t0 + i, _ptr(k))
         if record:
             E2[i] = xyfix_observables(k, F)[0]
     return acc, E2

@@ -17,7 +17,12 @@
  *   energy       dE = -round(((C[k'] - C[k]) hx + (S[k'] - S[k]) hy) / 2^F)
  *                (the sign-corrected Eq. S1 in local-field form);
  *   acceptance   dE <= 0, or u2 < A[dE] = floor(exp(-beta dE 2^-F) 2^32)
- *                (u2 a full 32-bit word, A a table over dE in [1, 9 2^F)).
+ *                (u2 a full 32-bit word, A a table over dE in [1, 9 2^F));
+ *                with qp = 1 the probability itself is held in the same
+ *                fixed-point type first, truncated to F fractional bits:
+ *                A[dE] = floor(exp(-beta dE 2^-F) 2^F) 2^(32-F) (clamped to
+ *                2^32 - 1), the reading in which every operand of the update
+ *                has the angle's type.
  * Sublattice (x + y) even first, then odd.  Random words: start k =
  * floor(w K / 2^32), w = word (n & 3) of Philox(n >> 2, 0, r, XYFIX_INIT << 16),
  * n = y L + x; sweep t, colour c: block Philox(j >> 1, t, r, XYFIX_MET << 16 |
@@ -57,10 +62,14 @@ void orc_xyfix_trig(int F, int32_t k, int32_t *c, int32_t *s)
 }
 
 /* Acceptance threshold for dE = e 2^-F > 0. */
-uint32_t orc_xyfix_accept(int F, double beta, int32_t e)
+uint32_t orc_xyfix_accept(int F, double beta, int32_t e, int qp)
 {
     double dE = ldexp((double)e, -F);
-    double t = floor(exp(-beta * dE) * 4294967296.0);
+    double t;
+    if (qp)
+        t = ldexp(floor(ldexp(exp(-beta * dE), F)), 32 - F);
+    else
+        t = floor(exp(-beta * dE) * 4294967296.0);
     if (t >= 4294967295.0) return 0xffffffffu;
     return (uint32_t)t;
 }
@@ -96,7 +105,8 @@ void orc_xyfix_init(int L, int F, uint64_t seed, uint32_t r, int32_t *k)
 }
 
 /* One sweep t in place; returns the number of accepted moves. */
-int64_t orc_xyfix_sweep(int L, int F, double beta, uint64_t seed, uint32_t r, uint32_t t, int32_t *k)
+int64_t orc_xyfix_sweep(int L, int F, int qp, double beta, uint64_t seed, uint32_t r, uint32_t t,
+                        int32_t *k)
 {
     uint32_t K = (uint32_t)orc_xyfix_K(F);
     int64_t acc = 0;
@@ -119,7 +129,7 @@ int64_t orc_xyfix_sweep(int L, int F, double beta, uint64_t seed, uint32_t r, ui
                 int32_t kold = k[(size_t)y * L + x];
                 int64_t dE = orc_xyfix_dE(F, kold, k2, hx, hy);
                 int ok = dE <= 0;
-                if (!ok) ok = u2 < orc_xyfix_accept(F, beta, (int32_t)dE);
+                if (!ok) ok = u2 < orc_xyfix_accept(F, beta, (int32_t)dE, qp);
                 if (ok) {
                     k[(size_t)y * L + x] = k2;
                     ++acc;

@@ -3,7 +3,8 @@
 * Angle grid and trig tables against the mathematics: K = round(2 pi 2^F)
   angles, every table entry within half a unit in the last place (2^-F-1) of
   the true cos / sin, exact at 0 and quarter turns.
-* Acceptance thresholds: 60-digit floor(exp(-beta dE 2^-F) 2^32).
+* Acceptance thresholds: 60-digit floor(exp(-beta dE 2^-F) 2^32), and with
+  the probability truncated to F bits, floor(exp(-beta dE 2^-F) 2^F) 2^(32-F).
 * The fixed-point energy change against the exact energy change of the grid
   angles (computed from cos of angle differences, Eq. S1 with its sign
   corrected), within the error bound of the table and product rounding.
@@ -44,6 +45,9 @@ def test_acceptance_table_closed_form(orc, F, beta):
     for e in [1, 2, 2 ** F, 8 * 2 ** F] + list(rng.integers(1, 9 * 2 ** F, 50)):
         want = int(mpmath.floor(mpmath.exp(-mpmath.mpf(beta) * mpmath.mpf(int(e)) / 2 ** F) * 2 ** 32))
         assert oracle.xyfix_accept(F, beta, int(e)) == min(want, 2 ** 32 - 1)
+        p = mpmath.exp(-mpmath.mpf(beta) * mpmath.mpf(int(e)) / 2 ** F)
+        want_q = int(mpmath.floor(p * 2 ** F)) * 2 ** (32 - F)
+        assert oracle.xyfix_accept(F, beta, int(e), qp=True) == min(want_q, 2 ** 32 - 1)
 
 
 @pytest.mark.parametrize("F", [8, 12, 16])
