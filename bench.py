@@ -799,6 +799,91 @@ def run_quad(args):
     return 0
 
 
+def run_xy_precision(args):
+    """The paper's operand-precision trial (Tab. S3) on the GPU: the XY model at
+    T = 0.85 with spin angles in FP64, FP32 and fixed point with 16, 12 and 8
+    fractional bits (the paper's (32,16), (24,12), (16,8)), full-width random
+    words; the fixed-point types twice, with the acceptance probability at full
+    width and truncated to the angle's type.  Time per MC step at L = 32 over
+    10^4 steps (the paper's setting); internal energy per spin on a 1024^2
+    lattice from an ordered start (below the BKT temperature), blocking errors,
+    and its bias against FP64."""
+    import numpy as np
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import stats
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    beta = 1.0 / 0.85
+    stream = torch.cuda.current_stream()
+    variants = [("(64, floating)", "fp", 64, False), ("(32, floating)", "fp", 32, False)]
+    for qp in (False, True):
+        variants += [("(32, 16)", "fix", 16, qp), ("(24, 12)", "fix", 12, qp), ("(16, 8)", "fix", 8, qp)]
+
+    def make(kind, bits, qp, L, seed):
+        if kind == "fp":
+            return ising.XY(L, beta, bits, stream=stream, seed=seed)
+        return ising.XYFix(L, beta, bits, stream=stream, seed=seed, quantise_p=qp)
+
+    def timed(x, n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.sweep(n)
+        e1.record(stream)
+        e1.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / n
+
+    rows = []
+    Lb = args.precision_L
+    for i, (name, kind, bits, qp) in enumerate(variants):
+        with make(kind, bits, qp, 32, 11) as x:
+            x.sweep(2000)
+            us32 = timed(x, args.xy_steps)
+        with make(kind, bits, qp, Lb, 100 + i) as x:
+            if kind == "fp":
+                u = np.zeros((Lb, Lb, 2))
+                u[..., 0] = 1.0
+                x.set_spins(u)
+            else:
+                x.set_angles(np.zeros((Lb, Lb), dtype=np.int32))
+            x.sweep(2000)
+            us_b = timed(x, 200)
+            x.sweep(args.precision_sweeps, 1)
+            if kind == "fp":
+                E, _, _ = x.series(args.precision_sweeps)
+            else:
+                E2, _, _ = x.series(args.precision_sweeps)
+                E = -E2.astype(np.float64) / 2.0 ** (2 * bits)
+        e = E / (Lb * Lb)
+        m, err = stats.mean_and_error(e)
+        rows.append({"type": name, "probability": "truncated to the type" if qp else "32-bit",
+                     "gpu_us_per_step_L32": us32,
+                     "site_updates_per_ns_L%d" % Lb: Lb * Lb / (us_b * 1e3),
+                     "energy_per_spin": m, "error": err, "tau_int_E": stats.tau_int(e)})
+    ref, ref_err = rows[0]["energy_per_spin"], rows[0]["error"]
+    for r in rows[1:]:
+        d = r["energy_per_spin"] - ref
+        r["bias_vs_fp64"] = d
+        r["bias_sigma"] = d / float(np.hypot(r["error"], ref_err))
+        r["bias_relative"] = d / abs(ref)
+    line = {"metric": "XY operand-precision trial (the paper's Tab. S3 setting)",
+            "value": rows[4]["gpu_us_per_step_L32"], "unit": "us per MC step, (16, 8) fixed point, L=32",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "i32",
+            "config": {"workload": "2D XY model T=0.85: angles in FP64 / FP32 / fixed point F=16,12,8, "
+                                   "32-bit random words; timing at L=32, energy bias at L=%d" % Lb,
+                       "timed_steps_L32": args.xy_steps, "chain_sweeps": args.precision_sweeps,
+                       "thermalise": 2000, "start": "ordered"},
+            "variants": rows,
+            "paper_context": "FPGA at L=32: 42.36 / 42.29 / 41.82 / 41.75 / 41.68 us per step for "
+                             "(64,fl) / (32,fl) / (32,16) / (24,12) / (16,8) (Tab. S3)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     global SWEEPS_PER_STEP
     ap = argparse.ArgumentParser()
@@ -819,7 +904,9 @@ def main(argv=None):
     ap.add_argument("--xy-steps", type=int, default=10000)
     ap.add_argument("--sw-steps", type=int, default=20000)
     ap.add_argument("--quad-sweeps", type=int, default=2000)
-    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw", "quad"],
+    ap.add_argument("--precision-sweeps", type=int, default=20000)
+    ap.add_argument("--precision-L", type=int, default=1024)
+    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw", "quad", "xy_precision"],
                     default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
@@ -845,6 +932,8 @@ def main(argv=None):
         return run_sw(args)
     if args.workload == "quad":
         return run_quad(args)
+    if args.workload == "xy_precision":
+        return run_xy_precision(args)
     return run_ours(args)
 
 

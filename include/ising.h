@@ -354,6 +354,18 @@ int ising_xy_create(ising_xy** out, int L, double beta, int precision, void* str
 int ising_xy_seed(ising_xy* x, uint64_t seed);
 /* n_sweeps sweeps (async). */
 int ising_xy_sweep(ising_xy* x, int n_sweeps, int measure_every);
+/* Kernel form: 0 automatic (persistent for L <= 256), 1 one launch per half
+ * sweep, 2 persistent cooperative kernel (all CTAs co-resident, one launch per
+ * ising_xy_sweep call, a bounded grid barrier between half sweeps).  Results
+ * are identical in every mode.  If a persistent barrier gives up (after ~2 s)
+ * the next synchronising call returns ISING_ETIMEOUT until ising_xy_seed. */
+int ising_xy_set_mode(ising_xy* x, int mode);
+/* Kernels this context has launched. */
+int ising_xy_launch_count(ising_xy* x, int64_t* count);
+/* Runs the persistent kernels' grid barrier with one CTA that never arrives;
+ * *timed_out = 1 when the others gave up after timeout_s (0 < timeout_s <= 10)
+ * as they must.  The context stays usable. */
+int ising_selftest_grid_barrier(double timeout_s, int* timed_out);
 /* Last n records (oldest first): E, Mx, My (host arrays; any may be NULL). */
 int ising_xy_series(ising_xy* x, double* E, double* Mx, double* My, int n);
 /* Spins as host [L][L][2] doubles (cos, sin), row-major y*L + x. */
@@ -362,6 +374,45 @@ int ising_xy_set_spins(ising_xy* x, const double* host_uv);
 /* Accepted updates since the last seed (synchronises). */
 int ising_xy_accepted(ising_xy* x, int64_t* accepted);
 int ising_xy_destroy(ising_xy* x);
+
+/* ------------------------------------------------------------------------
+ * Fixed-point XY model for the operand-precision study (Supplementary
+ * "Operand bit width optimization trial", Tab. S3): spin angles are fixed-point
+ * numbers with F = frac_bits fractional bits (the paper's (m, n) types with
+ * m - n = F), random words keep 32 bits, all arithmetic is integer.  Angle
+ * grid k 2^-F, k in [0, K), K = round(2 pi 2^F); C[k], S[k] = cos, sin of the
+ * grid angle rounded to F fractional bits (nearest, ties up); per site of colour
+ * c (even x + y first): (hx, hy) = sum of the four neighbours' (C, S);
+ * k' = floor(u1 K / 2^32); dE = -round(((C[k'] - C[k]) hx + (S[k'] - S[k]) hy)
+ * / 2^F); accept iff dE <= 0 or u2 < floor(exp(-beta dE 2^-F) 2^32).  Words:
+ * start k = floor(w K / 2^32), w = word (n & 3) of Philox(n >> 2, 0, 0,
+ * XYFIX_INIT << 16), n = y L + x; sweep t: Philox(j >> 1, t, 0, XYFIX_MET << 16
+ * | c << 8), j = y (L/2) + (x >> 1), words 2 (j & 1) and 2 (j & 1) + 1 = u1, u2.
+ * Records: E2 = sum over bonds of C C' + S S' (energy -E2 2^-2F), Mx = sum C,
+ * My = sum S (scale 2^-F).  L even in [2, 32768], frac_bits in [6, 16].
+ * flags: ISING_XYFIX_QUANTISE_P holds the acceptance probability in the same
+ * fixed-point type too, truncated to F fractional bits: the threshold becomes
+ * floor(exp(-beta dE 2^-F) 2^F) 2^(32-F) (clamped to 2^32 - 1).
+ * ------------------------------------------------------------------------ */
+enum { ISING_XYFIX_QUANTISE_P = 1 };
+typedef struct ising_xyfix ising_xyfix;
+int ising_xyfix_create(ising_xyfix** out, int L, double beta, int frac_bits, int flags,
+                       void* cuda_stream);
+/* Seeded random start; sweep counter 0; clears records and the accepted count. */
+int ising_xyfix_seed(ising_xyfix* x, uint64_t seed);
+/* n_sweeps sweeps (async). */
+int ising_xyfix_sweep(ising_xyfix* x, int n_sweeps, int measure_every);
+/* Kernel form, as ising_xy_set_mode. */
+int ising_xyfix_set_mode(ising_xyfix* x, int mode);
+/* Last n records, oldest first (host arrays; any may be NULL).  Synchronises. */
+int ising_xyfix_series(ising_xyfix* x, int64_t* E2, int64_t* Mx, int64_t* My, int n);
+/* Angle indices as host int32 [L][L], row-major y*L + x.  Synchronise; set
+ * rejects indices outside [0, K) with ISING_EINVAL. */
+int ising_xyfix_get_angles(ising_xyfix* x, int32_t* host_k);
+int ising_xyfix_set_angles(ising_xyfix* x, const int32_t* host_k);
+/* K, accepted moves since seeding, kernels launched (any may be NULL). */
+int ising_xyfix_info(ising_xyfix* x, int64_t* K, int64_t* accepted, int64_t* launches);
+int ising_xyfix_destroy(ising_xyfix* x);
 
 /* ------------------------------------------------------------------------
  * Ising model on lattices with a four-site unit cell, swept by sublattice

@@ -115,6 +115,18 @@ _PROTOS = [
     ("ising_xy_set_spins", _i, [_p, _p]),
     ("ising_xy_accepted", _i, [_p, _p]),
     ("ising_xy_destroy", _i, [_p]),
+    ("ising_xy_set_mode", _i, [_p, _i]),
+    ("ising_xy_launch_count", _i, [_p, _p]),
+    ("ising_selftest_grid_barrier", _i, [_d, _p]),
+    ("ising_xyfix_set_mode", _i, [_p, _i]),
+    ("ising_xyfix_create", _i, [ctypes.POINTER(_p), _i, _d, _i, _i, _p]),
+    ("ising_xyfix_seed", _i, [_p, _u64]),
+    ("ising_xyfix_sweep", _i, [_p, _i, _i]),
+    ("ising_xyfix_series", _i, [_p, _p, _p, _p, _i]),
+    ("ising_xyfix_get_angles", _i, [_p, _p]),
+    ("ising_xyfix_set_angles", _i, [_p, _p]),
+    ("ising_xyfix_info", _i, [_p, _p, _p, _p]),
+    ("ising_xyfix_destroy", _i, [_p]),
     ("ising_quad_create", _i, [ctypes.POINTER(_p), _i, _i, _d, _d, _d, _p]),
     ("ising_quad_seed", _i, [_p, _u64]),
     ("ising_quad_set_replica", _i, [_p, ctypes.c_uint32]),
@@ -706,6 +718,94 @@ class XY:
         a = ctypes.c_int64()
         _check(lib().ising_xy_accepted(self.h, ctypes.byref(a)))
         return int(a.value)
+
+    def set_mode(self, mode: int):
+        """0 automatic, 1 one launch per half sweep, 2 persistent kernel."""
+        _check(lib().ising_xy_set_mode(self.h, int(mode)))
+
+    def launch_count(self) -> int:
+        c = ctypes.c_int64()
+        _check(lib().ising_xy_launch_count(self.h, ctypes.byref(c)))
+        return int(c.value)
+
+
+def ising_selftest_grid_barrier(timeout_s: float) -> int:
+    """1 if the persistent kernels' grid barrier timed out as designed."""
+    st = ctypes.c_int()
+    _check(lib().ising_selftest_grid_barrier(float(timeout_s), ctypes.byref(st)))
+    return int(st.value)
+
+
+# ---------------------------------------------------------------------------
+# fixed-point XY model (operand-precision study)
+# ---------------------------------------------------------------------------
+
+ISING_XYFIX_QUANTISE_P = 1
+
+
+class XYFix:
+    """Owning wrapper of an ising_xyfix context (angles with F fractional bits)."""
+
+    def __init__(self, L: int, beta: float, frac_bits: int, stream=None, seed=None,
+                 quantise_p: bool = False):
+        self.L = int(L)
+        self.F = int(frac_bits)
+        out = ctypes.c_void_p()
+        _check(lib().ising_xyfix_create(ctypes.byref(out), self.L, float(beta), self.F,
+                                        ISING_XYFIX_QUANTISE_P if quantise_p else 0,
+                                        _stream_ptr(stream)))
+        self.h = out.value
+        if seed is not None:
+            self.seed(seed)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().ising_xyfix_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seed(self, seed: int):
+        _check(lib().ising_xyfix_seed(self.h, int(seed)))
+
+    def sweep(self, n: int, measure_every: int = 0):
+        _check(lib().ising_xyfix_sweep(self.h, int(n), int(measure_every)))
+
+    def series(self, n: int):
+        """(E2, Mx, My) integers of the last n records: energy = -E2 2^-2F."""
+        E2, Mx, My = (np.zeros(max(n, 1), dtype=np.int64) for _ in range(3))
+        _check(lib().ising_xyfix_series(self.h, _ptr(E2), _ptr(Mx), _ptr(My), int(n)))
+        return E2[:n], Mx[:n], My[:n]
+
+    def angles(self) -> np.ndarray:
+        k = np.zeros((self.L, self.L), dtype=np.int32)
+        _check(lib().ising_xyfix_get_angles(self.h, _ptr(k)))
+        return k
+
+    def set_angles(self, k: np.ndarray):
+        v = np.ascontiguousarray(k, dtype=np.int32)
+        if v.shape != (self.L, self.L):
+            raise ValueError("angles must have shape (L, L)")
+        _check(lib().ising_xyfix_set_angles(self.h, _ptr(v)))
+
+    def set_mode(self, mode: int):
+        """0 automatic, 1 one launch per half sweep, 2 persistent kernel."""
+        _check(lib().ising_xyfix_set_mode(self.h, int(mode)))
+
+    def info(self):
+        K, a, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ising_xyfix_info(self.h, ctypes.byref(K), ctypes.byref(a), ctypes.byref(n)))
+        return {"K": int(K.value), "accepted": int(a.value), "launches": int(n.value)}
 
 
 # ---------------------------------------------------------------------------

@@ -153,6 +153,55 @@ __device__ __forceinline__ bool bounded_wait_while_eq(const volatile unsigned in
   return true;
 }
 
+// Grid-wide barrier for persistent cooperative kernels (all CTAs co-resident):
+// generation counter + arrival count in global memory, a tight bounded spin
+// (clock64 budget `limit`).  On time-out it records 1 in ctl->status; every
+// thread of the CTA gets the same answer (read once into shared memory).
+struct GridCtl {
+  unsigned int count;
+  unsigned int gen;
+  int status;
+  int pad;
+};
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrival is an acq_rel atomic (it publishes, cumulatively, every write the CTA
+// made before the __syncthreads); waiting is an acquire load of the
+// generation, so no separate fences are needed.
+__device__ __forceinline__ bool grid_sync_bounded(GridCtl* ctl, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g = ld_acquire_gpu(&ctl->gen);
+    if (atom_add_acq_rel_gpu(&ctl->count, 1u) == gridDim.x - 1) {
+      ctl->count = 0u;  // ordered before the release below; nobody arrives again until it
+      atom_add_acq_rel_gpu(&ctl->gen, 1u);
+    } else {
+      const long long start = clock64();
+      while (ld_acquire_gpu(&ctl->gen) == g) {
+        if (clock64() - start > limit) {
+          atomicExch(&ctl->status, 1);
+          break;
+        }
+      }
+    }
+    s_ok = ld_acquire_gpu((const unsigned int*)&ctl->status) == 0u;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -14,6 +14,7 @@
 //
 // Layout: two colour planes of [L][L/2] vectors (T2 = float2 or double2);
 // site (x, y) of colour c = (x + y) & 1 is element y (L/2) + (x >> 1) of plane c.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -180,68 +181,98 @@ __global__ void k_xy_init(typename Vec<T>::type* __restrict__ u, int L, RngParam
   }
 }
 
+// Loads and stores of the state: plain in the one-launch-per-half-sweep
+// kernels; through L2 only (no L1) in the persistent kernel, whose CTAs read
+// what other SMs wrote after a grid barrier.
+template <bool CG, typename V>
+__device__ __forceinline__ V ld_state(const V* p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+template <bool CG, typename V>
+__device__ __forceinline__ void st_state(V* p, V v) {
+  if (CG) __stcg(p, v);
+  else *p = v;
+}
+
+// Metropolis trials of the two colour-compact sites k = 2b, 2b + 1 of colour
+// c (one Philox block); returns how many were accepted.
+template <typename T, bool CG>
+__device__ __forceinline__ unsigned int xy_pair(typename Vec<T>::type* __restrict__ own,
+                                                const typename Vec<T>::type* __restrict__ oth, int L,
+                                                long long nk, long long b, int c, uint32_t t, T beta,
+                                                const RngParams& rng) {
+  using V = typename Vec<T>::type;
+  const int half = L / 2;
+  unsigned int acc = 0;
+  const uint4 r = philox10_rk(make_uint4((uint32_t)b, t, rng.replica, (kTagXYMet << 16) | ((uint32_t)c << 8)),
+                              rng.rk0, rng.rk1);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const long long k = 2 * b + h;
+    if (k >= nk) break;
+    const int y = (int)(k / half), j = (int)(k - (k / half) * half);
+    const int o = (y + c) & 1;  // x = 2 j + o
+    const int jr = o == 0 ? j : (j + 1 == half ? 0 : j + 1);   // x + 1
+    const int jl = o == 0 ? (j == 0 ? half - 1 : j - 1) : j;   // x - 1
+    const int yd = y + 1 == L ? 0 : y + 1, yu = y == 0 ? L - 1 : y - 1;
+    const V a = ld_state<CG>(oth + (size_t)y * half + jr);
+    const V bl = ld_state<CG>(oth + (size_t)y * half + jl);
+    const V d = ld_state<CG>(oth + (size_t)yd * half + j);
+    const V e = ld_state<CG>(oth + (size_t)yu * half + j);
+    T hx = add_rn<T>(a.x, bl.x);
+    hx = add_rn<T>(hx, d.x);
+    hx = add_rn<T>(hx, e.x);
+    T hy = add_rn<T>(a.y, bl.y);
+    hy = add_rn<T>(hy, d.y);
+    hy = add_rn<T>(hy, e.y);
+    const uint32_t w1 = h == 0 ? r.x : r.z, w2 = h == 0 ? r.y : r.w;
+    T sn, cs;
+    own_sincos(angle_of<T>(w1), sn, cs);
+    const T p = mul_rn<T>((T)(w2 >> 8), inv24<T>());
+    V me = ld_state<CG>(own + k);
+    const T dE = -fma(sub_rn<T>(cs, me.x), hx, mul_rn<T>(sub_rn<T>(sn, me.y), hy));
+    if (dE <= (T)0 || p < own_exp(mul_rn<T>(-beta, dE))) {
+      me.x = cs;
+      me.y = sn;
+      st_state<CG>(own + k, me);
+      ++acc;
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void add_accepted(unsigned long long* accepted, unsigned int acc) {
+  if (!accepted) return;
+  unsigned int s = acc;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(accepted, (unsigned long long)s);
+}
+
 // One half sweep of colour c: thread = one Philox block = colour-compact sites
 // k = 2b and 2b + 1.
 template <typename T>
 __global__ void __launch_bounds__(256) k_xy_half(typename Vec<T>::type* __restrict__ u, int L,
                                                  int c, uint32_t t, T beta, RngParams rng,
                                                  unsigned long long* __restrict__ accepted) {
-  using V = typename Vec<T>::type;
   const int half = L / 2;
   const long long nk = (long long)L * half;
-  V* own = u + (size_t)c * L * half;
-  const V* oth = u + (size_t)(1 - c) * L * half;
+  typename Vec<T>::type* own = u + (size_t)c * L * half;
+  const typename Vec<T>::type* oth = u + (size_t)(1 - c) * L * half;
   unsigned int acc = 0;
   for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * b < nk;
-       b += (long long)gridDim.x * blockDim.x) {
-    const uint4 r = philox10_rk(make_uint4((uint32_t)b, t, rng.replica, (kTagXYMet << 16) | ((uint32_t)c << 8)),
-                                rng.rk0, rng.rk1);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const long long k = 2 * b + h;
-      if (k >= nk) break;
-      const int y = (int)(k / half), j = (int)(k - (k / half) * half);
-      const int o = (y + c) & 1;  // x = 2 j + o
-      const int jr = o == 0 ? j : (j + 1 == half ? 0 : j + 1);   // x + 1
-      const int jl = o == 0 ? (j == 0 ? half - 1 : j - 1) : j;   // x - 1
-      const int yd = y + 1 == L ? 0 : y + 1, yu = y == 0 ? L - 1 : y - 1;
-      const V a = oth[(size_t)y * half + jr];
-      const V bl = oth[(size_t)y * half + jl];
-      const V d = oth[(size_t)yd * half + j];
-      const V e = oth[(size_t)yu * half + j];
-      T hx = add_rn<T>(a.x, bl.x);
-      hx = add_rn<T>(hx, d.x);
-      hx = add_rn<T>(hx, e.x);
-      T hy = add_rn<T>(a.y, bl.y);
-      hy = add_rn<T>(hy, d.y);
-      hy = add_rn<T>(hy, e.y);
-      const uint32_t w1 = h == 0 ? r.x : r.z, w2 = h == 0 ? r.y : r.w;
-      T sn, cs;
-      own_sincos(angle_of<T>(w1), sn, cs);
-      const T p = mul_rn<T>((T)(w2 >> 8), inv24<T>());
-      V me = own[k];
-      const T dE = -fma(sub_rn<T>(cs, me.x), hx, mul_rn<T>(sub_rn<T>(sn, me.y), hy));
-      if (dE <= (T)0 || p < own_exp(mul_rn<T>(-beta, dE))) {
-        me.x = cs;
-        me.y = sn;
-        own[k] = me;
-        ++acc;
-      }
-    }
-  }
-  if (accepted) {
-    unsigned int s = acc;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(accepted, (unsigned long long)s);
-  }
+       b += (long long)gridDim.x * blockDim.x)
+    acc += xy_pair<T, false>(own, oth, L, nk, b, c, t, beta, rng);
+  add_accepted(accepted, acc);
 }
 
 // E = -sum over colour-0 sites of u . (sum of its four neighbours) (every bond
-// once), M = sum u; accumulated in double.
-template <typename T>
-__global__ void __launch_bounds__(256) k_xy_measure(const typename Vec<T>::type* __restrict__ u,
-                                                    int L, double* __restrict__ out3) {
+// once), M = sum u; per-thread partials over a grid-stride range, accumulated
+// in double and added to out3 by one atomic per warp.
+template <typename T, bool CG>
+__device__ __forceinline__ void xy_measure_part(const typename Vec<T>::type* __restrict__ u, int L,
+                                                double* __restrict__ out3) {
   using V = typename Vec<T>::type;
   const int half = L / 2;
   const long long nk = (long long)L * half;
@@ -255,13 +286,14 @@ __global__ void __launch_bounds__(256) k_xy_measure(const typename Vec<T>::type*
     const int jr = o == 0 ? j : (j + 1 == half ? 0 : j + 1);
     const int jl = o == 0 ? (j == 0 ? half - 1 : j - 1) : j;
     const int yd = y + 1 == L ? 0 : y + 1, yu = y == 0 ? L - 1 : y - 1;
-    const V s = p0[k];
-    const V a = p1[(size_t)y * half + jr], b = p1[(size_t)y * half + jl];
-    const V d = p1[(size_t)yd * half + j], f = p1[(size_t)yu * half + j];
+    const V s = ld_state<CG>(p0 + k);
+    const V a = ld_state<CG>(p1 + (size_t)y * half + jr), b = ld_state<CG>(p1 + (size_t)y * half + jl);
+    const V d = ld_state<CG>(p1 + (size_t)yd * half + j), f = ld_state<CG>(p1 + (size_t)yu * half + j);
     const double hx = (double)a.x + b.x + d.x + f.x, hy = (double)a.y + b.y + d.y + f.y;
     e -= (double)s.x * hx + (double)s.y * hy;
-    mx += (double)s.x + (double)p1[k].x;
-    my += (double)s.y + (double)p1[k].y;
+    const V s1 = ld_state<CG>(p1 + k);
+    mx += (double)s.x + (double)s1.x;
+    my += (double)s.y + (double)s1.y;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -274,6 +306,72 @@ __global__ void __launch_bounds__(256) k_xy_measure(const typename Vec<T>::type*
     atomicAdd(&out3[1], mx);
     atomicAdd(&out3[2], my);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_xy_measure(const typename Vec<T>::type* __restrict__ u,
+                                                    int L, double* __restrict__ out3) {
+  xy_measure_part<T, false>(u, L, out3);
+}
+
+// Persistent form for small lattices: n sweeps (from sweep t0) in one launch,
+// a barrier after each half sweep and each measurement.  PM = kOneCTA: one
+// CTA, __syncthreads(), state through L1; kCluster: one thread-block cluster,
+// the hardware cluster barrier (release / acquire), state through L2;
+// kGrid: a cooperative grid (every CTA co-resident), the bounded grid barrier,
+// state through L2.  Records go to ring slots rec0, rec0 + 1, ...; each slot is
+// zeroed by CTA 0 in the half sweep before it is filled.
+enum PersistMode { kOneCTA = 0, kCluster = 1, kGrid = 2 };
+
+template <int PM>
+__device__ __forceinline__ bool persist_sync(GridCtl* ctl, long long limit) {
+  if (PM == kGrid) return grid_sync_bounded(ctl, limit);
+  if (PM == kCluster) cooperative_groups::this_cluster().sync();
+  else __syncthreads();
+  return true;
+}
+
+template <typename T, int PM>
+__global__ void __launch_bounds__(PM == kGrid ? 256 : 1024) k_xy_persist(typename Vec<T>::type* __restrict__ u, int L,
+                                                    T beta, RngParams rng, uint32_t t0, int n, int m,
+                                                    double* __restrict__ rec, long long rec0,
+                                                    long long rec_cap,
+                                                    unsigned long long* __restrict__ accepted,
+                                                    GridCtl* ctl, long long limit) {
+  using V = typename Vec<T>::type;
+  const int half = L / 2;
+  const long long nk = (long long)L * half;
+  unsigned int acc = 0;
+  long long ri = rec0;
+  for (int s = 0; s < n; ++s) {
+    const uint32_t t = t0 + (uint32_t)s;
+    const bool meas = m > 0 && ((long long)t + 1) % m == 0;
+    double* slot = rec + 3 * (ri % rec_cap);
+    bool ok = true;
+    for (int c = 0; c < 2 && ok; ++c) {
+      V* own = u + (size_t)c * L * half;
+      const V* oth = u + (size_t)(1 - c) * L * half;
+      for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * b < nk;
+           b += (long long)gridDim.x * blockDim.x)
+        acc += xy_pair<T, PM != kOneCTA>(own, oth, L, nk, b, c, t, beta, rng);
+      if (meas && c == 1 && blockIdx.x == 0 && threadIdx.x == 0) slot[0] = slot[1] = slot[2] = 0.0;
+      ok = persist_sync<PM>(ctl, limit);
+    }
+    if (ok && meas) {
+      xy_measure_part<T, PM != kOneCTA>(u, L, slot);
+      ++ri;
+      ok = persist_sync<PM>(ctl, limit);
+    }
+    if (!ok) break;
+  }
+  add_accepted(accepted, acc);
+}
+
+// Self-test of the persistent kernels' barrier: CTA 0 never arrives, so every
+// other CTA must give up after `limit` cycles and record the time-out.
+__global__ void k_grid_barrier_selftest(GridCtl* ctl, long long limit) {
+  if (blockIdx.x == 0) return;
+  grid_sync_bounded(ctl, limit);
 }
 
 template <typename T>
@@ -328,6 +426,9 @@ using namespace ising;
 
 struct ising_xy {
   int L = 0, precision = 64;
+  int mode = 0;                      // 0 auto, 1 one launch per half sweep, 2 persistent
+  GridCtl* ctl = nullptr;            // persistent-kernel barrier and status
+  int64_t launches = 0;
   double beta = 0;
   uint64_t seed = 0;
   int64_t sweep = 0;
@@ -342,8 +443,84 @@ struct ising_xy {
 namespace {
 constexpr int64_t kXYRec = 65536;
 
+// Largest L for which the automatic mode runs the persistent kernel.
+constexpr int kXYPersistMaxL = 256;
+constexpr long long kXYSpinLimit = 4000000000LL;  // ~2 s of SM clock per barrier
+
+template <typename T>
+cudaError_t xy_persist_t(ising_xy* x, int n, int m) {
+  using V = typename Vec<T>::type;
+  const RngParams rng = make_rng(x->seed, 0, 0, 0);
+  const long long pairs = ((long long)x->L * (x->L / 2) + 1) / 2;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e) return e;
+  // FP32: one CTA up to 256 site pairs, one cluster of 8 CTAs up to 8192;
+  // FP64, which runs at a small fraction of the FP32 rate on this part: one CTA
+  // only up to 32 pairs.  Beyond, a cooperative grid spreading the pairs over
+  // the SMs (32 threads per CTA in FP64, 64 in FP32).
+  const bool fp64 = sizeof(T) == 8;
+  const int pm = pairs <= (fp64 ? 32 : 256) ? kOneCTA : (!fp64 && pairs <= 8192 ? kCluster : kGrid);
+  int threads;
+  long long grid;
+  const void* fn;
+  if (pm == kOneCTA) {
+    threads = (int)(((pairs + 31) / 32) * 32);
+    grid = 1;
+    fn = (const void*)k_xy_persist<T, kOneCTA>;
+  } else if (pm == kCluster) {
+    threads = (int)std::min<long long>(1024, ((pairs + 8 * 32 - 1) / (8 * 32)) * 32);
+    grid = 8;
+    fn = (const void*)k_xy_persist<T, kCluster>;
+  } else {
+    threads = fp64 ? 32 : 64;
+    grid = std::max(1LL, std::min((pairs + threads - 1) / threads, (long long)sms));
+    fn = (const void*)k_xy_persist<T, kGrid>;
+    e = cudaMemsetAsync(&x->ctl->count, 0, sizeof(unsigned int), x->stream);
+    if (e) return e;
+  }
+  V* u = (V*)x->u;
+  int L = x->L;
+  T beta = (T)x->beta;
+  uint32_t t0 = (uint32_t)x->sweep;
+  long long rec0 = x->rec_count, cap = kXYRec, limit = kXYSpinLimit;
+  double* rec = x->rec;
+  unsigned long long* acc = x->accepted;
+  GridCtl* ctl = x->ctl;
+  RngParams r = rng;
+  void* args[] = {&u, &L, &beta, &r, &t0, &n, &m, &rec, &rec0, &cap, &acc, &ctl, &limit};
+  if (pm == kOneCTA) {
+    e = cudaLaunchKernel(fn, dim3(1), dim3(threads), args, 0, x->stream);
+  } else if (pm == kCluster) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(threads);
+    cfg.stream = x->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)grid;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, fn, args);
+  } else {
+    e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(threads), args, 0, x->stream);
+  }
+  if (e) return e;
+  ++x->launches;
+  if (m > 0) {
+    for (int s = 0; s < n; ++s)
+      if (((int64_t)x->sweep + s + 1) % m == 0) ++x->rec_count;
+  }
+  return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t xy_sweep_t(ising_xy* x, int n, int m) {
+  const bool persist = x->mode == 2 || (x->mode == 0 && x->L <= kXYPersistMaxL);
+  if (persist) return n > 0 ? xy_persist_t<T>(x, n, m) : cudaSuccess;
   const RngParams rng = make_rng(x->seed, 0, 0, 0);
   const long long blocks = ((long long)x->L * (x->L / 2) + 1) / 2;
   using V = typename Vec<T>::type;
@@ -354,6 +531,7 @@ cudaError_t xy_sweep_t(ising_xy* x, int n, int m) {
                                                             x->accepted);
       cudaError_t e = cudaGetLastError();
       if (e) return e;
+      ++x->launches;
     }
     if (m > 0 && ((int64_t)t + 1) % m == 0) {
       double* slot = x->rec + 3 * (x->rec_count % kXYRec);
@@ -363,6 +541,7 @@ cudaError_t xy_sweep_t(ising_xy* x, int n, int m) {
                                                                                  x->L, slot);
       e = cudaGetLastError();
       if (e) return e;
+      ++x->launches;
       ++x->rec_count;
     }
   }
@@ -389,11 +568,14 @@ int ising_xy_create(ising_xy** out, int L, double beta, int precision, void* str
   if (!e) e = cudaMalloc((void**)&x->rec, kXYRec * 3 * sizeof(double));
   if (!e) e = cudaMalloc((void**)&x->accepted, sizeof(unsigned long long));
   if (!e) e = cudaMemset(x->accepted, 0, sizeof(unsigned long long));
+  if (!e) e = cudaMalloc((void**)&x->ctl, sizeof(GridCtl));
+  if (!e) e = cudaMemset(x->ctl, 0, sizeof(GridCtl));
   if (e) {
     cudaGetLastError();
     cudaFree(x->u);
     cudaFree(x->rec);
     cudaFree(x->accepted);
+    cudaFree(x->ctl);
     delete x;
     return xfail(ISING_ENOMEM, "XY allocation: %s", cudaGetErrorString(e));
   }
@@ -414,6 +596,7 @@ int ising_xy_seed(ising_xy* x, uint64_t seed) {
     k_xy_init<float><<<grid_of(N), 256, 0, x->stream>>>((float2*)x->u, x->L, rng);
   XTRY(cudaGetLastError());
   XTRY(cudaMemsetAsync(x->accepted, 0, sizeof(unsigned long long), x->stream));
+  XTRY(cudaMemsetAsync(x->ctl, 0, sizeof(GridCtl), x->stream));
   set_last_error("");
   return ISING_OK;
 }
@@ -430,12 +613,57 @@ int ising_xy_sweep(ising_xy* x, int n_sweeps, int measure_every) {
   return ISING_OK;
 }
 
+// After a synchronising call: ETIMEOUT if a persistent kernel's grid barrier
+// gave up (the flag stays set until the next seed).
+static int xy_status(ising_xy* x) {
+  int st = 0;
+  XTRY(cudaMemcpy(&st, &x->ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) return xfail(ISING_ETIMEOUT, "grid barrier timed out in the persistent XY kernel");
+  return ISING_OK;
+}
+
+int ising_selftest_grid_barrier(double timeout_s, int* timed_out) {
+  if (!timed_out || !(timeout_s > 0) || timeout_s > 10) return xfail(ISING_EINVAL, "bad arguments");
+  GridCtl* ctl = nullptr;
+  XTRY(cudaMalloc((void**)&ctl, sizeof(GridCtl)));
+  cudaError_t e = cudaMemset(ctl, 0, sizeof(GridCtl));
+  if (!e) {
+    GridCtl* c = ctl;
+    long long limit = (long long)(timeout_s * 2.1e9);  // SM clock cycles (<= 2.1 GHz)
+    void* args[] = {&c, &limit};
+    e = cudaLaunchCooperativeKernel((const void*)k_grid_barrier_selftest, dim3(4), dim3(32), args, 0, 0);
+  }
+  if (!e) e = cudaDeviceSynchronize();
+  GridCtl h{};
+  if (!e) e = cudaMemcpy(&h, ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost);
+  cudaFree(ctl);
+  if (e) return xfail(ISING_ECUDA, "barrier self-test: %s", cudaGetErrorString(e));
+  *timed_out = h.status;
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_xy_set_mode(ising_xy* x, int mode) {
+  if (!x) return xfail(ISING_EINVAL, "null context");
+  if (mode < 0 || mode > 2) return xfail(ISING_EINVAL, "mode must be 0 (auto), 1 (per half sweep) or 2 (persistent)");
+  x->mode = mode;
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_xy_launch_count(ising_xy* x, int64_t* count) {
+  if (!x || !count) return xfail(ISING_EINVAL, "null argument");
+  *count = x->launches;
+  return ISING_OK;
+}
+
 int ising_xy_series(ising_xy* x, double* E, double* Mx, double* My, int n) {
   if (!x) return xfail(ISING_EINVAL, "null context");
   if (n < 0 || n > std::min<int64_t>(x->rec_count, kXYRec)) return xfail(ISING_EINVAL, "n exceeds records");
   std::vector<double> h((size_t)3 * kXYRec);
   XTRY(cudaMemcpyAsync(h.data(), x->rec, h.size() * 8, cudaMemcpyDeviceToHost, x->stream));
   XTRY(cudaStreamSynchronize(x->stream));
+  if (int st = xy_status(x)) return st;
   for (int i = 0; i < n; ++i) {
     const int64_t slot = (x->rec_count - n + i) % kXYRec;
     if (E) E[i] = h[3 * slot];
@@ -460,6 +688,7 @@ int ising_xy_get_spins(ising_xy* x, double* host_uv) {
   if (!e) e = cudaStreamSynchronize(x->stream);
   cudaFree(d);
   if (e) return xfail(ISING_ECUDA, "get spins: %s", cudaGetErrorString(e));
+  if (int st = xy_status(x)) return st;
   set_last_error("");
   return ISING_OK;
 }
@@ -489,6 +718,7 @@ int ising_xy_accepted(ising_xy* x, int64_t* accepted) {
   unsigned long long h = 0;
   XTRY(cudaMemcpyAsync(&h, x->accepted, 8, cudaMemcpyDeviceToHost, x->stream));
   XTRY(cudaStreamSynchronize(x->stream));
+  if (int st = xy_status(x)) return st;
   *accepted = (int64_t)h;
   set_last_error("");
   return ISING_OK;
@@ -500,6 +730,7 @@ int ising_xy_destroy(ising_xy* x) {
   cudaFree(x->u);
   cudaFree(x->rec);
   cudaFree(x->accepted);
+  cudaFree(x->ctl);
   delete x;
   return ISING_OK;
 }

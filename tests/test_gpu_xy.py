@@ -79,3 +79,32 @@ def test_xy_rejects_bad_arguments():
         ising.XY(8, 1.0, precision=16)
     with pytest.raises(ising.IsingError):
         ising.XY(8, -1.0)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("L", [4, 32, 64, 130, 512])
+def test_xy_kernel_modes_bit_exact(precision, mode, L):
+    """One launch per half sweep (mode 1) and the persistent cooperative kernel
+    (mode 2) give the oracle's spins, acceptances and records."""
+    beta, seed, n = 1.0 / T_PAPER, 31 + L, 9
+    u = oracle.xy_init(L, seed, precision=precision)
+    acc, E_ref = oracle.xy_sweep(u, beta, seed, n)
+    with ising.XY(L, beta, precision, seed=seed) as x:
+        x.set_mode(mode)
+        x.sweep(4, 2)
+        x.sweep(5, 1)
+        got = x.spins()
+        E, _, _ = x.series(5)
+        assert x.accepted() == int(acc.sum())
+        launches = x.launch_count()
+    assert np.array_equal(got, u.astype(np.float64))
+    np.testing.assert_allclose(E, E_ref[4:], rtol=1e-12 if precision == 64 else 1e-9, atol=1e-9)
+    assert launches == (2 if mode == 2 else 2 * n + 2 + 5)
+
+
+def test_grid_barrier_times_out_and_context_survives():
+    assert ising.ising_selftest_grid_barrier(0.05) == 1
+    with ising.XY(16, 1.0, 32, seed=1) as x:
+        x.sweep(3)
+        assert x.spins().shape == (16, 16, 2)
