@@ -828,7 +828,7 @@ int ising_sw_step(ising_ctx* c, int n_steps, int measure_every) {
     cudaError_t e = launch_sw_step(c->lat(c->cur), (uint32_t)t, thr, rng, c->sw_parent, c->sw_flip,
                                    c->stream);
     if (int st = launch_result(c, e, "cluster step")) return st;
-    c->launches += 3;
+    c->launches += 4;  // four kernels per cluster step
     if (measure_every > 0 && (t + 1) % measure_every == 0) {
       const int64_t slot = c->rec_count % kRecCap;
       if (int st = zero_records(c, c->rec_count, 1)) return st;

@@ -7,7 +7,10 @@
 //   2. clusters = connected components of the active bonds, found by a lock-free
 //      union-find whose links always point from the larger to the smaller site
 //      index, so each cluster's root is its smallest site whatever the order in
-//      which threads link;
+//      which threads link.  When L >= 2048 is a multiple of the 128 x 64 tile, each CTA
+//      first labels its tile's inner bonds in shared memory (k_sw_local) and
+//      only the bonds crossing tile edges go through the global forest
+//      (k_sw_edges); otherwise every bond does (k_sw_bonds);
 //   3. each cluster flips iff bit 31 of word (m & 3) of
 //      Philox(m >> 2, step, replica, SW_FLIP << 16), m = its root.
 // The outcome depends only on (seed, step, replica, spins): bit-identical to
@@ -140,6 +143,210 @@ __global__ void k_sw_apply(uint32_t* __restrict__ planes, int L, int Wc,
   }
 }
 
+// ---- two-level labelling: union-find inside a TX x TY tile in shared memory,
+// then only the bonds that cross tile edges in global memory ----
+constexpr int kTileX = 128, kTileY = 64, kTileSites = kTileX * kTileY, kTileThreads = 512;
+
+__device__ __forceinline__ uint32_t sfind(volatile uint32_t* lab, uint32_t a) {
+  while (true) {
+    const uint32_t p = lab[a];
+    if (p == a) return a;
+    const uint32_t gp = lab[p];
+    if (gp != p) lab[a] = gp;  // an ancestor: stays in a's set
+    a = gp;
+  }
+}
+
+__device__ __forceinline__ void sunite(uint32_t* lab, uint32_t a, uint32_t b) {
+  while (true) {
+    a = sfind(lab, a);
+    b = sfind(lab, b);
+    if (a == b) return;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    const uint32_t old = atomicCAS(&lab[a], a, b);
+    if (old == a) return;
+    a = old;
+  }
+}
+
+// One CTA per tile: spins in, local clusters of the tile's inner bonds, and
+// parent[site] = global index of its local root (the smallest global index of
+// the local cluster: inside a tile local and global order agree); mark[site] = 2
+// for local roots, 0 otherwise.  Labelling: horizontal runs first (each site
+// labelled with the start of its run by a warp max-scan, no atomics), then the
+// vertical bonds unite runs (skipping a bond whose left neighbour already joined
+// the same two runs), then every label is resolved to its root.
+__global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __restrict__ planes, int L, int Wc,
+                                                           uint32_t step, uint32_t thr, RngParams rng,
+                                                           uint32_t* __restrict__ parent,
+                                                           uint8_t* __restrict__ mark) {
+  __shared__ uint32_t lab[kTileSites];
+  // per site: bit 0 spin, bit 1 bond li -> li + 1 active, bit 2 bond li -> li + TX
+  // active (bonds inside the tile only)
+  __shared__ uint8_t st[kTileSites];
+  const int tiles_x = L / kTileX;
+  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+  const int x0 = tx * kTileX, y0 = ty * kTileY;
+  // spins: each thread unpacks whole words (TX / 64 words per colour per row)
+  constexpr int kWordsRow = kTileX / 64;
+  for (int i = threadIdx.x; i < 2 * kTileY * kWordsRow; i += blockDim.x) {
+    const int c = i / (kTileY * kWordsRow), rem = i - c * (kTileY * kWordsRow);
+    const int ly = rem / kWordsRow, wi = rem - ly * kWordsRow;
+    const int y = y0 + ly;
+    const uint32_t w = __ldg(&planes[(size_t)c * L * Wc + (size_t)y * Wc + (x0 >> 6) + wi]);
+    const int o = (y + c) & 1;  // x = 2 j + o
+#pragma unroll 4
+    for (int b = 0; b < 32; ++b) st[ly * kTileX + 2 * (32 * wi + b) + o] = (uint8_t)((w >> b) & 1u);
+  }
+  __syncthreads();
+  // inner bonds: one thread per site pair (one Philox block for its four bonds)
+  for (int pp = threadIdx.x; pp < kTileSites / 2; pp += blockDim.x) {
+    const int ly = pp / (kTileX / 2), lx0 = 2 * (pp - ly * (kTileX / 2));
+    const long long a0 = (long long)(y0 + ly) * L + x0 + lx0;
+    const uint4 r = philox10_rk(make_uint4((uint32_t)(a0 >> 1), step, rng.replica, kTagSWBond << 16),
+                                rng.rk0, rng.rk1);
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      // other threads rewrite only the bond bits of their own sites: spin bits read here are stable
+      const int lx = lx0 + h, li = ly * kTileX + lx;
+      const uint8_t me = st[li] & 1u;
+      const bool hbond = lx + 1 < kTileX && w[2 * h] < thr && me == (st[li + 1] & 1u);
+      const bool vbond = ly + 1 < kTileY && w[2 * h + 1] < thr && me == (st[li + kTileX] & 1u);
+      st[li] = (uint8_t)(me | (hbond ? 2u : 0u) | (vbond ? 4u : 0u));
+    }
+  }
+  __syncthreads();
+  // horizontal runs: one warp per row, four consecutive sites per lane
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int ly = warp; ly < kTileY; ly += nwarps) {
+      const int base = ly * kTileX + 4 * lane;
+      int start[4], last = -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int lx = 4 * lane + k;
+        if (lx == 0 || !(st[base + k - 1] & 2u)) last = lx;
+        start[k] = last;
+      }
+      // carry: the last run start of lanes below (inclusive max-scan)
+      int carry = last;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, carry, off);
+        if (lane >= off) carry = max(carry, v);
+      }
+      int prev = __shfl_up_sync(0xffffffffu, carry, 1);
+      if (lane == 0) prev = -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) lab[base + k] = (uint32_t)(ly * kTileX + (start[k] >= 0 ? start[k] : prev));
+    }
+  }
+  __syncthreads();
+  // vertical bonds unite runs
+  for (int li = threadIdx.x; li < kTileSites; li += blockDim.x) {
+    if (!(st[li] & 4u)) continue;
+    const int lx = li % kTileX;
+    // the left neighbour's vertical bond already joined the same two runs
+    if (lx > 0 && (st[li - 1] & 6u) == 6u && (st[li - 1 + kTileX] & 2u)) continue;
+    sunite(lab, (uint32_t)(li + kTileX), (uint32_t)li);
+  }
+  __syncthreads();
+  for (int li = threadIdx.x; li < kTileSites; li += blockDim.x) {
+    const uint32_t r = sfind(lab, (uint32_t)li);
+    const int ly = li / kTileX, lx = li - ly * kTileX;
+    const int ry = (int)r / kTileX, rx = (int)r - ry * kTileX;
+    const size_t g = (size_t)(y0 + ly) * L + x0 + lx;
+    parent[g] = (uint32_t)((size_t)(y0 + ry) * L + x0 + rx);
+    mark[g] = (uint8_t)(r == (uint32_t)li ? 2 : 0);
+  }
+}
+
+// After the edge unions: every local root (mark 2) finds its final root and
+// stores it (its own entry only); a final root draws its cluster's coin into
+// mark[] (0 / 1).  Then parent[parent[i]] is every site's final root.
+__global__ void k_sw_resolve(uint32_t* __restrict__ parent, uint8_t* __restrict__ mark, long long N,
+                             uint32_t step, RngParams rng) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (mark[i] != 2) continue;
+    const uint32_t m = find_root_ro(parent, (uint32_t)i);
+    parent[i] = m;
+    if (m == (uint32_t)i) {
+      const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
+      const uint32_t w = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
+      mark[i] = (uint8_t)(w >> 31);
+    }
+  }
+}
+
+// One warp per packed word, one lane per site: each lane gathers its site's
+// final root (parent[parent[site]] after k_sw_resolve) and that root's coin;
+// a ballot assembles the flip mask (independent gathers in flight per lane).
+__global__ void __launch_bounds__(256) k_sw_apply2(uint32_t* __restrict__ planes, int L, int Wc,
+                                                   const uint32_t* __restrict__ parent,
+                                                   const uint8_t* __restrict__ coin) {
+  const int n = L / 2;
+  const long long words = 2LL * L * Wc;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = warp0; i < words; i += nwarps) {
+    const int c = (int)(i / ((long long)L * Wc));
+    const long long rem = i - (long long)c * L * Wc;
+    const int y = (int)(rem / Wc), w = (int)(rem - (rem / Wc) * Wc);
+    const int j = 32 * w + lane;
+    bool f = false;
+    if (j < n) {
+      const int x = 2 * j + ((y + c) & 1);
+      const uint32_t m = __ldg(&parent[__ldg(&parent[(size_t)y * L + x])]);
+      f = __ldg(&coin[m]) != 0;
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, f);
+    if (lane == 0 && mask) planes[i] ^= mask;
+  }
+}
+
+// Bonds across tile edges (right edge: dir 0 from the last column; bottom edge:
+// dir 1 from the last row; periodic), united in the global forest.
+__global__ void __launch_bounds__(256) k_sw_edges(const uint32_t* __restrict__ planes, int L, int Wc,
+                                                  uint32_t step, uint32_t thr, RngParams rng,
+                                                  uint32_t* __restrict__ parent) {
+  const int tiles_x = L / kTileX;
+  const long long n_tiles = (long long)tiles_x * (L / kTileY);
+  const long long total = n_tiles * (kTileX + kTileY);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long tile = i / (kTileX + kTileY);
+    const int k = (int)(i - tile * (kTileX + kTileY));
+    const int tx = (int)(tile % tiles_x), ty = (int)(tile / tiles_x);
+    int x, y, dir;
+    if (k < kTileY) {
+      x = tx * kTileX + kTileX - 1;
+      y = ty * kTileY + k;
+      dir = 0;
+    } else {
+      x = tx * kTileX + (k - kTileY);
+      y = ty * kTileY + kTileY - 1;
+      dir = 1;
+    }
+    const int xn = dir == 0 ? (x + 1 == L ? 0 : x + 1) : x;
+    const int yn = dir == 0 ? y : (y + 1 == L ? 0 : y + 1);
+    if (bit_at(planes, L, Wc, x, y) != bit_at(planes, L, Wc, xn, yn)) continue;
+    const long long a = (long long)y * L + x;
+    const uint4 r = philox10_rk(make_uint4((uint32_t)(a >> 1), step, rng.replica, kTagSWBond << 16),
+                                rng.rk0, rng.rk1);
+    const int wsel = 2 * (int)(a & 1) + dir;
+    const uint32_t u = wsel == 0 ? r.x : (wsel == 1 ? r.y : (wsel == 2 ? r.z : r.w));
+    if (u >= thr) continue;
+    unite(parent, (uint32_t)a, (uint32_t)yn * (uint32_t)L + (uint32_t)xn);
+  }
+}
+
 int grid_of(long long items) {
   long long g = (items + 255) / 256;
   if (g < 1) g = 1;
@@ -153,12 +360,31 @@ cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
                            const RngParams& rng, uint32_t* parent, uint8_t* flip,
                            cudaStream_t s) {
   const long long N = (long long)lat.L * lat.L;
-  k_sw_init<<<grid_of(N), 256, 0, s>>>(parent, N);
-  cudaError_t e = cudaGetLastError();
-  if (e) return e;
-  k_sw_bonds<<<grid_of((N + 1) / 2), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent);
-  e = cudaGetLastError();
-  if (e) return e;
+  cudaError_t e;
+  // tiles only pay when there are enough of them to fill the GPU (>= 512 CTAs)
+  if (lat.L % kTileX == 0 && lat.L % kTileY == 0 && lat.L >= 2048) {
+    const long long tiles = (long long)(lat.L / kTileX) * (lat.L / kTileY);
+    k_sw_local<<<(unsigned)tiles, kTileThreads, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
+                                                        flip);
+    e = cudaGetLastError();
+    if (e) return e;
+    k_sw_edges<<<grid_of(tiles * (kTileX + kTileY)), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng,
+                                                                  parent);
+    e = cudaGetLastError();
+    if (e) return e;
+    k_sw_resolve<<<grid_of(N), 256, 0, s>>>(parent, flip, N, step, rng);
+    e = cudaGetLastError();
+    if (e) return e;
+    k_sw_apply2<<<grid_of(2LL * lat.L * lat.Wc * 32), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, parent, flip);
+    return cudaGetLastError();
+  } else {
+    k_sw_init<<<grid_of(N), 256, 0, s>>>(parent, N);
+    e = cudaGetLastError();
+    if (e) return e;
+    k_sw_bonds<<<grid_of((N + 1) / 2), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent);
+    e = cudaGetLastError();
+    if (e) return e;
+  }
   k_sw_roots<<<grid_of(N), 256, 0, s>>>(parent, N, step, rng, flip);
   e = cudaGetLastError();
   if (e) return e;

@@ -25,7 +25,7 @@ def _cuda():
     ising.lib()
 
 
-@pytest.mark.parametrize("L", [4, 6, 62, 64, 130, 256])
+@pytest.mark.parametrize("L", [4, 6, 62, 64, 128, 130, 256, 384])
 @pytest.mark.parametrize("beta", [1e-9, 0.3, BETA_C, 0.7, 50.0])
 def test_sw_bit_exact(L, beta):
     seed, n = 0xBEEF0000 + L, 6
@@ -56,6 +56,22 @@ def test_sw_after_metropolis_and_replica():
     oracle.sweep(s, beta, seed, 2, t0=4, replica=3)
     oracle.sw_steps(s, beta, seed, 1, step0=5, replica=3)
     assert np.array_equal(got, s)
+
+
+@pytest.mark.parametrize("L,beta", [(2048, BETA_C), (2560, 0.3), (2048, 0.7)])
+def test_sw_tiled_labelling_bit_exact(L, beta):
+    """Lattices of >= 2048 sites a side that are multiples of the 128 x 64 tile
+    take the shared-memory labelling path."""
+    seed = 40 + L
+    s = oracle.init(L, seed)
+    with ising.Lattice(L, beta, seed=seed) as lat:
+        lat.set_spins(s)
+        lat.sw_step(2, 1)
+        got = lat.spins()
+        E, M = lat.series(2)
+    E_ref, M_ref, _ = oracle.sw_steps(s, beta, seed, 2)
+    assert np.array_equal(got, s)
+    assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
 
 
 def test_sw_large_lattice_one_step():
