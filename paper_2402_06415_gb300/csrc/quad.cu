@@ -67,29 +67,38 @@ struct Count3 {  // bit-sliced 3-bit counter per lane (counts 0..4)
   }
 };
 
+// Neighbour-plane loads: through the read-only path from global memory (G), or
+// plain loads from shared memory in the persistent single-CTA kernel.
+template <bool G>
+__device__ __forceinline__ uint32_t ldw(const uint32_t* p) {
+  if (G) return __ldg(p);
+  return *p;
+}
+
 // Word whose bit b holds the spin of cell X = 32 w + b + DX (periodic in X) of a row.
-template <int DX>
+template <int DX, bool G = true>
 __device__ __forceinline__ uint32_t xword(const uint32_t* __restrict__ row, const QuadGeom& g, int w) {
-  const uint32_t cur = __ldg(row + w);
+  const uint32_t cur = ldw<G>(row + w);
   if (DX == 0) return cur;
   if (DX > 0) {
     const bool last = w == g.Wq - 1;
-    const uint32_t nxt = __ldg(row + (last ? 0 : w + 1));
+    const uint32_t nxt = ldw<G>(row + (last ? 0 : w + 1));
     const int valid = last ? g.nlast : 32;
     return (cur >> 1) | ((nxt & 1u) << (valid - 1));
   }
   const bool first = w == 0;
-  const uint32_t prv = __ldg(row + (first ? g.Wq - 1 : w - 1));
+  const uint32_t prv = ldw<G>(row + (first ? g.Wq - 1 : w - 1));
   const int pvalid = first ? g.nlast : 32;
   return (cur << 1) | ((prv >> (pvalid - 1)) & 1u);
 }
 
+template <bool G>
 __device__ __forceinline__ uint32_t xword_dir(const uint32_t* row, const QuadGeom& g, int w, int dx) {
-  return dx > 0 ? xword<1>(row, g, w) : xword<-1>(row, g, w);
+  return dx > 0 ? xword<1, G>(row, g, w) : xword<-1, G>(row, g, w);
 }
 
 // Antiparallel J1 / J2 neighbour counts of the 32 sites of word (q, Y, w).
-template <int LAT>
+template <int LAT, bool G = true>
 __device__ __forceinline__ void count_anti(const uint32_t* __restrict__ planes, const QuadGeom& g,
                                            int q, int Y, int w, uint32_t me, Count3& n1, Count3& n2) {
   const size_t plane = (size_t)g.Lc * g.Wq;
@@ -102,23 +111,23 @@ __device__ __forceinline__ void count_anti(const uint32_t* __restrict__ planes, 
     const uint32_t* ry1 = planes + (size_t)(q ^ 2) * plane + (size_t)Yn * g.Wq;
     const uint32_t* rd0 = planes + (size_t)(q ^ 3) * plane + (size_t)Y * g.Wq;
     const uint32_t* rd1 = planes + (size_t)(q ^ 3) * plane + (size_t)Yn * g.Wq;
-    n1.add(me ^ xword<0>(rx, g, w));
-    n1.add(me ^ xword_dir(rx, g, w, sx));
-    n1.add(me ^ xword<0>(ry0, g, w));
-    n1.add(me ^ xword<0>(ry1, g, w));
-    n2.add(me ^ xword<0>(rd0, g, w));
-    n2.add(me ^ xword_dir(rd0, g, w, sx));
-    n2.add(me ^ xword<0>(rd1, g, w));
-    n2.add(me ^ xword_dir(rd1, g, w, sx));
+    n1.add(me ^ xword<0, G>(rx, g, w));
+    n1.add(me ^ xword_dir<G>(rx, g, w, sx));
+    n1.add(me ^ xword<0, G>(ry0, g, w));
+    n1.add(me ^ xword<0, G>(ry1, g, w));
+    n2.add(me ^ xword<0, G>(rd0, g, w));
+    n2.add(me ^ xword_dir<G>(rd0, g, w, sx));
+    n2.add(me ^ xword<0, G>(rd1, g, w));
+    n2.add(me ^ xword_dir<G>(rd1, g, w, sx));
   } else {
     const int nxt = (q + 1) & 3, prv = (q + 3) & 3;
-    n1.add(me ^ xword<0>(planes + (size_t)nxt * plane + (size_t)Y * g.Wq, g, w));
-    n1.add(me ^ xword<0>(planes + (size_t)prv * plane + (size_t)Y * g.Wq, g, w));
+    n1.add(me ^ xword<0, G>(planes + (size_t)nxt * plane + (size_t)Y * g.Wq, g, w));
+    n1.add(me ^ xword<0, G>(planes + (size_t)prv * plane + (size_t)Y * g.Wq, g, w));
     uint32_t o;
-    if (q == 0) o = xword<0>(planes + 2 * plane + (size_t)Yp * g.Wq, g, w);
-    else if (q == 1) o = xword<1>(planes + 3 * plane + (size_t)Y * g.Wq, g, w);
-    else if (q == 2) o = xword<0>(planes + 0 * plane + (size_t)Ym * g.Wq, g, w);
-    else o = xword<-1>(planes + 1 * plane + (size_t)Y * g.Wq, g, w);
+    if (q == 0) o = xword<0, G>(planes + 2 * plane + (size_t)Yp * g.Wq, g, w);
+    else if (q == 1) o = xword<1, G>(planes + 3 * plane + (size_t)Y * g.Wq, g, w);
+    else if (q == 2) o = xword<0, G>(planes + 0 * plane + (size_t)Ym * g.Wq, g, w);
+    else o = xword<-1, G>(planes + 1 * plane + (size_t)Y * g.Wq, g, w);
     n2.add(me ^ o);
   }
 }
@@ -127,60 +136,64 @@ __device__ __forceinline__ uint32_t valid_bits(const QuadGeom& g, int w) {
   return (w == g.Wq - 1 && g.nlast < 32) ? ((1u << g.nlast) - 1u) : 0xffffffffu;
 }
 
+// Metropolis trials of the 32 sites of word i = Y Wq + w of sublattice q.
+template <int LAT, int NV, bool G>
+__device__ __forceinline__ void quad_word(uint32_t* __restrict__ planes, const QuadGeom& g, int q,
+                                          long long i, uint32_t t, const RngParams& rng, const QuadTable& tab) {
+  constexpr int Z2 = LAT == ISING_QUAD_SQUARE ? 4 : 1;
+  constexpr int Z1 = LAT == ISING_QUAD_SQUARE ? 4 : 2;
+  const int Y = (int)(i / g.Wq), w = (int)(i - (long long)Y * g.Wq);
+  uint32_t* own = planes + (size_t)q * g.Lc * g.Wq + i;
+  const uint32_t me = *own;
+  const uint32_t valid = valid_bits(g, w);
+  Count3 n1, n2;
+  count_anti<LAT, G>(planes, g, q, Y, w, me, n1, n2);
+  uint32_t e2[Z2 + 1];
+#pragma unroll
+  for (int a2 = 0; a2 <= Z2; ++a2) e2[a2] = n2.eq(a2);
+  uint32_t always = 0, vm[NV];
+#pragma unroll
+  for (int d = 0; d < NV; ++d) vm[d] = 0;
+#pragma unroll
+  for (int a1 = 0; a1 <= Z1; ++a1) {
+    const uint32_t e1 = n1.eq(a1);
+#pragma unroll
+    for (int a2 = 0; a2 <= Z2; ++a2) {
+      const int c = a1 * (Z2 + 1) + a2;
+      const uint32_t cm = e1 & e2[a2];
+      always |= cm & (0u - ((tab.always >> c) & 1u));
+#pragma unroll
+      for (int d = 0; d < NV; ++d) vm[d] |= cm & (0u - ((tab.cls[d] >> c) & 1u));
+    }
+  }
+  uint32_t und = ~always & valid, lt = 0;
+  const uint32_t g_idx = (uint32_t)i;
+#pragma unroll 1
+  for (int m = 0; m < 8 && und; ++m) {
+    const uint4 r = philox10_rk(make_uint4(g_idx, t, rng.replica, (kTagQuadMet << 16) | ((uint32_t)q << 8) | (uint32_t)m),
+                                rng.rk0, rng.rk1);
+    const uint32_t pw[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int lvl = 4 * m + k;
+      uint32_t tm = 0;
+#pragma unroll
+      for (int d = 0; d < NV; ++d) tm |= vm[d] & (0u - ((tab.val[d] >> (31 - lvl)) & 1u));
+      lt |= und & ~pw[k] & tm;
+      und &= ~(pw[k] ^ tm);
+    }
+  }
+  const uint32_t flip = (always | lt) & valid;
+  if (flip) *own = me ^ flip;
+}
+
 template <int LAT, int NV>
 __global__ void __launch_bounds__(256) k_quad_quarter(uint32_t* __restrict__ planes, QuadGeom g, int q,
                                                       uint32_t t, RngParams rng, QuadTable tab) {
-  constexpr int Z2 = LAT == ISING_QUAD_SQUARE ? 4 : 1;
-  constexpr int Z1 = LAT == ISING_QUAD_SQUARE ? 4 : 2;
-  constexpr int NC = (Z1 + 1) * (Z2 + 1);
   const long long words = (long long)g.Lc * g.Wq;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int Y = (int)(i / g.Wq), w = (int)(i - (long long)Y * g.Wq);
-    uint32_t* own = planes + (size_t)q * g.Lc * g.Wq + i;
-    const uint32_t me = *own;
-    const uint32_t valid = valid_bits(g, w);
-    Count3 n1, n2;
-    count_anti<LAT>(planes, g, q, Y, w, me, n1, n2);
-    uint32_t e2[Z2 + 1];
-#pragma unroll
-    for (int a2 = 0; a2 <= Z2; ++a2) e2[a2] = n2.eq(a2);
-    uint32_t always = 0, vm[NV];
-#pragma unroll
-    for (int d = 0; d < NV; ++d) vm[d] = 0;
-#pragma unroll
-    for (int a1 = 0; a1 <= Z1; ++a1) {
-      const uint32_t e1 = n1.eq(a1);
-#pragma unroll
-      for (int a2 = 0; a2 <= Z2; ++a2) {
-        const int c = a1 * (Z2 + 1) + a2;
-        const uint32_t cm = e1 & e2[a2];
-        always |= cm & (0u - ((tab.always >> c) & 1u));
-#pragma unroll
-        for (int d = 0; d < NV; ++d) vm[d] |= cm & (0u - ((tab.cls[d] >> c) & 1u));
-      }
-    }
-    (void)NC;
-    uint32_t und = ~always & valid, lt = 0;
-    const uint32_t g_idx = (uint32_t)i;
-#pragma unroll 1
-    for (int m = 0; m < 8 && und; ++m) {
-      const uint4 r = philox10_rk(make_uint4(g_idx, t, rng.replica, (kTagQuadMet << 16) | ((uint32_t)q << 8) | (uint32_t)m),
-                                  rng.rk0, rng.rk1);
-      const uint32_t pw[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int lvl = 4 * m + k;
-        uint32_t tm = 0;
-#pragma unroll
-        for (int d = 0; d < NV; ++d) tm |= vm[d] & (0u - ((tab.val[d] >> (31 - lvl)) & 1u));
-        lt |= und & ~pw[k] & tm;
-        und &= ~(pw[k] ^ tm);
-      }
-    }
-    const uint32_t flip = (always | lt) & valid;
-    if (flip) *own = me ^ flip;
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    quad_word<LAT, NV, true>(planes, g, q, i, t, rng, tab);
 }
 
 __global__ void k_quad_init(uint32_t* __restrict__ planes, QuadGeom g, RngParams rng) {
@@ -196,30 +209,38 @@ __global__ void k_quad_init(uint32_t* __restrict__ planes, QuadGeom g, RngParams
   }
 }
 
-// rec[0] += 2 B1, rec[1] += 2 B2 (each bond seen from both ends), rec[2] += M.
-template <int LAT>
-__global__ void __launch_bounds__(256) k_quad_measure(const uint32_t* __restrict__ planes, QuadGeom g,
-                                                      unsigned long long* __restrict__ rec) {
+// Bond sums of word i of the 4 Lc Wq words: (2 B1, 2 B2, M) contributions (each
+// bond is seen from both ends).
+template <int LAT, bool G>
+__device__ __forceinline__ void quad_measure_word(const uint32_t* __restrict__ planes, const QuadGeom& g,
+                                                  long long i, long long& b1, long long& b2, long long& m) {
   constexpr int Z1 = LAT == ISING_QUAD_SQUARE ? 4 : 2;
   constexpr int Z2 = LAT == ISING_QUAD_SQUARE ? 4 : 1;
   const long long words = (long long)g.Lc * g.Wq;
+  const int q = (int)(i / words);
+  const long long gi = i - (long long)q * words;
+  const int Y = (int)(gi / g.Wq), w = (int)(gi - (long long)Y * g.Wq);
+  const uint32_t v = valid_bits(g, w);
+  const uint32_t me = planes[i];
+  Count3 n1, n2;
+  count_anti<LAT, G>(planes, g, q, Y, w, me, n1, n2);
+  const int nv = __popc(v);
+  const int anti1 = __popc(n1.c0 & v) + 2 * __popc(n1.c1 & v) + 4 * __popc(n1.c2 & v);
+  const int anti2 = __popc(n2.c0 & v) + 2 * __popc(n2.c1 & v) + 4 * __popc(n2.c2 & v);
+  b1 += (long long)Z1 * nv - 2LL * anti1;
+  b2 += (long long)Z2 * nv - 2LL * anti2;
+  m += 2LL * __popc(me & v) - nv;
+}
+
+// rec[0] += 2 B1, rec[1] += 2 B2, rec[2] += M.
+template <int LAT>
+__global__ void __launch_bounds__(256) k_quad_measure(const uint32_t* __restrict__ planes, QuadGeom g,
+                                                      unsigned long long* __restrict__ rec) {
+  const long long words = (long long)g.Lc * g.Wq;
   long long b1 = 0, b2 = 0, m = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * words;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(i / words);
-    const long long gi = i - (long long)q * words;
-    const int Y = (int)(gi / g.Wq), w = (int)(gi - (long long)Y * g.Wq);
-    const uint32_t v = valid_bits(g, w);
-    const uint32_t me = planes[i];
-    Count3 n1, n2;
-    count_anti<LAT>(planes, g, q, Y, w, me, n1, n2);
-    const int nv = __popc(v);
-    const int anti1 = __popc(n1.c0 & v) + 2 * __popc(n1.c1 & v) + 4 * __popc(n1.c2 & v);
-    const int anti2 = __popc(n2.c0 & v) + 2 * __popc(n2.c1 & v) + 4 * __popc(n2.c2 & v);
-    b1 += (long long)Z1 * nv - 2LL * anti1;
-    b2 += (long long)Z2 * nv - 2LL * anti2;
-    m += 2LL * __popc(me & v) - nv;
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    quad_measure_word<LAT, true>(planes, g, i, b1, b2, m);
   const unsigned long long s1 = warp_sum_u64((unsigned long long)b1);
   const unsigned long long s2 = warp_sum_u64((unsigned long long)b2);
   const unsigned long long s3 = warp_sum_u64((unsigned long long)m);
@@ -228,6 +249,58 @@ __global__ void __launch_bounds__(256) k_quad_measure(const uint32_t* __restrict
     atomicAdd(&rec[1], s2);
     atomicAdd(&rec[2], s3);
   }
+}
+
+// Small lattices (the paper's N = 16 ... 4096 and up to 256^2 cells): the whole
+// lattice in shared memory, one CTA, n sweeps in one launch with __syncthreads()
+// between quarter sweeps; records (2 B1, 2 B2, M) written to ring slots rec0, ...
+template <int LAT, int NV>
+__global__ void __launch_bounds__(1024) k_quad_persist(uint32_t* __restrict__ planes, QuadGeom g, uint32_t t0,
+                                                       int n, int meas_every, RngParams rng, QuadTable tab,
+                                                       unsigned long long* __restrict__ rec, long long rec0,
+                                                       long long rec_cap) {
+  extern __shared__ uint32_t sp[];
+  __shared__ long long red[3][32];
+  const long long words = (long long)g.Lc * g.Wq;
+  for (long long i = threadIdx.x; i < 4 * words; i += blockDim.x) sp[i] = planes[i];
+  __syncthreads();
+  long long ri = rec0;
+  for (int s = 0; s < n; ++s) {
+    const uint32_t t = t0 + (uint32_t)s;
+    for (int q = 0; q < 4; ++q) {
+      for (long long i = threadIdx.x; i < words; i += blockDim.x) quad_word<LAT, NV, false>(sp, g, q, i, t, rng, tab);
+      __syncthreads();
+    }
+    if (meas_every > 0 && ((long long)t + 1) % meas_every == 0) {
+      long long b1 = 0, b2 = 0, m = 0;
+      for (long long i = threadIdx.x; i < 4 * words; i += blockDim.x) quad_measure_word<LAT, false>(sp, g, i, b1, b2, m);
+      b1 = (long long)warp_sum_u64((unsigned long long)b1);
+      b2 = (long long)warp_sum_u64((unsigned long long)b2);
+      m = (long long)warp_sum_u64((unsigned long long)m);
+      const int wid = threadIdx.x >> 5;
+      if ((threadIdx.x & 31) == 0) {
+        red[0][wid] = b1;
+        red[1][wid] = b2;
+        red[2][wid] = m;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long a = 0, b = 0, c = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+          a += red[0][k];
+          b += red[1][k];
+          c += red[2][k];
+        }
+        unsigned long long* slot = rec + 3 * (ri % rec_cap);
+        slot[0] = (unsigned long long)a;
+        slot[1] = (unsigned long long)b;
+        slot[2] = (unsigned long long)c;
+      }
+      ++ri;
+      __syncthreads();
+    }
+  }
+  for (long long i = threadIdx.x; i < 4 * words; i += blockDim.x) planes[i] = sp[i];
 }
 
 int qfail(int code, const char* fmt, ...) {
@@ -321,8 +394,39 @@ cudaError_t quarter_dispatch(ising_quad* x, int q, uint32_t t, const RngParams& 
   return cudaErrorInvalidValue;  // the square-octagon lattice has at most 6 classes
 }
 
+constexpr int kQuadPersistMaxLc = 256;  // shared memory: 4 Lc ceil(Lc/32) words <= 32 KB
+
+template <int LAT, int NV>
+cudaError_t launch_persist(ising_quad* x, int n, int m, const RngParams& rng) {
+  const long long words = (long long)x->Lc * x->geom.Wq;
+  const int threads = (int)std::min<long long>(1024, ((words + 31) / 32) * 32);
+  const size_t smem = (size_t)4 * words * sizeof(uint32_t);
+  k_quad_persist<LAT, NV><<<1, threads, smem, x->stream>>>(x->planes, x->geom, (uint32_t)x->sweep, n, m, rng,
+                                                           x->tab, x->rec, x->rec_count, kQuadRec);
+  return cudaGetLastError();
+}
+
+template <int LAT>
+cudaError_t persist_dispatch(ising_quad* x, int n, int m, const RngParams& rng) {
+  const int nv = x->tab.n_vals;
+  if (nv <= 2) return launch_persist<LAT, 2>(x, n, m, rng);
+  if (nv <= 8) return launch_persist<LAT, 8>(x, n, m, rng);
+  if (LAT == ISING_QUAD_SQUARE) return launch_persist<LAT, kMaxClasses>(x, n, m, rng);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t quad_sweeps(ising_quad* x, int n, int m) {
   const RngParams rng = make_rng(x->seed, x->replica, 0, 0);
+  if (x->Lc <= kQuadPersistMaxLc && n > 0) {
+    cudaError_t e = x->lattice == ISING_QUAD_SQUARE ? persist_dispatch<ISING_QUAD_SQUARE>(x, n, m, rng)
+                                                    : persist_dispatch<ISING_QUAD_SQOCT>(x, n, m, rng);
+    if (e) return e;
+    ++x->launches;
+    if (m > 0)
+      for (int s = 0; s < n; ++s)
+        if ((x->sweep + s + 1) % m == 0) ++x->rec_count;
+    return cudaSuccess;
+  }
   for (int s = 0; s < n; ++s) {
     const uint32_t t = (uint32_t)(x->sweep + s);
     for (int q = 0; q < 4; ++q) {

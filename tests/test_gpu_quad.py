@@ -27,7 +27,7 @@ CASES = [(SQ, 1.0, 0.0), (SQ, 1.0, 0.5), (SQ, 1.0, -0.5), (SQ, 0.75, 1.25), (SQ,
 
 
 @pytest.mark.parametrize("lattice,J1,J2", CASES)
-@pytest.mark.parametrize("Lc", [2, 3, 5, 32, 33, 70, 128])
+@pytest.mark.parametrize("Lc", [2, 3, 5, 32, 33, 70, 128, 256, 300])
 @pytest.mark.parametrize("beta", [0.2, 0.4406868, 0.9])
 def test_quad_bit_exact(lattice, J1, J2, Lc, beta):
     seed, n = 0xC0FFEE00 + Lc, 5
