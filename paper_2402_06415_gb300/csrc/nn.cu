@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -48,7 +49,8 @@ constexpr int kOffW1 = 0, kOffB1 = 576, kOffW2 = 608, kOffB2 = 9824, kOffW3 = 98
               kOffB3 = 10144, kNParams = 10145;
 constexpr uint32_t kTagBlkSample = 4, kTagBlkAccept = 5, kTagBlkOffset = 6;
 constexpr int kMaxB = 16;
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;       // training kernels
+constexpr int kInferThreads = 512;  // inference / block-pass kernels
 
 __host__ __device__ constexpr int frame_of(int B) { return B + 2; }
 
@@ -65,12 +67,68 @@ struct InferSmem {
   float logit[kMaxB * kMaxB];
   int8_t win[(kMaxB + 2) * (kMaxB + 2)];
   int8_t nw[kMaxB * kMaxB];
-  float red_lq[kThreads / 32];
-  int red_de[kThreads / 32];
+  float red_lq[kInferThreads / 32];
+  int red_de[kInferThreads / 32];
   int accept;
+  // Positions whose values depend on the window.  The input is nonzero only on
+  // the ring (frame distance 0), so layer-1 outputs at frame distance >= 2,
+  // layer-2 outputs at distance >= 3 and logits at distance >= 4 are the same
+  // for every window: computed once per CTA (first window), then only these
+  // lists are recomputed.  d = min(fy, fx, F-1-fy, F-1-fx).
+  int16_t var1[(kMaxB + 2) * (kMaxB + 2)];  // frame positions, d <= 1
+  int16_t var2[(kMaxB + 2) * (kMaxB + 2)];  // frame positions, d <= 2
+  int16_t var3[kMaxB * kMaxB];              // interior indices iy B + ix, d <= 3
+  int n_var1, n_var2, n_var3;
 };
 
+// Builds the variable-position lists (warp 0, ballot compaction; the order of
+// a list does not matter).  Call before the first window, then __syncthreads().
+__device__ void build_var_lists(InferSmem& S, int B) {
+  if (threadIdx.x >= 32) return;
+  const int F = B + 2, lane = threadIdx.x;
+  int n1 = 0, n2 = 0, n3 = 0;
+  for (int p0 = 0; p0 < F * F; p0 += 32) {
+    const int p = p0 + lane;
+    const int fy = p / F, fx = p - (p / F) * F;
+    const int d = min(min(fy, fx), min(F - 1 - fy, F - 1 - fx));
+    const bool in = p < F * F;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned b1 = __ballot_sync(0xffffffffu, in && d <= 1);
+    const unsigned b2 = __ballot_sync(0xffffffffu, in && d <= 2);
+    const unsigned b3 = __ballot_sync(0xffffffffu, in && d >= 1 && d <= 3);
+    if (in && d <= 1) S.var1[n1 + __popc(b1 & below)] = (int16_t)p;
+    if (in && d <= 2) S.var2[n2 + __popc(b2 & below)] = (int16_t)p;
+    if (in && d >= 1 && d <= 3) S.var3[n3 + __popc(b3 & below)] = (int16_t)((fy - 1) * B + fx - 1);
+    n1 += __popc(b1);
+    n2 += __popc(b2);
+    n3 += __popc(b3);
+  }
+  if (lane == 0) {
+    S.n_var1 = n1;
+    S.n_var2 = n2;
+    S.n_var3 = n3;
+  }
+}
+
 __device__ __forceinline__ float bf(const __nv_bfloat16& v) { return __bfloat162float(v); }
+
+// Per-network cache of the window-independent activations, one slot per block
+// size B in {2, 4, 8, 16}: the bytes of h1, h1lo, h2 (with their zero padding)
+// followed by the logits, as a CTA holds them after processing any window.  It
+// lives behind the re-laid-out W2 in the same allocation and is rebuilt by
+// k_nn_const whenever weights are loaded.
+constexpr size_t kActBytes = sizeof(__nv_bfloat16) * 2 * (kMaxB + 4) * (kMaxB + 4) * kCP +
+                             sizeof(float) * (kMaxB + 4) * (kMaxB + 4) * kC;
+constexpr size_t kCacheSlot = ((kActBytes + sizeof(float) * kMaxB * kMaxB) + 255) / 256 * 256;
+constexpr size_t kW2tBytes = ((size_t)kC * kK2P * sizeof(__nv_bfloat16) + 255) / 256 * 256;
+
+static_assert(offsetof(InferSmem, h1) == 0 && offsetof(InferSmem, w2t) == kActBytes && kActBytes % 16 == 0,
+              "the activation cache copies the leading h1 / h1lo / h2 grids as one block");
+static_assert(offsetof(InferSmem, w2t) % 16 == 0 && (kC * kK2P * 2) % 16 == 0, "W2 is copied as uint4");
+
+__host__ __device__ inline int cache_slot_of(int B) {
+  return B == 2 ? 0 : (B == 4 ? 1 : (B == 8 ? 2 : (B == 16 ? 3 : -1)));
+}
 
 // is frame position (fy, fx) on one of the four ring edges (not a corner)?
 __device__ __forceinline__ bool ring_edge(int fy, int fx, int F) {
@@ -79,42 +137,77 @@ __device__ __forceinline__ bool ring_edge(int fy, int fx, int F) {
   return ey || ex;
 }
 
-// Loads weights into shared memory and zeroes the padding of the grids.
-__device__ void load_weights(InferSmem& S, const __nv_bfloat16* __restrict__ w,
-                             const __nv_bfloat16* __restrict__ w2t, int B) {
+// Loads weights into shared memory and zeroes the padding of the grids; with a
+// cache slot, the grids and logits come from it instead (returns true: only the
+// window-dependent positions need computing).
+__device__ bool load_weights(InferSmem& S, const __nv_bfloat16* __restrict__ w,
+                             const __nv_bfloat16* __restrict__ w2t, int B, bool use_cache) {
   const int FP = frame_of(B) + 2;
   for (int i = threadIdx.x; i < kOffB1 + kC; i += blockDim.x) S.w1[i] = bf(w[kOffW1 + i]);
   for (int i = threadIdx.x; i < kC * 9 + 1; i += blockDim.x) S.w3[i] = bf(w[kOffW3 + i]);
   for (int i = threadIdx.x; i < kC; i += blockDim.x) S.b2[i] = bf(w[kOffB2 + i]);
-  for (int i = threadIdx.x; i < kC * kK2P; i += blockDim.x) S.w2t[i] = w2t[i];
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(w2t);
+    uint4* dst = reinterpret_cast<uint4*>(S.w2t);
+    for (int i = threadIdx.x; i < kC * kK2P * 2 / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  const int slot = use_cache ? cache_slot_of(B) : -1;
+  if (slot >= 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(w2t) + kW2tBytes +
+                                                      (size_t)slot * kCacheSlot);
+    uint4* dst = reinterpret_cast<uint4*>(&S);  // h1, h1lo, h2 lead the struct
+    for (int i = threadIdx.x; i < (int)(kActBytes / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    const float* lsrc = reinterpret_cast<const float*>(reinterpret_cast<const char*>(src) + kActBytes);
+    for (int i = threadIdx.x; i < kMaxB * kMaxB; i += blockDim.x) S.logit[i] = __ldg(lsrc + i);
+    return true;
+  }
   const __nv_bfloat16 z = __float2bfloat16(0.f);
   for (int i = threadIdx.x; i < FP * FP * kCP; i += blockDim.x) {
     S.h1[i] = z;
     S.h1lo[i] = z;
   }
   for (int i = threadIdx.x; i < FP * FP * kC; i += blockDim.x) S.h2[i] = 0.f;
+  return false;
 }
 
-// Layer 1 on the CUDA cores: h1 = relu(conv(frame)) on the F x F frame.
-__device__ void layer1(InferSmem& S, int B) {
+// Layer 1 on the CUDA cores: h1 = relu(conv(frame)) on the F x F frame (all
+// positions when full, else the window-dependent ones).  The input is nonzero
+// only on ring sites, so each (position, 4-channel group) task visits only its
+// ring taps (a 9-bit mask, ascending tap order as in the plain convolution).
+__device__ void layer1(InferSmem& S, int B, bool full) {
   const int F = frame_of(B), FP = F + 2;
-  for (int i = threadIdx.x; i < F * F * kC; i += blockDim.x) {
-    const int c = i % kC, p = i / kC;
+  const int np = full ? F * F : S.n_var1;
+  for (int task = threadIdx.x; task < np * (kC / 4); task += blockDim.x) {
+    const int cg = task & (kC / 4 - 1), k = task / (kC / 4);
+    const int p = full ? k : S.var1[k];
     const int fy = p / F, fx = p - (p / F) * F;
-    float z = S.w1[kOffB1 + c];
+    unsigned mask = 0;
 #pragma unroll
-    for (int dy = 0; dy < 3; ++dy)
+    for (int t = 0; t < 9; ++t) {
+      const int yy = fy + t / 3 - 1, xx = fx + t % 3 - 1;
+      if (yy >= 0 && yy < F && xx >= 0 && xx < F && ring_edge(yy, xx, F)) mask |= 1u << t;
+    }
+    float z[4];
 #pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        const int yy = fy + dy - 1, xx = fx + dx - 1;
-        if (yy < 0 || yy >= F || xx < 0 || xx >= F || !ring_edge(yy, xx, F)) continue;
-        const float s = (float)S.win[yy * F + xx];
-        z += S.w1[(c * 2 + 0) * 9 + dy * 3 + dx] * s + S.w1[(c * 2 + 1) * 9 + dy * 3 + dx];
+    for (int j = 0; j < 4; ++j) z[j] = S.w1[kOffB1 + 4 * cg + j];
+    while (mask) {
+      const int t = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const float sv = (float)S.win[(fy + t / 3 - 1) * F + fx + t % 3 - 1];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = 4 * cg + j;
+        z[j] += S.w1[(c * 2 + 0) * 9 + t] * sv + S.w1[(c * 2 + 1) * 9 + t];
       }
-    const float h = fmaxf(z, 0.f);
-    const __nv_bfloat16 hi = __float2bfloat16(h);
-    S.h1[((fy + 1) * FP + fx + 1) * kCP + c] = hi;
-    S.h1lo[((fy + 1) * FP + fx + 1) * kCP + c] = __float2bfloat16(h - __bfloat162float(hi));
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 4 * cg + j;
+      const float h = fmaxf(z[j], 0.f);
+      const __nv_bfloat16 hi = __float2bfloat16(h);
+      S.h1[((fy + 1) * FP + fx + 1) * kCP + c] = hi;
+      S.h1lo[((fy + 1) * FP + fx + 1) * kCP + c] = __float2bfloat16(h - __bfloat162float(hi));
+    }
   }
 }
 
@@ -124,8 +217,8 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 
 // Layer 2 on the tensor cores: implicit GEMM, M = F^2 positions, N = 32
 // channels, K = 288 (tap-major, 16 channels per step).
-__device__ void layer2(InferSmem& S, int B) {
-  const int F = frame_of(B), FP = F + 2, M = F * F;
+__device__ void layer2(InferSmem& S, int B, bool full) {
+  const int F = frame_of(B), FP = F + 2, M = full ? F * F : S.n_var2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int n_mt = (M + 15) / 16;
   for (int mt = warp; mt < n_mt; mt += nwarps) {
@@ -135,8 +228,9 @@ __device__ void layer2(InferSmem& S, int B) {
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
     // this lane's A row (output position) for ldmatrix.x4
-    int p = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-    if (p >= M) p = 0;  // padding rows: any valid address, results dropped
+    const int row = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+    // padding rows: any valid address, results dropped
+    const int p = row >= M ? 0 : (full ? row : S.var2[row]);
     const int py = p / F, px = p - (p / F) * F;
     const int acol = (lane >> 4) * 8;
 #pragma unroll 1
@@ -174,8 +268,9 @@ __device__ void layer2(InferSmem& S, int B) {
     const int g = lane >> 2, t2 = (lane & 3) * 2;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      const int pp = mt * 16 + g + half * 8;
-      if (pp >= M) continue;
+      const int rr = mt * 16 + g + half * 8;
+      if (rr >= M) continue;
+      const int pp = full ? rr : S.var2[rr];
       const int fy = pp / F, fx = pp - (pp / F) * F;
       float* dst = &S.h2[((fy + 1) * FP + fx + 1) * kC];
 #pragma unroll
@@ -188,20 +283,36 @@ __device__ void layer2(InferSmem& S, int B) {
   }
 }
 
-// Layer 3 on the CUDA cores: logits of the B x B interior.
-__device__ void layer3(InferSmem& S, int B) {
+// Layer 3 on the CUDA cores: logits of the B x B interior (all, or the
+// window-dependent ones).  Eight lanes per logit, four channels each over the
+// nine taps, then a three-step shuffle sum.
+__device__ void layer3(InferSmem& S, int B, bool full) {
   const int F = frame_of(B), FP = F + 2;
-  for (int i = threadIdx.x; i < B * B; i += blockDim.x) {
-    const int iy = i / B, ix = i - (i / B) * B;
-    const int fy = iy + 1, fx = ix + 1;
-    float z = S.w3[kC * 9];
-    for (int dy = 0; dy < 3; ++dy)
-      for (int dx = 0; dx < 3; ++dx) {
-        const float* h = &S.h2[((fy + dy) * FP + fx + dx) * kC];
-#pragma unroll 8
-        for (int c = 0; c < kC; ++c) z += S.w3[c * 9 + dy * 3 + dx] * h[c];
-      }
-    S.logit[i] = z;
+  const int n = full ? B * B : S.n_var3;
+  const int sub = threadIdx.x & 7, c0 = 4 * sub;
+  const int rounds = (n + (int)(blockDim.x >> 3) - 1) / (int)(blockDim.x >> 3);
+  for (int r = 0; r < rounds; ++r) {
+    const int k = r * (int)(blockDim.x >> 3) + (int)(threadIdx.x >> 3);
+    float z = 0.f;
+    int i = 0;
+    if (k < n) {
+      i = full ? k : S.var3[k];
+      const int iy = i / B, ix = i - (i / B) * B;
+      const int fy = iy + 1, fx = ix + 1;
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const float4 h = *reinterpret_cast<const float4*>(&S.h2[((fy + dy) * FP + fx + dx) * kC + c0]);
+          const int t = dy * 3 + dx;
+          z += S.w3[(c0 + 0) * 9 + t] * h.x + S.w3[(c0 + 1) * 9 + t] * h.y +
+               S.w3[(c0 + 2) * 9 + t] * h.z + S.w3[(c0 + 3) * 9 + t] * h.w;
+        }
+    }
+    z += __shfl_xor_sync(0xffffffffu, z, 4);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    if (k < n && sub == 0) S.logit[i] = z + S.w3[kC * 9];
   }
 }
 
@@ -244,7 +355,7 @@ __device__ void block_offset(uint32_t pass, uint32_t replica, const RngParams& r
 // One exact block MH update of square (bx, by) of a lattice (whole CTA).
 __device__ void process_block(InferSmem& S, uint32_t* planes, int L, int Wc, int B, int colour,
                               int ox, int oy, int bx, int by, uint32_t pass, uint32_t replica,
-                              const RngParams& rng, float beta, unsigned long long* stats) {
+                              const RngParams& rng, float beta, unsigned long long* stats, bool full) {
   const int F = frame_of(B);
   const int nbx = L / B;
   const int x0 = ox + bx * B, y0 = oy + by * B;  // interior origin (mod L)
@@ -257,11 +368,11 @@ __device__ void process_block(InferSmem& S, uint32_t* planes, int L, int Wc, int
     S.win[i] = (int8_t)get_spin(planes, L, Wc, y, x);
   }
   __syncthreads();
-  layer1(S, B);
+  layer1(S, B, full);
   __syncthreads();
-  layer2(S, B);
+  layer2(S, B, full);
   __syncthreads();
-  layer3(S, B);
+  layer3(S, B, full);
   __syncthreads();
   // proposal draw, log q terms and local energy terms
   float lq = 0.f;
@@ -338,7 +449,7 @@ __device__ void process_block(InferSmem& S, uint32_t* planes, int L, int Wc, int
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_nn_block_pass(PassParams P,
+__global__ void __launch_bounds__(kInferThreads) k_nn_block_pass(PassParams P,
                                                            const __nv_bfloat16* __restrict__ w,
                                                            const __nv_bfloat16* __restrict__ w2t) {
   extern __shared__ uint4 smem_raw[];
@@ -348,12 +459,14 @@ __global__ void __launch_bounds__(kThreads) k_nn_block_pass(PassParams P,
   const int n_blocks = nbx * half;  // squares of this colour
   int ox, oy;
   block_offset(P.pass, P.rng.replica, P.rng, B, ox, oy);
-  load_weights(S, w, w2t, B);
+  bool full = !load_weights(S, w, w2t, B, true);
+  build_var_lists(S, B);
   __syncthreads();
   for (int blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     const int by = blk / half, bx = 2 * (blk - by * half) + ((by + P.colour) & 1);
     process_block(S, P.planes, L, P.Wc, B, P.colour, ox, oy, bx, by, P.pass, P.rng.replica, P.rng,
-                  P.beta, P.stats);
+                  P.beta, P.stats, full);
+    full = false;
   }
 }
 
@@ -374,13 +487,14 @@ struct BatchPassParams {
   unsigned long long* stats;
 };
 
-__global__ void __launch_bounds__(kThreads) k_nn_batch_block_pass(BatchPassParams P,
+__global__ void __launch_bounds__(kInferThreads) k_nn_batch_block_pass(BatchPassParams P,
                                                                  const __nv_bfloat16* __restrict__ w,
                                                                  const __nv_bfloat16* __restrict__ w2t) {
   extern __shared__ uint4 smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
   const int B = P.B;
-  load_weights(S, w, w2t, B);
+  bool full = !load_weights(S, w, w2t, B, true);
+  build_var_lists(S, B);
   __syncthreads();
   const long long total = P.unit0[P.n_rep];
   for (long long u = blockIdx.x; u < total; u += gridDim.x) {
@@ -399,32 +513,61 @@ __global__ void __launch_bounds__(kThreads) k_nn_batch_block_pass(BatchPassParam
     block_offset(P.pass, (uint32_t)r, P.rng, B, ox, oy);
     const float beta = P.beta_of_slot[P.slot_of[r]];
     process_block(S, P.spins + P.off[r], L, Wc, B, P.colour, ox, oy, bx, by, P.pass, (uint32_t)r,
-                  P.rng, beta, P.stats);
+                  P.rng, beta, P.stats, full);
+    full = false;
   }
 }
 
 // Logits of windows [n][F][F] (int8 spins incl. interior, which is ignored).
-__global__ void __launch_bounds__(kThreads) k_nn_logits(const int8_t* __restrict__ windows, int n,
+__global__ void __launch_bounds__(kInferThreads) k_nn_logits(const int8_t* __restrict__ windows, int n,
                                                        int B, const __nv_bfloat16* __restrict__ w,
                                                        const __nv_bfloat16* __restrict__ w2t,
                                                        float* __restrict__ out) {
   extern __shared__ uint4 smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
   const int F = frame_of(B);
-  load_weights(S, w, w2t, B);
+  load_weights(S, w, w2t, B, false);
+  build_var_lists(S, B);
   __syncthreads();
+  bool full = true;
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
     for (int i = threadIdx.x; i < F * F; i += blockDim.x) S.win[i] = windows[(size_t)k * F * F + i];
     __syncthreads();
-    layer1(S, B);
+    layer1(S, B, full);
     __syncthreads();
-    layer2(S, B);
+    layer2(S, B, full);
     __syncthreads();
-    layer3(S, B);
+    layer3(S, B, full);
     __syncthreads();
+    full = false;
     for (int i = threadIdx.x; i < B * B; i += blockDim.x) out[(size_t)k * B * B + i] = S.logit[i];
     __syncthreads();
   }
+}
+
+// Builds the cache slot of block size B = 2 << blockIdx.x: a full pass over a
+// window of +1 ring spins (any window gives the same window-independent part).
+__global__ void __launch_bounds__(kInferThreads) k_nn_const(const __nv_bfloat16* __restrict__ w,
+                                                           __nv_bfloat16* __restrict__ w2t) {
+  extern __shared__ uint4 smem_raw[];
+  InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
+  const int B = 2 << blockIdx.x, F = frame_of(B);
+  load_weights(S, w, w2t, B, false);
+  build_var_lists(S, B);
+  for (int i = threadIdx.x; i < F * F; i += blockDim.x) S.win[i] = 1;
+  __syncthreads();
+  layer1(S, B, true);
+  __syncthreads();
+  layer2(S, B, true);
+  __syncthreads();
+  layer3(S, B, true);
+  __syncthreads();
+  uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<char*>(w2t) + kW2tBytes +
+                                        (size_t)cache_slot_of(B) * kCacheSlot);
+  const uint4* src = reinterpret_cast<const uint4*>(&S);
+  for (int i = threadIdx.x; i < (int)(kActBytes / 16); i += blockDim.x) dst[i] = src[i];
+  float* ldst = reinterpret_cast<float*>(reinterpret_cast<char*>(dst) + kActBytes);
+  for (int i = threadIdx.x; i < kMaxB * kMaxB; i += blockDim.x) ldst[i] = S.logit[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -669,7 +812,8 @@ int sms_of_current() {
 cudaError_t nn_alloc_weights(__nv_bfloat16** wbf, __nv_bfloat16** w2t) {
   cudaError_t e = cudaMalloc((void**)wbf, kNParams * sizeof(__nv_bfloat16));
   if (e) return e;
-  return cudaMalloc((void**)w2t, kC * kK2P * sizeof(__nv_bfloat16));
+  // re-laid-out W2, then the four activation-cache slots
+  return cudaMalloc((void**)w2t, kW2tBytes + 4 * kCacheSlot);
 }
 
 cudaError_t nn_load_blob(__nv_bfloat16* wbf, __nv_bfloat16* w2t, const void* host_blob,
@@ -678,6 +822,15 @@ cudaError_t nn_load_blob(__nv_bfloat16* wbf, __nv_bfloat16* w2t, const void* hos
                                   cudaMemcpyHostToDevice, s);
   if (e) return e;
   k_relayout<<<(kC * kK2P + 255) / 256, 256, 0, s>>>(wbf, w2t);
+  e = cudaGetLastError();
+  if (e) return e;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_nn_const, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)infer_smem());
+    if (e) return e;
+    attr = true;
+  }
+  k_nn_const<<<4, kInferThreads, infer_smem(), s>>>(wbf, w2t);
   e = cudaGetLastError();
   if (e) return e;
   return cudaStreamSynchronize(s);
@@ -707,7 +860,7 @@ cudaError_t nn_block_pass(uint32_t* planes, int L, int Wc, int B, uint32_t pass,
   P.stats = stats;
   const int n_blocks = (L / B) * (L / B) / 2;
   const int grid = std::max(1, std::min(n_blocks, 2 * sms_of_current()));
-  k_nn_block_pass<<<grid, kThreads, infer_smem(), s>>>(P, wbf, w2t);
+  k_nn_block_pass<<<grid, kInferThreads, infer_smem(), s>>>(P, wbf, w2t);
   return cudaGetLastError();
 }
 
@@ -740,7 +893,7 @@ cudaError_t nn_batch_block_pass(uint32_t* spins, const long long* off, const int
   P.rng = rng;
   P.stats = stats;
   const long long g = std::min<long long>(total_units, 2LL * sms_of_current());
-  k_nn_batch_block_pass<<<(int)std::max<long long>(g, 1), kThreads, infer_smem(), s>>>(P, wbf, w2t);
+  k_nn_batch_block_pass<<<(int)std::max<long long>(g, 1), kInferThreads, infer_smem(), s>>>(P, wbf, w2t);
   return cudaGetLastError();
 }
 
@@ -830,7 +983,7 @@ int ising_nn_logits(ising_nn* n, const int8_t* dev_windows, int count, float* de
   if (!n || (count > 0 && (!dev_windows || !dev_logits))) return nfail(ISING_EINVAL, "bad arguments");
   if (count <= 0) return ISING_OK;
   const int grid = std::max(1, std::min(count, 2 * sms_of_current()));
-  k_nn_logits<<<grid, kThreads, infer_smem(), n->stream>>>(dev_windows, count, n->B, n->wbf,
+  k_nn_logits<<<grid, kInferThreads, infer_smem(), n->stream>>>(dev_windows, count, n->B, n->wbf,
                                                            n->w2t, dev_logits);
   NTRY(cudaGetLastError());
   set_last_error("");
