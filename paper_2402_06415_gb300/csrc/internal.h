@@ -39,6 +39,27 @@ struct RngParams {
   uint32_t rk0[10], rk1[10];
 };
 
+// Unsigned 32-bit division by a divisor fixed per launch, as a multiply-high, an
+// add and a shift (Granlund & Montgomery, PLDI 1994, the round-up method):
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(m, n) + n) >> l,
+// exact for every 32-bit n and d >= 1.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while (((uint64_t)1 << l) < d) ++l;
+  const uint64_t m = ((((uint64_t)1 << l) - d) << 32) / d + 1;
+  return FastDiv{d, (uint32_t)m, l};
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return (uint32_t)(((uint64_t)__umulhi(f.m, n) + n) >> f.l);
+}
+#endif
+
 inline RngParams make_rng(uint64_t seed, uint32_t replica, uint32_t t4, uint32_t t8) {
   RngParams p;
   p.key0 = (uint32_t)(seed & 0xffffffffu);

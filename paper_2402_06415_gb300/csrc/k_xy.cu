@@ -91,7 +91,10 @@ __device__ __forceinline__ double own_exp(double x) {
   p = fma(p, r, 0.5);
   p = fma(p, r, 1.0);
   p = fma(p, r, 1.0);
-  return ldexp(p, (int)k);
+  // p 2^k with 2^k built from its exponent field (k in [-1010, 0], a normal
+  // number): a multiplication by a power of two is exact, or correctly rounded
+  // when the product is subnormal, i.e. the same result as ldexp
+  return p * __longlong_as_double((long long)((int)k + 1023) << 52);
 }
 
 // ---- own elementary functions (float) ----
@@ -136,7 +139,8 @@ __device__ __forceinline__ float own_exp(float x) {
   p = fmaf(p, r, 0.5f);
   p = fmaf(p, r, 1.0f);
   p = fmaf(p, r, 1.0f);
-  return ldexpf(p, (int)k);
+  // p 2^k, 2^k from its exponent field (k in [-126, 0]): same result as ldexpf
+  return p * __int_as_float(((int)k + 127) << 23);
 }
 
 template <typename T> __device__ __forceinline__ T two_pi();
@@ -200,18 +204,18 @@ __device__ __forceinline__ void st_state(V* p, V v) {
 template <typename T, bool CG>
 __device__ __forceinline__ unsigned int xy_pair(typename Vec<T>::type* __restrict__ own,
                                                 const typename Vec<T>::type* __restrict__ oth, int L,
-                                                long long nk, long long b, int c, uint32_t t, T beta,
-                                                const RngParams& rng) {
+                                                uint32_t nk, uint32_t b, int c, uint32_t t, T beta,
+                                                const RngParams& rng, const FastDiv& fh) {
   using V = typename Vec<T>::type;
   const int half = L / 2;
   unsigned int acc = 0;
-  const uint4 r = philox10_rk(make_uint4((uint32_t)b, t, rng.replica, (kTagXYMet << 16) | ((uint32_t)c << 8)),
+  const uint4 r = philox10_rk(make_uint4(b, t, rng.replica, (kTagXYMet << 16) | ((uint32_t)c << 8)),
                               rng.rk0, rng.rk1);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const long long k = 2 * b + h;
+    const uint32_t k = 2 * b + h;
     if (k >= nk) break;
-    const int y = (int)(k / half), j = (int)(k - (k / half) * half);
+    const int y = (int)fdiv(k, fh), j = (int)(k - (uint32_t)y * (uint32_t)half);
     const int o = (y + c) & 1;  // x = 2 j + o
     const int jr = o == 0 ? j : (j + 1 == half ? 0 : j + 1);   // x + 1
     const int jl = o == 0 ? (j == 0 ? half - 1 : j - 1) : j;   // x - 1
@@ -254,16 +258,15 @@ __device__ __forceinline__ void add_accepted(unsigned long long* accepted, unsig
 // k = 2b and 2b + 1.
 template <typename T>
 __global__ void __launch_bounds__(256) k_xy_half(typename Vec<T>::type* __restrict__ u, int L,
-                                                 int c, uint32_t t, T beta, RngParams rng,
+                                                 int c, uint32_t t, T beta, RngParams rng, FastDiv fh,
                                                  unsigned long long* __restrict__ accepted) {
   const int half = L / 2;
-  const long long nk = (long long)L * half;
+  const uint32_t nk = (uint32_t)L * (uint32_t)half;  // < 2^29 for L <= 32768
   typename Vec<T>::type* own = u + (size_t)c * L * half;
   const typename Vec<T>::type* oth = u + (size_t)(1 - c) * L * half;
   unsigned int acc = 0;
-  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * b < nk;
-       b += (long long)gridDim.x * blockDim.x)
-    acc += xy_pair<T, false>(own, oth, L, nk, b, c, t, beta, rng);
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; 2 * b < nk; b += gridDim.x * blockDim.x)
+    acc += xy_pair<T, false>(own, oth, L, nk, b, c, t, beta, rng, fh);
   add_accepted(accepted, acc);
 }
 
@@ -272,16 +275,15 @@ __global__ void __launch_bounds__(256) k_xy_half(typename Vec<T>::type* __restri
 // in double and added to out3 by one atomic per warp.
 template <typename T, bool CG>
 __device__ __forceinline__ void xy_measure_part(const typename Vec<T>::type* __restrict__ u, int L,
-                                                double* __restrict__ out3) {
+                                                double* __restrict__ out3, const FastDiv& fh) {
   using V = typename Vec<T>::type;
   const int half = L / 2;
-  const long long nk = (long long)L * half;
+  const uint32_t nk = (uint32_t)L * (uint32_t)half;
   const V* p0 = u;
   const V* p1 = u + (size_t)L * half;
   double e = 0, mx = 0, my = 0;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nk;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(k / half), j = (int)(k - (k / half) * half);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nk; k += gridDim.x * blockDim.x) {
+    const int y = (int)fdiv(k, fh), j = (int)(k - (uint32_t)y * (uint32_t)half);
     const int o = y & 1;
     const int jr = o == 0 ? j : (j + 1 == half ? 0 : j + 1);
     const int jl = o == 0 ? (j == 0 ? half - 1 : j - 1) : j;
@@ -310,8 +312,8 @@ __device__ __forceinline__ void xy_measure_part(const typename Vec<T>::type* __r
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_xy_measure(const typename Vec<T>::type* __restrict__ u,
-                                                    int L, double* __restrict__ out3) {
-  xy_measure_part<T, false>(u, L, out3);
+                                                    int L, double* __restrict__ out3, FastDiv fh) {
+  xy_measure_part<T, false>(u, L, out3, fh);
 }
 
 // Persistent form for small lattices: n sweeps (from sweep t0) in one launch,
@@ -337,10 +339,10 @@ __global__ void __launch_bounds__(PM == kGrid ? 256 : 1024) k_xy_persist(typenam
                                                     double* __restrict__ rec, long long rec0,
                                                     long long rec_cap,
                                                     unsigned long long* __restrict__ accepted,
-                                                    GridCtl* ctl, long long limit) {
+                                                    GridCtl* ctl, long long limit, FastDiv fh) {
   using V = typename Vec<T>::type;
   const int half = L / 2;
-  const long long nk = (long long)L * half;
+  const uint32_t nk = (uint32_t)L * (uint32_t)half;
   unsigned int acc = 0;
   long long ri = rec0;
   for (int s = 0; s < n; ++s) {
@@ -351,14 +353,13 @@ __global__ void __launch_bounds__(PM == kGrid ? 256 : 1024) k_xy_persist(typenam
     for (int c = 0; c < 2 && ok; ++c) {
       V* own = u + (size_t)c * L * half;
       const V* oth = u + (size_t)(1 - c) * L * half;
-      for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * b < nk;
-           b += (long long)gridDim.x * blockDim.x)
-        acc += xy_pair<T, PM != kOneCTA>(own, oth, L, nk, b, c, t, beta, rng);
+      for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; 2 * b < nk; b += gridDim.x * blockDim.x)
+        acc += xy_pair<T, PM != kOneCTA>(own, oth, L, nk, b, c, t, beta, rng, fh);
       if (meas && c == 1 && blockIdx.x == 0 && threadIdx.x == 0) slot[0] = slot[1] = slot[2] = 0.0;
       ok = persist_sync<PM>(ctl, limit);
     }
     if (ok && meas) {
-      xy_measure_part<T, PM != kOneCTA>(u, L, slot);
+      xy_measure_part<T, PM != kOneCTA>(u, L, slot, fh);
       ++ri;
       ok = persist_sync<PM>(ctl, limit);
     }
@@ -489,7 +490,8 @@ cudaError_t xy_persist_t(ising_xy* x, int n, int m) {
   unsigned long long* acc = x->accepted;
   GridCtl* ctl = x->ctl;
   RngParams r = rng;
-  void* args[] = {&u, &L, &beta, &r, &t0, &n, &m, &rec, &rec0, &cap, &acc, &ctl, &limit};
+  FastDiv fh = make_fastdiv((uint32_t)(x->L / 2));
+  void* args[] = {&u, &L, &beta, &r, &t0, &n, &m, &rec, &rec0, &cap, &acc, &ctl, &limit, &fh};
   if (pm == kOneCTA) {
     e = cudaLaunchKernel(fn, dim3(1), dim3(threads), args, 0, x->stream);
   } else if (pm == kCluster) {
@@ -528,7 +530,7 @@ cudaError_t xy_sweep_t(ising_xy* x, int n, int m) {
     const uint32_t t = (uint32_t)(x->sweep + s);
     for (int c = 0; c < 2; ++c) {
       k_xy_half<T><<<grid_of(blocks), 256, 0, x->stream>>>((V*)x->u, x->L, c, t, (T)x->beta, rng,
-                                                            x->accepted);
+                                                            make_fastdiv((uint32_t)(x->L / 2)), x->accepted);
       cudaError_t e = cudaGetLastError();
       if (e) return e;
       ++x->launches;
@@ -537,8 +539,8 @@ cudaError_t xy_sweep_t(ising_xy* x, int n, int m) {
       double* slot = x->rec + 3 * (x->rec_count % kXYRec);
       cudaError_t e = cudaMemsetAsync(slot, 0, 3 * sizeof(double), x->stream);
       if (e) return e;
-      k_xy_measure<T><<<grid_of((long long)x->L * (x->L / 2)), 256, 0, x->stream>>>((const V*)x->u,
-                                                                                 x->L, slot);
+      k_xy_measure<T><<<grid_of((long long)x->L * (x->L / 2)), 256, 0, x->stream>>>(
+          (const V*)x->u, x->L, slot, make_fastdiv((uint32_t)(x->L / 2)));
       e = cudaGetLastError();
       if (e) return e;
       ++x->launches;

@@ -41,6 +41,7 @@ struct FixTables {
   int n_accept;
   uint32_t K;
   int F;
+  FastDiv fh;              // division by L / 2
 };
 
 __global__ void k_xyfix_init(int32_t* __restrict__ kp, int L, uint32_t K, RngParams rng) {
@@ -74,18 +75,18 @@ __device__ __forceinline__ void st_k(int32_t* p, int32_t v) {
 // number accepted.
 template <bool CG>
 __device__ __forceinline__ unsigned int xyfix_pair(int32_t* __restrict__ own, const int32_t* __restrict__ oth,
-                                                   int L, long long nk, long long b, int c, uint32_t t,
+                                                   int L, uint32_t nk, uint32_t b, int c, uint32_t t,
                                                    const RngParams& rng, const FixTables& tb) {
   const int half = L / 2;
   const long long round_half = 1LL << (tb.F - 1);
   unsigned int acc = 0;
-  const uint4 r = philox10_rk(make_uint4((uint32_t)b, t, rng.replica, (kTagXYFixMet << 16) | ((uint32_t)c << 8)),
+  const uint4 r = philox10_rk(make_uint4(b, t, rng.replica, (kTagXYFixMet << 16) | ((uint32_t)c << 8)),
                               rng.rk0, rng.rk1);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const long long j = 2 * b + h;
+    const uint32_t j = 2 * b + h;
     if (j >= nk) break;
-    const int y = (int)(j / half), jj = (int)(j - (j / half) * half);
+    const int y = (int)fdiv(j, tb.fh), jj = (int)(j - (uint32_t)y * (uint32_t)half);
     const int o = (y + c) & 1;
     const int jr = o == 0 ? jj : (jj + 1 == half ? 0 : jj + 1);
     const int jl = o == 0 ? (jj == 0 ? half - 1 : jj - 1) : jj;
@@ -126,12 +127,11 @@ __global__ void __launch_bounds__(256) k_xyfix_half(int32_t* __restrict__ kp, in
                                                     RngParams rng, FixTables tb,
                                                     unsigned long long* __restrict__ accepted) {
   const int half = L / 2;
-  const long long nk = (long long)L * half;
+  const uint32_t nk = (uint32_t)L * (uint32_t)half;
   int32_t* own = kp + (size_t)c * L * half;
   const int32_t* oth = kp + (size_t)(1 - c) * L * half;
   unsigned int acc = 0;
-  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * b < nk;
-       b += (long long)gridDim.x * blockDim.x)
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; 2 * b < nk; b += gridDim.x * blockDim.x)
     acc += xyfix_pair<false>(own, oth, L, nk, b, c, t, rng, tb);
   fix_add_accepted(accepted, acc);
 }
@@ -141,15 +141,14 @@ __global__ void __launch_bounds__(256) k_xyfix_half(int32_t* __restrict__ kp, in
 template <bool CG>
 __device__ __forceinline__ void xyfix_measure_part(const int32_t* __restrict__ kp, int L,
                                                    const int2* __restrict__ trig,
-                                                   unsigned long long* __restrict__ out3) {
+                                                   unsigned long long* __restrict__ out3, const FastDiv& fh) {
   const int half = L / 2;
-  const long long nk = (long long)L * half;
+  const uint32_t nk = (uint32_t)L * (uint32_t)half;
   const int32_t* p0 = kp;
   const int32_t* p1 = kp + (size_t)L * half;
   long long e = 0, mx = 0, my = 0;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nk;
-       j += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(j / half), jj = (int)(j - (j / half) * half);
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nk; j += gridDim.x * blockDim.x) {
+    const int y = (int)fdiv(j, fh), jj = (int)(j - (uint32_t)y * (uint32_t)half);
     const int o = y & 1;
     const int jr = o == 0 ? jj : (jj + 1 == half ? 0 : jj + 1);
     const int jl = o == 0 ? (jj == 0 ? half - 1 : jj - 1) : jj;
@@ -176,8 +175,8 @@ __device__ __forceinline__ void xyfix_measure_part(const int32_t* __restrict__ k
 
 __global__ void __launch_bounds__(256) k_xyfix_measure(const int32_t* __restrict__ kp, int L,
                                                        const int2* __restrict__ trig,
-                                                       unsigned long long* __restrict__ out3) {
-  xyfix_measure_part<false>(kp, L, trig, out3);
+                                                       unsigned long long* __restrict__ out3, FastDiv fh) {
+  xyfix_measure_part<false>(kp, L, trig, out3, fh);
 }
 
 // Persistent form for small lattices (as for the floating-point XY kernel): n
@@ -201,7 +200,7 @@ __global__ void __launch_bounds__(PM == 2 ? 256 : 1024) k_xyfix_persist(int32_t*
                                                        unsigned long long* __restrict__ accepted,
                                                        GridCtl* ctl, long long limit) {
   const int half = L / 2;
-  const long long nk = (long long)L * half;
+  const uint32_t nk = (uint32_t)L * (uint32_t)half;
   unsigned int acc = 0;
   long long ri = rec0;
   for (int s = 0; s < n; ++s) {
@@ -212,14 +211,13 @@ __global__ void __launch_bounds__(PM == 2 ? 256 : 1024) k_xyfix_persist(int32_t*
     for (int c = 0; c < 2 && ok; ++c) {
       int32_t* own = kp + (size_t)c * L * half;
       const int32_t* oth = kp + (size_t)(1 - c) * L * half;
-      for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * b < nk;
-           b += (long long)gridDim.x * blockDim.x)
+      for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; 2 * b < nk; b += gridDim.x * blockDim.x)
         acc += xyfix_pair<PM != 0>(own, oth, L, nk, b, c, t, rng, tb);
       if (meas && c == 1 && blockIdx.x == 0 && threadIdx.x == 0) slot[0] = slot[1] = slot[2] = 0ull;
       ok = fix_sync<PM>(ctl, limit);
     }
     if (ok && meas) {
-      xyfix_measure_part<PM != 0>(kp, L, tb.trig, slot);
+      xyfix_measure_part<PM != 0>(kp, L, tb.trig, slot, tb.fh);
       ++ri;
       ok = fix_sync<PM>(ctl, limit);
     }
@@ -382,7 +380,7 @@ int ising_xyfix_sweep(ising_xyfix* x, int n_sweeps, int measure_every) {
   if (x->sweep + n_sweeps >= ((int64_t)1 << 32)) return ffail(ISING_EINVAL, "sweep counter overflow");
   NvtxRange nvtx("ising_xyfix_sweep");
   const RngParams rng = make_rng(x->seed, 0, 0, 0);
-  const FixTables tb{x->trig, x->accept, x->n_accept, x->K, x->F};
+  const FixTables tb{x->trig, x->accept, x->n_accept, x->K, x->F, make_fastdiv((uint32_t)(x->L / 2))};
   if (x->mode == 2 || (x->mode == 0 && x->L <= kFixPersistMaxL)) {
     if (n_sweeps == 0) return ISING_OK;
     int dev = 0, sms = 0;
@@ -446,7 +444,7 @@ int ising_xyfix_sweep(ising_xyfix* x, int n_sweeps, int measure_every) {
       unsigned long long* slot = x->rec + 3 * (x->rec_count % kFixRec);
       FTRY(cudaMemsetAsync(slot, 0, 3 * sizeof(unsigned long long), x->stream));
       k_xyfix_measure<<<fgrid((long long)x->L * (x->L / 2)), 256, 0, x->stream>>>(x->kp, x->L, x->trig,
-                                                                                   slot);
+                                                                                   slot, tb.fh);
       FTRY(cudaGetLastError());
       ++x->launches;
       ++x->rec_count;

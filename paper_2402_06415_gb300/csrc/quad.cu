@@ -43,6 +43,7 @@ constexpr int kMaxClasses = 25;
 
 struct QuadGeom {
   int Lc, Wq, nlast;  // nlast: valid bits of a row's last word (1..32)
+  FastDiv fw;         // division by Wq
 };
 
 // Decision table of one (lattice, beta, J1, J2): class c = a1 (z2 + 1) + a2.
@@ -142,7 +143,7 @@ __device__ __forceinline__ void quad_word(uint32_t* __restrict__ planes, const Q
                                           long long i, uint32_t t, const RngParams& rng, const QuadTable& tab) {
   constexpr int Z2 = LAT == ISING_QUAD_SQUARE ? 4 : 1;
   constexpr int Z1 = LAT == ISING_QUAD_SQUARE ? 4 : 2;
-  const int Y = (int)(i / g.Wq), w = (int)(i - (long long)Y * g.Wq);
+  const int Y = (int)fdiv((uint32_t)i, g.fw), w = (int)((uint32_t)i - (uint32_t)Y * (uint32_t)g.Wq);
   uint32_t* own = planes + (size_t)q * g.Lc * g.Wq + i;
   const uint32_t me = *own;
   const uint32_t valid = valid_bits(g, w);
@@ -219,7 +220,7 @@ __device__ __forceinline__ void quad_measure_word(const uint32_t* __restrict__ p
   const long long words = (long long)g.Lc * g.Wq;
   const int q = (int)(i / words);
   const long long gi = i - (long long)q * words;
-  const int Y = (int)(gi / g.Wq), w = (int)(gi - (long long)Y * g.Wq);
+  const int Y = (int)fdiv((uint32_t)gi, g.fw), w = (int)((uint32_t)gi - (uint32_t)Y * (uint32_t)g.Wq);
   const uint32_t v = valid_bits(g, w);
   const uint32_t me = planes[i];
   Count3 n1, n2;
@@ -472,6 +473,7 @@ int ising_quad_create(ising_quad** out, int lattice, int Lc, double beta, double
   x->geom.Lc = Lc;
   x->geom.Wq = (Lc + 31) / 32;
   x->geom.nlast = Lc - 32 * (x->geom.Wq - 1);
+  x->geom.fw = make_fastdiv((uint32_t)x->geom.Wq);
   x->beta = beta;
   x->J1 = J1;
   x->J2 = J2;

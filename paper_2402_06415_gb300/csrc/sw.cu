@@ -79,7 +79,8 @@ __global__ void k_sw_init(uint32_t* __restrict__ parent, long long N) {
 // the four words of one Philox block.
 __global__ void __launch_bounds__(256) k_sw_bonds(const uint32_t* __restrict__ planes, int L,
                                                   int Wc, uint32_t step, uint32_t thr,
-                                                  RngParams rng, uint32_t* __restrict__ parent) {
+                                                  RngParams rng, uint32_t* __restrict__ parent,
+                                                  FastDiv fL) {
   const long long N = (long long)L * L;
   for (long long pr = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * pr < N;
        pr += (long long)gridDim.x * blockDim.x) {
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(256) k_sw_bonds(const uint32_t* __restrict__ p
     for (int h = 0; h < 2; ++h) {
       const long long a = 2 * pr + h;
       if (a >= N) break;
-      const int y = (int)(a / L), x = (int)(a - (a / L) * L);
+      const int y = (int)fdiv((uint32_t)a, fL), x = (int)((uint32_t)a - (uint32_t)y * (uint32_t)L);
       const int sa = bit_at(planes, L, Wc, x, y);
 #pragma unroll
       for (int dir = 0; dir < 2; ++dir) {
@@ -123,14 +124,14 @@ __global__ void k_sw_roots(uint32_t* __restrict__ parent, long long N, uint32_t 
 
 // One thread per packed word: XOR in the flips of its sites' clusters.
 __global__ void k_sw_apply(uint32_t* __restrict__ planes, int L, int Wc,
-                           const uint32_t* __restrict__ parent, const uint8_t* __restrict__ flip) {
+                           const uint32_t* __restrict__ parent, const uint8_t* __restrict__ flip,
+                           FastDiv fplane, FastDiv fwc) {
   const int n = L / 2;
-  const long long words = 2LL * L * Wc;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / ((long long)L * Wc));
-    const long long rem = i - (long long)c * L * Wc;
-    const int y = (int)(rem / Wc), w = (int)(rem - (rem / Wc) * Wc);
+  const uint32_t words = 2u * (uint32_t)L * (uint32_t)Wc;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) {
+    const int c = (int)fdiv(i, fplane);
+    const uint32_t rem = i - (uint32_t)c * fplane.d;
+    const int y = (int)fdiv(rem, fwc), w = (int)(rem - (uint32_t)y * (uint32_t)Wc);
     uint32_t mask = 0;
     for (int b = 0; b < 32; ++b) {
       const int j = 32 * w + b;
@@ -289,16 +290,17 @@ __global__ void k_sw_resolve(uint32_t* __restrict__ parent, uint8_t* __restrict_
 // a ballot assembles the flip mask (independent gathers in flight per lane).
 __global__ void __launch_bounds__(256) k_sw_apply2(uint32_t* __restrict__ planes, int L, int Wc,
                                                    const uint32_t* __restrict__ parent,
-                                                   const uint8_t* __restrict__ coin) {
+                                                   const uint8_t* __restrict__ coin, FastDiv fplane,
+                                                   FastDiv fwc) {
   const int n = L / 2;
-  const long long words = 2LL * L * Wc;
+  const uint32_t words = 2u * (uint32_t)L * (uint32_t)Wc;
   const int lane = threadIdx.x & 31;
-  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long i = warp0; i < words; i += nwarps) {
-    const int c = (int)(i / ((long long)L * Wc));
-    const long long rem = i - (long long)c * L * Wc;
-    const int y = (int)(rem / Wc), w = (int)(rem - (rem / Wc) * Wc);
+  const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i = warp0; i < words; i += nwarps) {
+    const int c = (int)fdiv(i, fplane);
+    const uint32_t rem = i - (uint32_t)c * fplane.d;
+    const int y = (int)fdiv(rem, fwc), w = (int)(rem - (uint32_t)y * (uint32_t)Wc);
     const int j = 32 * w + lane;
     bool f = false;
     if (j < n) {
@@ -375,20 +377,25 @@ cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
     k_sw_resolve<<<grid_of(N), 256, 0, s>>>(parent, flip, N, step, rng);
     e = cudaGetLastError();
     if (e) return e;
-    k_sw_apply2<<<grid_of(2LL * lat.L * lat.Wc * 32), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, parent, flip);
+    k_sw_apply2<<<grid_of(2LL * lat.L * lat.Wc * 32), 256, 0, s>>>(
+        lat.planes, lat.L, lat.Wc, parent, flip, make_fastdiv((uint32_t)lat.L * (uint32_t)lat.Wc),
+        make_fastdiv((uint32_t)lat.Wc));
     return cudaGetLastError();
   } else {
     k_sw_init<<<grid_of(N), 256, 0, s>>>(parent, N);
     e = cudaGetLastError();
     if (e) return e;
-    k_sw_bonds<<<grid_of((N + 1) / 2), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent);
+    k_sw_bonds<<<grid_of((N + 1) / 2), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
+                                                    make_fastdiv((uint32_t)lat.L));
     e = cudaGetLastError();
     if (e) return e;
   }
   k_sw_roots<<<grid_of(N), 256, 0, s>>>(parent, N, step, rng, flip);
   e = cudaGetLastError();
   if (e) return e;
-  k_sw_apply<<<grid_of(2LL * lat.L * lat.Wc), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, parent, flip);
+  k_sw_apply<<<grid_of(2LL * lat.L * lat.Wc), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, parent, flip,
+                                                            make_fastdiv((uint32_t)lat.L * (uint32_t)lat.Wc),
+                                                            make_fastdiv((uint32_t)lat.Wc));
   return cudaGetLastError();
 }
 
