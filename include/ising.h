@@ -213,8 +213,8 @@ int ising_batch_create(ising_batch** out, int n_ladders, const int* L, int n_bet
 int ising_batch_seed(ising_batch* b, uint64_t seed);
 
 /* Work decomposition: replica words per work item (16..16384, default 512),
- * threads per CTA (128 or 256; 0 = 256), grid (0 = all resident CTAs).  Never
- * changes results.  Drops a captured graph. */
+ * threads per CTA (32, 64, 128 or 256; 0 = 256), grid (0 = all resident CTAs).
+ * Never changes results.  Drops a captured graph. */
 int ising_batch_set_kernel(ising_batch* b, int words_per_item, int threads, int grid);
 
 /* Keep E, M and the slot of every replica at each exchange step in a device

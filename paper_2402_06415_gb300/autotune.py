@@ -140,7 +140,7 @@ def tune_batch(Ls, betas, pt_every: int, sweeps: int = 100, reps: int = 2,
             cache = {}
         if key in cache:
             return cache[key]
-    cands = cands or [(w, t) for w in (128, 256, 512, 1024, 2048) for t in (128, 256)]
+    cands = cands or [(w, t) for w in (64, 128, 256, 512, 1024) for t in (32, 64, 128, 256)]
     table = []
     st = torch.cuda.current_stream()
     with B.Batch(Ls, betas, pt_every, stream=st, seed=1) as b:

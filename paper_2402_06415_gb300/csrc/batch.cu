@@ -71,6 +71,7 @@ struct BatchDev {
   BatchCounters* ctr;
   int n_ladders, n_beta, pt_every;
   uint32_t key0, key1;
+  uint32_t rk0[10], rk1[10];  // Philox round keys of (key0, key1)
   long long spin_limit;  // clock64 cycles a barrier may wait
 };
 
@@ -115,17 +116,21 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
     s_ones[qq] = 0u;
   }
   __syncthreads();
+  // Sweeps: the CTA's threads cover the item's words of one colour, then a CTA
+  // barrier.  (Warp-owned replicas with only __syncwarp() between half sweeps
+  // measured slower: too few resident warps per SM for this many replicas.)
   const int lane = threadIdx.x & 31;
   const int words = nr * plane;
+  const FastDiv fplane = make_fastdiv((uint32_t)plane), fwc = make_fastdiv((uint32_t)Wc);
   for (int s = 0; s < ns; ++s) {
     const uint32_t t = t0 + (uint32_t)s;
     for (int c = 0; c < 2; ++c) {
       for (int b0 = threadIdx.x & ~31; b0 < words; b0 += blockDim.x) {
         const int idx = b0 + lane;
         const bool active = idx < words;
-        const int qq = active ? idx / plane : 0;
+        const int qq = active ? (int)fdiv((uint32_t)idx, fplane) : 0;
         const int rem = active ? idx - qq * plane : 0;
-        const int y = rem / Wc, w = rem - (rem / Wc) * Wc;
+        const int y = (int)fdiv((uint32_t)rem, fwc), w = rem - y * Wc;
         uint32_t* So = sm + qq * per_rep + c * plane;
         const uint32_t* Sn = sm + qq * per_rep + (1 - c) * plane;
         const uint32_t* rm = Sn + y * Wc;
@@ -136,8 +141,8 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
         const uint32_t side = side_word([rm](int ww) { return rm[ww]; }, w, Wc, n, (y + c) & 1);
         const uint32_t valid = active ? valid_mask(w, Wc, n) : 0u;
         const Classes k = classify(sv, up, dn, mid, side);
-        const uint32_t f = flip_mask(k, valid, (uint32_t)(y * Wc + w), t, (uint32_t)(r0 + qq),
-                                     (uint32_t)c, d.key0, d.key1, s_t4[qq], s_t8[qq]);
+        const uint32_t f = flip_mask_rk(k, valid, (uint32_t)(y * Wc + w), t, (uint32_t)(r0 + qq),
+                                        (uint32_t)c, d.rk0, d.rk1, s_t4[qq], s_t8[qq]);
         if (active) So[y * Wc + w] = sv ^ f;
       }
       __syncthreads();
@@ -468,6 +473,13 @@ BatchDev dev_view(const ising_batch* b) {
   d.pt_every = b->pt_every;
   d.key0 = (uint32_t)(b->seed & 0xffffffffu);
   d.key1 = (uint32_t)(b->seed >> 32);
+  {
+    const RngParams rp = make_rng(b->seed, 0, 0, 0);
+    for (int r = 0; r < 10; ++r) {
+      d.rk0[r] = rp.rk0[r];
+      d.rk1[r] = rp.rk1[r];
+    }
+  }
   d.spin_limit = 4000000000ll;  // ~2 s at 2 GHz
   return d;
 }
@@ -595,8 +607,8 @@ int ising_batch_set_kernel(ising_batch* b, int words_per_item, int threads, int 
   if (int st = check_b(b)) return st;
   if (words_per_item < 16 || words_per_item > 16384)
     return bfail(ISING_EINVAL, "words_per_item must be in [16, 16384]");
-  if (threads != 0 && threads != 128 && threads != 256)
-    return bfail(ISING_EINVAL, "threads must be 128 or 256");
+  if (threads != 0 && threads != 32 && threads != 64 && threads != 128 && threads != 256)
+    return bfail(ISING_EINVAL, "threads must be 32, 64, 128 or 256");
   if (grid < 0) return bfail(ISING_EINVAL, "grid must be >= 0");
   BTRY(cudaStreamSynchronize(b->stream));
   b->words_per_item = words_per_item;

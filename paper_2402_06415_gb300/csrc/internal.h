@@ -47,7 +47,7 @@ struct FastDiv {
   uint32_t d, m, l;
 };
 
-inline FastDiv make_fastdiv(uint32_t d) {
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
   uint32_t l = 0;
   while (((uint64_t)1 << l) < d) ++l;
   const uint64_t m = ((((uint64_t)1 << l) - d) << 32) / d + 1;

@@ -117,6 +117,24 @@ __device__ __forceinline__ uint32_t flip_mask(const Classes& k, uint32_t valid, 
   return (k.ge2 & valid) | acc;
 }
 
+// flip_mask with the ten Philox round keys given (as philox10_rk).
+__device__ __forceinline__ uint32_t flip_mask_rk(const Classes& k, uint32_t valid, uint32_t g,
+                                                 uint32_t t, uint32_t rep, uint32_t colour,
+                                                 const uint32_t (&rk0)[10], const uint32_t (&rk1)[10],
+                                                 uint32_t t4, uint32_t t8) {
+  const uint32_t one = k.one & valid;
+  const uint32_t zero = k.zero & valid;
+  uint32_t D = one | zero;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if (!__any_sync(0xffffffffu, D != 0u)) break;
+    const uint4 r = philox10_rk(make_uint4(g, t, rep, ctr_w(kTagMet, colour, b)), rk0, rk1);
+    compare_block(r, b, t4, t8, one, zero, D, acc);
+  }
+  return (k.ge2 & valid) | acc;
+}
+
 // Valid-lane mask of word w when the colour row has n sites (n = L/2).
 __device__ __forceinline__ uint32_t valid_mask(int w, int Wc, int n) {
   if (w < Wc - 1) return 0xffffffffu;

@@ -39,7 +39,7 @@ SMALL_LS = [16, 24, 6, 32, 66]
 SMALL_BETAS = np.linspace(0.35, 0.5, 8)
 
 
-@pytest.mark.parametrize("kernel", [(512, 256), (16, 128), (4096, 256), (64, 256)])
+@pytest.mark.parametrize("kernel", [(512, 256), (16, 128), (4096, 256), (64, 256), (64, 32), (256, 64)])
 def test_batch_bit_exact_small(kernel):
     seed, n, pt = 11, 23, 5
     ref = oracle.run_ladders(SMALL_LS, SMALL_BETAS, seed, n, pt)
