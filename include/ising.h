@@ -308,7 +308,7 @@ int ising_sweep_blocks(ising_ctx* ctx, int n_sweeps, int measure_every, int bloc
  * iff bit 31 of word (m & 3) of Philox(m >> 2, n, replica, SW_FLIP << 16), m its
  * smallest site index.  Records E, M after every step n with
  * (n + 1) % measure_every == 0 into the same record ring as ising_sweep.  The
- * step counter n is separate from the sweep counter and starts at 0.  Allocates
+ * step counter n is separate from the sweep counter; ising_seed resets it to 0.  Allocates
  * 5 bytes per site of scratch on first use; L = 65536 (2^32 sites) is
  * rejected with ISING_EINVAL.  Async. */
 int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);

@@ -440,6 +440,7 @@ int ising_seed(ising_ctx* c, uint64_t seed) {
   c->seed = seed;
   c->sweep = 0;
   c->rec_count = 0;
+  c->sw_steps = 0;
   cudaError_t e;
   if (c->layout == ISING_LAYOUT_BITS) {
     c->cur = 0;

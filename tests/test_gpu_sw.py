@@ -86,6 +86,18 @@ def test_sw_large_lattice_one_step():
     assert np.array_equal(got, s)
 
 
+def test_sw_step_counter_resets_on_seed():
+    L, beta, seed = 64, 0.44, 21
+    with ising.Lattice(L, beta, seed=seed) as lat:
+        lat.sw_step(3)
+        lat.seed(seed)            # back to the seeded start, step counter 0
+        s = lat.spins()
+        lat.sw_step(2)
+        got = lat.spins()
+    oracle.sw_steps(s, beta, seed, 2)
+    assert np.array_equal(got, s)
+
+
 def test_sw_rejects_byte_layout():
     with ising.Lattice(8, 0.4, layout=ising.ISING_LAYOUT_I8) as lat:
         with pytest.raises(ising.IsingError):
