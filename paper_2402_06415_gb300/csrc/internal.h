@@ -37,6 +37,9 @@ struct RngParams {
   // Philox round keys key0 + r W0, key1 + r W1 (r = 0..9), filled by
   // make_rng(); passed by value so device code reads them as constants
   uint32_t rk0[10], rk1[10];
+  // per-plane threshold masks: tm4[k] = all ones iff bit 31 - k of t4 is set
+  // (likewise tm8), so the bit-serial compare reads them as constants
+  uint32_t tm4[32], tm8[32];
 };
 
 // Unsigned 32-bit division by a divisor fixed per launch, as a multiply-high, an
@@ -67,6 +70,10 @@ inline RngParams make_rng(uint64_t seed, uint32_t replica, uint32_t t4, uint32_t
   p.replica = replica;
   p.t4 = t4;
   p.t8 = t8;
+  for (int k = 0; k < 32; ++k) {
+    p.tm4[k] = ((t4 >> (31 - k)) & 1u) ? 0xffffffffu : 0u;
+    p.tm8[k] = ((t8 >> (31 - k)) & 1u) ? 0xffffffffu : 0u;
+  }
   for (int r = 0; r < 10; ++r) {
     p.rk0[r] = p.key0 + (uint32_t)r * 0x9E3779B9u;
     p.rk1[r] = p.key1 + (uint32_t)r * 0xBB67AE85u;

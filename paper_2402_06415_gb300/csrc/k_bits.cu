@@ -234,8 +234,7 @@ __device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int k = 4 * b + q;
-      const uint32_t m4 = 0u - ((rng.t4 >> (31 - k)) & 1u);
-      const uint32_t m8 = 0u - ((rng.t8 >> (31 - k)) & 1u);
+      const uint32_t m4 = rng.tm4[k], m8 = rng.tm8[k];
       const uint32_t tm = (cls & m4) | (~cls & m8);  // lane's threshold bit
       acc |= D & tm & ~p[q];                          // u bit 0 < T bit 1: accept
       D &= ~(tm ^ p[q]);                              // equal bits: still undecided
@@ -261,8 +260,7 @@ __device__ __forceinline__ void lazy_planes2(uint32_t ga, uint32_t gb, uint32_t 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int k = 4 * b + q;
-      const uint32_t m4 = 0u - ((rng.t4 >> (31 - k)) & 1u);
-      const uint32_t m8 = 0u - ((rng.t8 >> (31 - k)) & 1u);
+      const uint32_t m4 = rng.tm4[k], m8 = rng.tm8[k];
       const uint32_t ta = (clsa & m4) | (~clsa & m8);
       const uint32_t tb = (clsb & m4) | (~clsb & m8);
       acca |= Da & ta & ~pa[q];
