@@ -316,12 +316,19 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
     const int w0 = tx * TW;
     const int rows = Ty + 2 * H;
     constexpr int QROW = SP / 4;
-    for (int i = tid; i < 2 * rows * QROW; i += blockDim.x) {
-      const int c = i / (rows * QROW);
-      const int rem = i - c * rows * QROW;
+    const int per_colour = rows * QROW;
+    for (int i = tid; i < 2 * per_colour; i += blockDim.x) {
+      // no runtime division or modulo: one compare for the colour, constant
+      // divisor for the row, conditional wraps (|y0 - H + r| < 2L, |w| < 2 Wc)
+      const int c = i >= per_colour;
+      const int rem = i - c * per_colour;
       const int r = rem / QROW, q = rem - (rem / QROW) * QROW;
-      const int gy = wrap(y0 - H + r, L);
-      const int gw = wrap(w0 - 4 + 4 * q, Wc);
+      int gy = y0 - H + r;
+      gy += gy < 0 ? L : 0;
+      gy -= gy >= L ? L : 0;
+      int gw = w0 - 4 + 4 * q;
+      gw += gw < 0 ? Wc : 0;
+      gw -= gw >= Wc ? Wc : 0;
       const uint4 v =
           *reinterpret_cast<const uint4*>(in + (size_t)c * L * Wc + (size_t)gy * Wc + gw);
       reinterpret_cast<uint4*>(S + c * SR * SP + r * SP)[q] = v;
@@ -496,7 +503,7 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
     }
     constexpr int QIN = TW / 4;
     for (int i = tid; i < 2 * Ty * QIN; i += blockDim.x) {
-      const int c = i / (Ty * QIN);
+      const int c = i >= Ty * QIN;
       const int rem = i - c * Ty * QIN;
       const int r = rem / QIN, q = rem - (rem / QIN) * QIN;
       const uint4 v = reinterpret_cast<const uint4*>(S + c * SR * SP + (H + r) * SP + 4)[q];
