@@ -52,6 +52,7 @@ struct QuadTable {
   int n_vals;                 // distinct thresholds of the other classes
   uint32_t val[kMaxClasses];  // the thresholds
   uint32_t cls[kMaxClasses];  // bitset of the classes holding val[d]
+  uint32_t lm[kMaxClasses][32];  // all ones iff bit 31 - k of val[d] is set
 };
 
 struct Count3 {  // bit-sliced 3-bit counter per lane (counts 0..4)
@@ -138,15 +139,19 @@ __device__ __forceinline__ uint32_t valid_bits(const QuadGeom& g, int w) {
 }
 
 // Metropolis trials of the 32 sites of word i = Y Wq + w of sublattice q.
+// All 32 lanes of the warp call it together (warp vote); lanes past the end pass
+// active = false (any in-range i) and change nothing.
 template <int LAT, int NV, bool G>
 __device__ __forceinline__ void quad_word(uint32_t* __restrict__ planes, const QuadGeom& g, int q,
-                                          long long i, uint32_t t, const RngParams& rng, const QuadTable& tab) {
+                                          long long i, bool active, uint32_t t, const RngParams& rng,
+                                          const QuadTable& tab) {
   constexpr int Z2 = LAT == ISING_QUAD_SQUARE ? 4 : 1;
   constexpr int Z1 = LAT == ISING_QUAD_SQUARE ? 4 : 2;
+  if (!active) i = 0;
   const int Y = (int)fdiv((uint32_t)i, g.fw), w = (int)((uint32_t)i - (uint32_t)Y * (uint32_t)g.Wq);
   uint32_t* own = planes + (size_t)q * g.Lc * g.Wq + i;
   const uint32_t me = *own;
-  const uint32_t valid = valid_bits(g, w);
+  const uint32_t valid = active ? valid_bits(g, w) : 0u;
   Count3 n1, n2;
   count_anti<LAT, G>(planes, g, q, Y, w, me, n1, n2);
   uint32_t e2[Z2 + 1];
@@ -169,8 +174,11 @@ __device__ __forceinline__ void quad_word(uint32_t* __restrict__ planes, const Q
   }
   uint32_t und = ~always & valid, lt = 0;
   const uint32_t g_idx = (uint32_t)i;
-#pragma unroll 1
-  for (int m = 0; m < 8 && und; ++m) {
+  // planes block by block while any lane of the warp is undecided; the level is
+  // a compile-time index, so each threshold-bit mask is a constant operand
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    if (!__any_sync(0xffffffffu, und != 0u)) break;
     const uint4 r = philox10_rk(make_uint4(g_idx, t, rng.replica, (kTagQuadMet << 16) | ((uint32_t)q << 8) | (uint32_t)m),
                                 rng.rk0, rng.rk1);
     const uint32_t pw[4] = {r.x, r.y, r.z, r.w};
@@ -179,22 +187,23 @@ __device__ __forceinline__ void quad_word(uint32_t* __restrict__ planes, const Q
       const int lvl = 4 * m + k;
       uint32_t tm = 0;
 #pragma unroll
-      for (int d = 0; d < NV; ++d) tm |= vm[d] & (0u - ((tab.val[d] >> (31 - lvl)) & 1u));
+      for (int d = 0; d < NV; ++d) tm |= vm[d] & tab.lm[d][lvl];
       lt |= und & ~pw[k] & tm;
       und &= ~(pw[k] ^ tm);
     }
   }
   const uint32_t flip = (always | lt) & valid;
-  if (flip) *own = me ^ flip;
+  if (active && flip) *own = me ^ flip;
 }
 
 template <int LAT, int NV>
 __global__ void __launch_bounds__(256) k_quad_quarter(uint32_t* __restrict__ planes, QuadGeom g, int q,
                                                       uint32_t t, RngParams rng, QuadTable tab) {
   const long long words = (long long)g.Lc * g.Wq;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words;
-       i += (long long)gridDim.x * blockDim.x)
-    quad_word<LAT, NV, true>(planes, g, q, i, t, rng, tab);
+  const int lane = threadIdx.x & 31;
+  for (long long base = (blockIdx.x * (long long)blockDim.x + threadIdx.x) - lane; base < words;
+       base += (long long)gridDim.x * blockDim.x)
+    quad_word<LAT, NV, true>(planes, g, q, base + lane, base + lane < words, t, rng, tab);
 }
 
 __global__ void k_quad_init(uint32_t* __restrict__ planes, QuadGeom g, RngParams rng) {
@@ -269,7 +278,9 @@ __global__ void __launch_bounds__(1024) k_quad_persist(uint32_t* __restrict__ pl
   for (int s = 0; s < n; ++s) {
     const uint32_t t = t0 + (uint32_t)s;
     for (int q = 0; q < 4; ++q) {
-      for (long long i = threadIdx.x; i < words; i += blockDim.x) quad_word<LAT, NV, false>(sp, g, q, i, t, rng, tab);
+      for (long long base = threadIdx.x & ~31; base < words; base += blockDim.x)
+        quad_word<LAT, NV, false>(sp, g, q, base + (threadIdx.x & 31), base + (threadIdx.x & 31) < words, t,
+                                  rng, tab);
       __syncthreads();
     }
     if (meas_every > 0 && ((long long)t + 1) % meas_every == 0) {
@@ -352,6 +363,8 @@ bool build_table(int lattice, double beta, double J1, double J2, QuadTable* tab)
       }
       t.cls[d] |= 1u << c;
     }
+  for (int d = 0; d < t.n_vals; ++d)
+    for (int k = 0; k < 32; ++k) t.lm[d][k] = ((t.val[d] >> (31 - k)) & 1u) ? 0xffffffffu : 0u;
   *tab = t;
   return true;
 }

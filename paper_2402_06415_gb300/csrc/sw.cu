@@ -188,20 +188,26 @@ __global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __res
   __shared__ uint32_t lab[kTileSites];
   // per site: bit 0 spin, bit 1 bond li -> li + 1 active, bit 2 bond li -> li + TX
   // active (bonds inside the tile only)
-  __shared__ uint8_t st[kTileSites];
+  __shared__ __align__(16) uint8_t st[kTileSites];
   const int tiles_x = L / kTileX;
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
   const int x0 = tx * kTileX, y0 = ty * kTileY;
-  // spins: each thread unpacks whole words (TX / 64 words per colour per row)
+  // spins: one thread per (row, 64-site column block) reads the two colour
+  // words of the block and writes 64 spin bytes as 16 four-byte stores
   constexpr int kWordsRow = kTileX / 64;
-  for (int i = threadIdx.x; i < 2 * kTileY * kWordsRow; i += blockDim.x) {
-    const int c = i / (kTileY * kWordsRow), rem = i - c * (kTileY * kWordsRow);
-    const int ly = rem / kWordsRow, wi = rem - ly * kWordsRow;
+  for (int i = threadIdx.x; i < kTileY * kWordsRow; i += blockDim.x) {
+    const int ly = i / kWordsRow, wi = i - ly * kWordsRow;
     const int y = y0 + ly;
-    const uint32_t w = __ldg(&planes[(size_t)c * L * Wc + (size_t)y * Wc + (x0 >> 6) + wi]);
-    const int o = (y + c) & 1;  // x = 2 j + o
-#pragma unroll 4
-    for (int b = 0; b < 32; ++b) st[ly * kTileX + 2 * (32 * wi + b) + o] = (uint8_t)((w >> b) & 1u);
+    const int ce = y & 1;  // the colour whose sites sit at even x
+    const uint32_t we = __ldg(&planes[(size_t)ce * L * Wc + (size_t)y * Wc + (x0 >> 6) + wi]);
+    const uint32_t wo = __ldg(&planes[(size_t)(1 - ce) * L * Wc + (size_t)y * Wc + (x0 >> 6) + wi]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&st[ly * kTileX + 64 * wi]);
+#pragma unroll
+    for (int b = 0; b < 32; b += 2) {
+      // bytes x = 2b, 2b + 1, 2b + 2, 2b + 3: even, odd, even, odd sites
+      const uint32_t e = (we >> b) & 3u, o = (wo >> b) & 3u;
+      dst[b >> 1] = (e & 1u) | ((o & 1u) << 8) | ((e & 2u) << 15) | ((o & 2u) << 23);
+    }
   }
   __syncthreads();
   // inner bonds: one thread per site pair (one Philox block for its four bonds)
