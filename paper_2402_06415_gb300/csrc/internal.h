@@ -1,6 +1,7 @@
 // Internal launchers shared by the C-ABI layer (api.cu) and the kernel files.
 // Every launcher enqueues on `stream` and returns the launch status.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -40,6 +41,24 @@ struct RngParams {
   // per-plane threshold masks: tm4[k] = all ones iff bit 31 - k of t4 is set
   // (likewise tm8), so the bit-serial compare reads them as constants
   uint32_t tm4[32], tm8[32];
+};
+
+// Per-device memo for launch settings that CUDA keeps per device (a kernel's
+// dynamic shared-memory limit, its occupancy): one slot per device ordinal,
+// atomic so concurrent host threads may race on it harmlessly.
+struct DeviceCache {
+  static constexpr int kMaxDevices = 64;
+  std::atomic<long long> v[kMaxDevices];
+  DeviceCache() {
+    for (auto& x : v) x.store(0);
+  }
+  static int device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d >= 0 && d < kMaxDevices ? d : 0;
+  }
+  long long get() { return v[device()].load(std::memory_order_relaxed); }
+  void set(long long x) { v[device()].store(x, std::memory_order_relaxed); }
 };
 
 // Unsigned 32-bit division by a divisor fixed per launch, as a multiply-high, an

@@ -656,28 +656,30 @@ static cudaError_t launch_tiled32_k(const BitsLattice& in, uint32_t* out, const 
                                     uint32_t sweep0, const RecordSlots& slots,
                                     unsigned long long* rec, int n_ty, int grid, cudaStream_t s) {
   const size_t smem = tiled32_smem_bytes(in.L, K, n_ty, 32 * TWW);
-  static size_t configured = 0;  // per instantiation
-  if (smem > configured) {
+  static DeviceCache configured;  // per instantiation and device
+  if ((long long)smem > configured.get()) {
     cudaError_t e = cudaFuncSetAttribute(k_tiled32_bits<K, TWW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    configured.set((long long)smem);
   }
   const int n_tiles = n_ty * (in.Wc / (32 * TWW));
   if (grid <= 0) {
-    static size_t occ_smem = 0;  // resident CTAs per SM, cached per shared-memory size
-    static int occ_grid = 0;
-    if (occ_smem != smem) {
+    // resident CTAs, cached per device as (shared-memory size << 20 | grid)
+    static DeviceCache occ;
+    const long long memo = occ.get();
+    if ((memo >> 20) == (long long)smem) {
+      grid = (int)(memo & 0xfffff);
+    } else {
       int per_sm = 0, dev = 0, sms = 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &per_sm, k_tiled32_bits<K, TWW>, 256, smem);
       if (e != cudaSuccess) return e;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      occ_grid = per_sm * sms;
-      occ_smem = smem;
+      grid = per_sm * sms;
+      occ.set(((long long)smem << 20) | (long long)grid);
     }
-    grid = occ_grid;
   }
   if (grid > n_tiles) grid = n_tiles;
   if (grid < 1) grid = 1;

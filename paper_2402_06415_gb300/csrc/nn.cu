@@ -824,11 +824,11 @@ cudaError_t nn_load_blob(__nv_bfloat16* wbf, __nv_bfloat16* w2t, const void* hos
   k_relayout<<<(kC * kK2P + 255) / 256, 256, 0, s>>>(wbf, w2t);
   e = cudaGetLastError();
   if (e) return e;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceCache attr;
+  if (!attr.get()) {
     e = cudaFuncSetAttribute(k_nn_const, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)infer_smem());
     if (e) return e;
-    attr = true;
+    attr.set(1);
   }
   k_nn_const<<<4, kInferThreads, infer_smem(), s>>>(wbf, w2t);
   e = cudaGetLastError();
@@ -841,12 +841,12 @@ size_t nn_blob_bytes() { return kNParams * sizeof(__nv_bfloat16); }
 cudaError_t nn_block_pass(uint32_t* planes, int L, int Wc, int B, uint32_t pass, int colour,
                           const RngParams& rng, double beta, const __nv_bfloat16* wbf,
                           const __nv_bfloat16* w2t, unsigned long long* stats, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static DeviceCache attr;
+  if (!attr.get()) {
     cudaError_t e = cudaFuncSetAttribute(k_nn_block_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)infer_smem());
     if (e) return e;
-    attr = true;
+    attr.set(1);
   }
   PassParams P;
   P.planes = planes;
@@ -870,13 +870,13 @@ cudaError_t nn_batch_block_pass(uint32_t* spins, const long long* off, const int
                                 int n_beta, int B, int colour, uint32_t pass, const RngParams& rng,
                                 const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
                                 unsigned long long* stats, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static DeviceCache attr;
+  if (!attr.get()) {
     cudaError_t e = cudaFuncSetAttribute(k_nn_batch_block_pass,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)infer_smem());
     if (e) return e;
-    attr = true;
+    attr.set(1);
   }
   BatchPassParams P;
   P.spins = spins;
