@@ -185,6 +185,26 @@ __global__ void k_xy_init(typename Vec<T>::type* __restrict__ u, int L, RngParam
   }
 }
 
+// The acceptance decision p < own_exp(x) (x = -beta dE < 0), decided first from
+// the hardware exponential __expf: its documented error on this range is at most
+// 2 + 1.173 |x| ulp (about 1e-5 relative for x >= -80), the rounding of x to
+// float adds at most |x| 2^-24 relative, so when p lies outside
+// e (1 -+ 1e-4) the exact own_exp gives the same answer and is skipped; inside
+// that band (rare), or for x < -80 with p = 0, own_exp decides.  For x < -80,
+// exp(x) < 2^-115 < p whenever p > 0 (p is a multiple of 2^-24).
+template <typename T>
+__device__ __forceinline__ bool accept_exp(T p, T x) {
+  if (x >= (T)-80) {
+    const float e = __expf((float)x);
+    const float pf = (float)p;  // exact: p = k 2^-24, k < 2^24
+    if (pf < e * 0.9999f) return true;
+    if (pf > e * 1.0001f) return false;
+  } else if (p > (T)0) {
+    return false;
+  }
+  return p < own_exp(x);
+}
+
 // Loads and stores of the state: plain in the one-launch-per-half-sweep
 // kernels; through L2 only (no L1) in the persistent kernel, whose CTAs read
 // what other SMs wrote after a grid barrier.
@@ -236,7 +256,7 @@ __device__ __forceinline__ unsigned int xy_pair(typename Vec<T>::type* __restric
     const T p = mul_rn<T>((T)(w2 >> 8), inv24<T>());
     V me = ld_state<CG>(own + k);
     const T dE = -fma(sub_rn<T>(cs, me.x), hx, mul_rn<T>(sub_rn<T>(sn, me.y), hy));
-    if (dE <= (T)0 || p < own_exp(mul_rn<T>(-beta, dE))) {
+    if (dE <= (T)0 || accept_exp<T>(p, mul_rn<T>(-beta, dE))) {
       me.x = cs;
       me.y = sn;
       st_state<CG>(own + k, me);
