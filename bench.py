@@ -38,7 +38,8 @@ BETAS = [0.40, 0.4406868, 0.50]
 SEED = 1
 
 # Tiled-kernel launch shape for L = 16384 (sweeps per launch, row strips,
-# words per tile row); chosen by the tuning sweep recorded in the design doc.
+# words per tile row): the best shape of an autotuning sweep on GB300, used when
+# the autotuner is switched off.
 BENCH_KERNEL = {"kernel": 2, "k": 2, "tile_rows": 228, "tile_words": 64}
 
 
@@ -132,7 +133,7 @@ def measured_peaks() -> dict:
 
 
 # ---------------------------------------------------------------------------
-# roofline model of the dominant kernel (derivation in the design doc)
+# roofline model of the dominant kernel
 # ---------------------------------------------------------------------------
 # Algorithmic integer lane-operations per site update of the bit-sliced,
 # lazily evaluated acceptance test (per 32-site word: neighbour classes and

@@ -105,12 +105,12 @@ def test_block_mh_detailed_balance_4x4():
     L, B, beta, ox, oy = 4, 2, 0.44, 1, 2
     p = cnn.init_params(C=4, seed=7, scale=3.0)
     rng = np.random.default_rng(8)
-    configs = exact.all_configs(L)
+    states = exact.all_configs(L)
     pi = exact.boltzmann(L, beta)
-    idx = {c.tobytes(): i for i, c in enumerate(configs)}
+    idx = {c.tobytes(): i for i, c in enumerate(states)}
     checked = 0
-    for k in rng.choice(len(configs), size=60, replace=False):
-        x = configs[k]
+    for k in rng.choice(len(states), size=60, replace=False):
+        x = states[k]
         fr, old = cnn.frame(x, ox, oy, B)
         P = cnn.quantise(cnn.forward(p, fr[None])[0])
         for bits in itertools.product([-1, 1], repeat=B * B):
