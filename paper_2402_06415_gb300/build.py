@@ -68,8 +68,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             print(r.stdout + r.stderr, file=sys.stderr)
         return obj
 
-    srcs = _sources()
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    # longest translation units first: the per-K tiled kernels (k_tiled_k<K>.cu)
+    # grow with K
+    def weight(p):
+        b = os.path.basename(p)
+        return int(b[len("k_tiled_k"):-len(".cu")]) if b.startswith("k_tiled_k") else 0
+    srcs = sorted(_sources(), key=lambda p: -weight(p))
+    # the per-K tiled kernels are the long poles: one worker per core
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB_PATH + ".tmp%d" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]

@@ -113,411 +113,6 @@ __global__ void __launch_bounds__(256) k_half_sweep_bits(uint32_t* __restrict__ 
   if (MEASURE) block_add2(anti, ones, rec);
 }
 
-// Temporal blocking: one CTA loads a tile of Ty rows x Tw words of both colour
-// planes plus a halo of H = 2K rows above and below and one word left and right
-// (read as 4-word, 16-byte aligned chunks), runs K full sweeps on it in shared
-// memory, and stores the inner Ty x Tw words.  Each half sweep invalidates one
-// more halo row on each side and one more halo bit, so after K sweeps exactly
-// the inner region is correct (K <= 8 keeps the bit penetration inside the
-// halo word).  Sites in the halo are updated with the same (sweep, site)
-// random numbers as their owners, so the result is bit-identical to K plain
-// sweeps.  Tiles are processed persistently: tile = blockIdx.x + i gridDim.x.
-template <int K>
-__global__ void __launch_bounds__(256) k_tiled_bits(const uint32_t* __restrict__ in,
-                                                    uint32_t* __restrict__ out, int L, int Wc,
-                                                    int n_ty, int Tw, uint32_t t0,
-                                                    RngParams rng, RecordSlots slots,
-                                                    unsigned long long* __restrict__ rec) {
-  extern __shared__ uint4 smem4[];
-  uint32_t* S = reinterpret_cast<uint32_t*>(smem4);
-  constexpr int H = 2 * K;
-  const int SP = Tw + 8;
-  const int Ty_max = (L + n_ty - 1) / n_ty;
-  const int SR = Ty_max + 2 * H;
-  uint32_t* S0 = S;
-  uint32_t* S1 = S + SR * SP;
-  const int n_tx = Wc / Tw;
-  const int n_tiles = n_ty * n_tx;
-  const int lane = threadIdx.x & 31;
-  unsigned long long acc_anti[K], acc_ones[K];
-#pragma unroll
-  for (int s = 0; s < K; ++s) acc_anti[s] = acc_ones[s] = 0ull;
-
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int ty = tile / n_tx, tx = tile - (tile / n_tx) * n_tx;
-    const int y0 = (int)((long long)ty * L / n_ty);
-    const int y1 = (int)((long long)(ty + 1) * L / n_ty);
-    const int Ty = y1 - y0;
-    const int w0 = tx * Tw;
-    const int rows = Ty + 2 * H;
-    const int qrow = SP / 4;
-    for (int i = threadIdx.x; i < 2 * rows * qrow; i += blockDim.x) {
-      const int c = i / (rows * qrow);
-      const int rem = i - c * rows * qrow;
-      const int r = rem / qrow, q = rem - (rem / qrow) * qrow;
-      const int gy = wrap(y0 - H + r, L);
-      const int gw = wrap(w0 - 4 + 4 * q, Wc);
-      const uint4 v =
-          *reinterpret_cast<const uint4*>(in + (size_t)c * L * Wc + (size_t)gy * Wc + gw);
-      reinterpret_cast<uint4*>(S + c * SR * SP + r * SP)[q] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2 * K; ++h) {
-      const int c = h & 1;
-      const int sw = h >> 1;
-      const uint32_t t = t0 + (uint32_t)sw;
-      const int r_lo = h + 1;
-      const int ncols = Tw + 2;
-      const int count = (rows - 2 * h - 2) * ncols;
-      uint32_t* So = c ? S1 : S0;
-      const uint32_t* Sn = c ? S0 : S1;
-      for (int base = (threadIdx.x & ~31); base < count; base += blockDim.x) {
-        const int idx = base + lane;
-        const bool active = idx < count;
-        int r = r_lo, col = 3;
-        if (active) {
-          r = r_lo + idx / ncols;
-          col = 3 + (idx - (idx / ncols) * ncols);
-        }
-        const uint32_t s = So[r * SP + col];
-        const uint32_t up = Sn[(r - 1) * SP + col];
-        const uint32_t dn = Sn[(r + 1) * SP + col];
-        const uint32_t mid = Sn[r * SP + col];
-        const int o = (y0 + r + c) & 1;  // H is even
-        const uint32_t side = o == 0 ? ((mid << 1) | (Sn[r * SP + col - 1] >> 31))
-                                     : ((mid >> 1) | (Sn[r * SP + col + 1] << 31));
-        const int gy = wrap(y0 - H + r, L);
-        const int gw = wrap(w0 - 4 + col, Wc);
-        const Classes k = classify(s, up, dn, mid, side);
-        const uint32_t f = flip_mask(k, active ? 0xffffffffu : 0u, (uint32_t)gy * Wc + gw, t,
-                                     rng.replica, c, rng.key0, rng.key1, rng.t4, rng.t8);
-        const uint32_t ns = s ^ f;
-        if (active) {
-          So[r * SP + col] = ns;
-          if (c == 1 && r >= H && r < H + Ty && col >= 4 && col < 4 + Tw) {
-            acc_anti[sw] += __popc(ns ^ up) + __popc(ns ^ dn) + __popc(ns ^ mid) + __popc(ns ^ side);
-            acc_ones[sw] += __popc(ns) + __popc(mid);
-          }
-        }
-      }
-      __syncthreads();
-    }
-    const int qin = Tw / 4;
-    for (int i = threadIdx.x; i < 2 * Ty * qin; i += blockDim.x) {
-      const int c = i / (Ty * qin);
-      const int rem = i - c * Ty * qin;
-      const int r = rem / qin, q = rem - (rem / qin) * qin;
-      const uint4 v = reinterpret_cast<const uint4*>(S + c * SR * SP + (H + r) * SP + 4)[q];
-      *reinterpret_cast<uint4*>(out + (size_t)c * L * Wc + (size_t)(y0 + r) * Wc + w0 + 4 * q) = v;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int s = 0; s < K; ++s)
-    if (slots.slot[s] >= 0) block_add2(acc_anti[s], acc_ones[s], rec + 2 * (size_t)slots.slot[s]);
-}
-
-// Planes of Philox blocks b = B0 .. B1-1 for the undecided lanes D of one
-// word; cls marks the lanes that test against t4 (the others test against t8).
-// Accepted lanes are added to acc.  Stops early once no lane of the warp is
-// undecided (warp vote), so every lane of the warp must call it.
-template <int B0, int B1>
-__device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep, uint32_t colour,
-                                            const RngParams& rng, uint32_t& D, uint32_t cls,
-                                            uint32_t& acc) {
-#pragma unroll
-  for (int b = B0; b < B1; ++b) {
-    if (!__any_sync(0xffffffffu, D != 0u)) break;
-    const uint4 r = philox10_rk(make_uint4(g, t, rep, ctr_w(kTagMet, colour, b)), rng.rk0, rng.rk1);
-    const uint32_t p[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = 4 * b + q;
-      const uint32_t m4 = rng.tm4[k], m8 = rng.tm8[k];
-      const uint32_t tm = (cls & m4) | (~cls & m8);  // lane's threshold bit
-      acc |= D & tm & ~p[q];                          // u bit 0 < T bit 1: accept
-      D &= ~(tm ^ p[q]);                              // equal bits: still undecided
-    }
-  }
-}
-
-// lazy_planes for two independent words at once (one warp vote for both; two
-// Philox chains in flight per thread).
-template <int B0, int B1>
-__device__ __forceinline__ void lazy_planes2(uint32_t ga, uint32_t gb, uint32_t t, uint32_t rep,
-                                             uint32_t colour, const RngParams& rng, uint32_t& Da,
-                                             uint32_t clsa, uint32_t& acca, uint32_t& Db,
-                                             uint32_t clsb, uint32_t& accb) {
-#pragma unroll
-  for (int b = B0; b < B1; ++b) {
-    if (!__any_sync(0xffffffffu, (Da | Db) != 0u)) break;
-    const uint32_t cw = ctr_w(kTagMet, colour, b);
-    const uint4 ra = philox10_rk(make_uint4(ga, t, rep, cw), rng.rk0, rng.rk1);
-    const uint4 rb = philox10_rk(make_uint4(gb, t, rep, cw), rng.rk0, rng.rk1);
-    const uint32_t pa[4] = {ra.x, ra.y, ra.z, ra.w};
-    const uint32_t pb[4] = {rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = 4 * b + q;
-      const uint32_t m4 = rng.tm4[k], m8 = rng.tm8[k];
-      const uint32_t ta = (clsa & m4) | (~clsa & m8);
-      const uint32_t tb = (clsb & m4) | (~clsb & m8);
-      acca |= Da & ta & ~pa[q];
-      accb |= Db & tb & ~pb[q];
-      Da &= ~(ta ^ pa[q]);
-      Db &= ~(tb ^ pb[q]);
-    }
-  }
-}
-
-// Tiled sweep with one warp per 32-word tile row segment.  Same tiling, halo
-// and results as k_tiled_bits; differences are for speed only:
-//  * the inner 32*TWW words of a row are updated by TWW warps (lane = word), the
-//    two halo words per row by a separate short pass, so no integer division
-//    or modulo runs per word;
-//  * phase 1 evaluates the first two Philox blocks (8 planes) of every word;
-//    words with lanes still undecided (about 1 in 10) go to a shared-memory
-//    queue, and phase 2 finishes them with all lanes of a warp busy on queued
-//    words, instead of every warp waiting for its slowest word;
-//  * per-sweep observables are summed in shared memory, not registers.
-template <int K, int TWW>
-__global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restrict__ in,
-                                                         uint32_t* __restrict__ out, int L, int Wc,
-                                                         int n_ty, uint32_t t0, RngParams rng,
-                                                         RecordSlots slots,
-                                                         unsigned long long* __restrict__ rec) {
-  constexpr int H = 2 * K;
-  constexpr int TW = 32 * TWW;
-  constexpr int SP = TW + 8;
-  constexpr int QCAP = 512;
-  extern __shared__ uint4 smem4[];
-  __shared__ uint32_t q_pos[QCAP], q_d[QCAP], q_cls[QCAP];
-  __shared__ int q_n[2];
-  __shared__ unsigned long long s_anti[K], s_ones[K];
-  uint32_t* S = reinterpret_cast<uint32_t*>(smem4);
-  const int Ty_max = (L + n_ty - 1) / n_ty;
-  const int SR = Ty_max + 2 * H;
-  uint32_t* S0 = S;
-  uint32_t* S1 = S + SR * SP;
-  const int n_tx = Wc / TW;
-  const int n_tiles = n_ty * n_tx;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  if (tid < K) {
-    s_anti[tid] = 0ull;
-    s_ones[tid] = 0ull;
-  }
-
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int ty = tile / n_tx, tx = tile - (tile / n_tx) * n_tx;
-    const int y0 = (int)((long long)ty * L / n_ty);
-    const int y1 = (int)((long long)(ty + 1) * L / n_ty);
-    const int Ty = y1 - y0;
-    const int w0 = tx * TW;
-    const int rows = Ty + 2 * H;
-    constexpr int QROW = SP / 4;
-    const int per_colour = rows * QROW;
-    for (int i = tid; i < 2 * per_colour; i += blockDim.x) {
-      // no runtime division or modulo: one compare for the colour, constant
-      // divisor for the row, conditional wraps (|y0 - H + r| < 2L, |w| < 2 Wc)
-      const int c = i >= per_colour;
-      const int rem = i - c * per_colour;
-      const int r = rem / QROW, q = rem - (rem / QROW) * QROW;
-      int gy = y0 - H + r;
-      gy += gy < 0 ? L : 0;
-      gy -= gy >= L ? L : 0;
-      int gw = w0 - 4 + 4 * q;
-      gw += gw < 0 ? Wc : 0;
-      gw -= gw >= Wc ? Wc : 0;
-      const uint4 v =
-          *reinterpret_cast<const uint4*>(in + (size_t)c * L * Wc + (size_t)gy * Wc + gw);
-      reinterpret_cast<uint4*>(S + c * SR * SP + r * SP)[q] = v;
-    }
-    if (tid == 0) q_n[0] = 0;
-    __syncthreads();
-    // global row of tile row r (no modulo: |y0 - H + r| < 2L since H <= 16 <= L)
-    auto grow = [&](int r) {
-      int gy = y0 - H + r;
-      gy += gy < 0 ? L : 0;
-      gy -= gy >= L ? L : 0;
-      return gy;
-    };
-    auto gcol = [&](int col) {
-      int gw = w0 - 4 + col;
-      gw += gw < 0 ? Wc : 0;
-      gw -= gw >= Wc ? Wc : 0;
-      return gw;
-    };
-#pragma unroll
-    for (int h = 0; h < 2 * K; ++h) {
-      const int c = h & 1;
-      const int sw = h >> 1;
-      const uint32_t t = t0 + (uint32_t)sw;
-      const int r_lo = h + 1;
-      const int nrows = rows - 2 * h - 2;
-      uint32_t* So = c ? S1 : S0;
-      const uint32_t* Sn = c ? S0 : S1;
-      int* qn = &q_n[h & 1];
-
-      // ---- phase 1: classes, planes 0..7, write, queue the undecided ----
-      auto phase1 = [&](int r, int col, bool active) {
-        const uint32_t s = So[r * SP + col];
-        const uint32_t up = Sn[(r - 1) * SP + col];
-        const uint32_t dn = Sn[(r + 1) * SP + col];
-        const uint32_t mid = Sn[r * SP + col];
-        const int o = (y0 + r + c) & 1;
-        const uint32_t side = o == 0 ? ((mid << 1) | (Sn[r * SP + col - 1] >> 31))
-                                     : ((mid >> 1) | (Sn[r * SP + col + 1] << 31));
-        const Classes k = classify(s, up, dn, mid, side);
-        const uint32_t valid = active ? 0xffffffffu : 0u;
-        uint32_t D = (k.one | k.zero) & valid, acc = 0;
-        const uint32_t cls = k.one;
-        const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
-        lazy_planes<0, 2>(g, t, rng.replica, c, rng, D, cls, acc);
-        bool ovf = false;
-        if (active) {
-          So[r * SP + col] = s ^ ((k.ge2 & valid) | acc);
-          if (D != 0u) {
-            const int slot = atomicAdd(qn, 1);
-            if (slot < QCAP) {
-              q_pos[slot] = ((uint32_t)r << 8) | (uint32_t)col;
-              q_d[slot] = D;
-              q_cls[slot] = cls;
-            } else {
-              ovf = true;
-            }
-          }
-        }
-        // queue full (not expected at these tile sizes): finish in place
-        if (__any_sync(0xffffffffu, ovf)) {
-          uint32_t e = ovf ? D : 0u, acc2 = 0;
-          lazy_planes<2, 8>(g, t, rng.replica, c, rng, e, cls, acc2);
-          if (ovf) So[r * SP + col] ^= acc2;
-        }
-      };
-      // queue a word whose lanes are still undecided after phase 1 (returns
-      // false if the queue is full; the caller then finishes it in place)
-      auto enqueue = [&](int r, int col, uint32_t D, uint32_t cls) {
-        const int slot = atomicAdd(qn, 1);
-        if (slot >= QCAP) return false;
-        q_pos[slot] = ((uint32_t)r << 8) | (uint32_t)col;
-        q_d[slot] = D;
-        q_cls[slot] = cls;
-        return true;
-      };
-      // inner words of two adjacent rows (r, r+1) per thread: the two words
-      // share the other colour's rows r and r+1 as neighbours
-      auto phase1_pair = [&](int r, int col) {
-        const uint32_t sa = So[r * SP + col];
-        const uint32_t sb = So[(r + 1) * SP + col];
-        const uint32_t u0 = Sn[(r - 1) * SP + col];
-        const uint32_t m0 = Sn[r * SP + col];
-        const uint32_t m1 = Sn[(r + 1) * SP + col];
-        const uint32_t d1 = Sn[(r + 2) * SP + col];
-        const int oa = (y0 + r + c) & 1;  // row r+1 has the other offset
-        uint32_t side_a, side_b;
-        if (oa == 0) {
-          side_a = (m0 << 1) | (Sn[r * SP + col - 1] >> 31);
-          side_b = (m1 >> 1) | (Sn[(r + 1) * SP + col + 1] << 31);
-        } else {
-          side_a = (m0 >> 1) | (Sn[r * SP + col + 1] << 31);
-          side_b = (m1 << 1) | (Sn[(r + 1) * SP + col - 1] >> 31);
-        }
-        const Classes ka = classify(sa, u0, m1, m0, side_a);
-        const Classes kb = classify(sb, m0, d1, m1, side_b);
-        uint32_t Da = ka.one | ka.zero, Db = kb.one | kb.zero, acca = 0, accb = 0;
-        const int gya = grow(r);
-        const int gyb = gya + 1 == L ? 0 : gya + 1;
-        const uint32_t gw = (uint32_t)(w0 + col - 4);  // inner column: no wrap
-        const uint32_t ga = (uint32_t)gya * (uint32_t)Wc + gw;
-        const uint32_t gb = (uint32_t)gyb * (uint32_t)Wc + gw;
-        lazy_planes2<0, 2>(ga, gb, t, rng.replica, c, rng, Da, ka.one, acca, Db, kb.one, accb);
-        So[r * SP + col] = sa ^ (ka.ge2 | acca);
-        So[(r + 1) * SP + col] = sb ^ (kb.ge2 | accb);
-        const bool ovfa = Da != 0u && !enqueue(r, col, Da, ka.one);
-        const bool ovfb = Db != 0u && !enqueue(r + 1, col, Db, kb.one);
-        if (__any_sync(0xffffffffu, ovfa || ovfb)) {  // queue full: finish in place
-          uint32_t ea = ovfa ? Da : 0u, eb = ovfb ? Db : 0u, xa = 0, xb = 0;
-          lazy_planes2<2, 8>(ga, gb, t, rng.replica, c, rng, ea, ka.one, xa, eb, kb.one, xb);
-          if (ovfa) So[r * SP + col] ^= xa;
-          if (ovfb) So[(r + 1) * SP + col] ^= xb;
-        }
-      };
-      const int npairs = nrows >> 1;
-      for (int item = warp; item < npairs * TWW; item += nwarps) {
-        const int r = r_lo + 2 * (item / TWW);
-        const int col = 4 + 32 * (item % TWW) + lane;
-        phase1_pair(r, col);
-      }
-      if (nrows & 1) {  // odd row count: the last row alone
-        for (int item = warp; item < TWW; item += nwarps)
-          phase1(r_lo + nrows - 1, 4 + 32 * item + lane, true);
-      }
-      for (int base = warp * 32; base < 2 * nrows; base += blockDim.x) {
-        const int idx = base + lane;
-        const bool active = idx < 2 * nrows;
-        const int r = r_lo + (active ? (idx >> 1) : 0);
-        const int col = (idx & 1) ? 4 + TW : 3;
-        phase1(r, col, active);
-      }
-      __syncthreads();
-
-      // ---- phase 2: finish the queued words, all lanes busy ----
-      const int n = min(*qn, QCAP);
-      if (tid == 0) q_n[(h + 1) & 1] = 0;
-      for (int base = warp * 32; base < n; base += blockDim.x) {
-        const int e = base + lane;
-        const bool act = e < n;
-        const uint32_t pos = act ? q_pos[e] : (3u | ((uint32_t)r_lo << 8));
-        uint32_t D = act ? q_d[e] : 0u, acc = 0;
-        const uint32_t cls = act ? q_cls[e] : 0u;
-        const int r = (int)(pos >> 8), col = (int)(pos & 255u);
-        const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
-        lazy_planes<2, 8>(g, t, rng.replica, c, rng, D, cls, acc);
-        if (act && acc) So[r * SP + col] ^= acc;
-      }
-      if (c == 1 && slots.slot[sw] >= 0) {
-        __syncthreads();
-        unsigned long long anti = 0, ones = 0;
-        for (int item = warp; item < Ty * TWW; item += nwarps) {
-          const int r = H + item / TWW;
-          const int col = 4 + 32 * (item % TWW) + lane;
-          const uint32_t ns = S1[r * SP + col];
-          const uint32_t up = S0[(r - 1) * SP + col];
-          const uint32_t dn = S0[(r + 1) * SP + col];
-          const uint32_t mid = S0[r * SP + col];
-          const int o = (y0 + r + 1) & 1;
-          const uint32_t side = o == 0 ? ((mid << 1) | (S0[r * SP + col - 1] >> 31))
-                                       : ((mid >> 1) | (S0[r * SP + col + 1] << 31));
-          anti += __popc(ns ^ up) + __popc(ns ^ dn) + __popc(ns ^ mid) + __popc(ns ^ side);
-          ones += __popc(ns) + __popc(mid);
-        }
-        anti = warp_sum_u64(anti);
-        ones = warp_sum_u64(ones);
-        if (lane == 0) {
-          atomicAdd(&s_anti[sw], anti);
-          atomicAdd(&s_ones[sw], ones);
-        }
-      }
-      __syncthreads();
-    }
-    constexpr int QIN = TW / 4;
-    for (int i = tid; i < 2 * Ty * QIN; i += blockDim.x) {
-      const int c = i >= Ty * QIN;
-      const int rem = i - c * Ty * QIN;
-      const int r = rem / QIN, q = rem - (rem / QIN) * QIN;
-      const uint4 v = reinterpret_cast<const uint4*>(S + c * SR * SP + (H + r) * SP + 4)[q];
-      *reinterpret_cast<uint4*>(out + (size_t)c * L * Wc + (size_t)(y0 + r) * Wc + w0 + 4 * q) = v;
-    }
-    __syncthreads();
-  }
-  if (tid < K && slots.slot[tid] >= 0) {
-    unsigned long long* dst = rec + 2 * (size_t)slots.slot[tid];
-    if (s_anti[tid]) atomicAdd(dst, s_anti[tid]);
-    if (s_ones[tid]) atomicAdd(dst + 1, s_ones[tid]);
-  }
-}
-
 // Observables of the current configuration: antiparallel bonds counted from
 // every colour-0 site to its four colour-1 neighbours, and up spins.
 __global__ void __launch_bounds__(256) k_measure_bits(const uint32_t* __restrict__ planes, int L,
@@ -586,6 +181,27 @@ int grid_for(long long items, int block) {
 
 }  // namespace
 
+// Per-K tiled launchers (k_tiled_k<K>.cu).
+#define ISING_TILED_DECLARE(K)                                                                   \
+  cudaError_t launch_tiled_k##K(const BitsLattice&, uint32_t*, const RngParams&, uint32_t,       \
+                                const RecordSlots&, unsigned long long*, int, int, int, int,     \
+                                cudaStream_t);                                                   \
+  cudaError_t launch_tiled32_k##K##_w1(const BitsLattice&, uint32_t*, const RngParams&, uint32_t, \
+                                       const RecordSlots&, unsigned long long*, int, int,        \
+                                       cudaStream_t);                                            \
+  cudaError_t launch_tiled32_k##K##_w2(const BitsLattice&, uint32_t*, const RngParams&, uint32_t, \
+                                       const RecordSlots&, unsigned long long*, int, int,        \
+                                       cudaStream_t);
+ISING_TILED_DECLARE(1)
+ISING_TILED_DECLARE(2)
+ISING_TILED_DECLARE(3)
+ISING_TILED_DECLARE(4)
+ISING_TILED_DECLARE(5)
+ISING_TILED_DECLARE(6)
+ISING_TILED_DECLARE(7)
+ISING_TILED_DECLARE(8)
+#undef ISING_TILED_DECLARE
+
 cudaError_t launch_init_bits(const BitsLattice& lat, const RngParams& rng, cudaStream_t s) {
   const long long items = 2LL * lat.L * lat.Wc;
   k_init_bits<<<grid_for(items, 256), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, lat.pitch, rng);
@@ -612,19 +228,6 @@ size_t tiled_smem_bytes(int L, int k, int n_tile_rows, int tile_words) {
   return 2ull * (size_t)(Ty_max + 4 * k) * (size_t)(tile_words + 8) * sizeof(uint32_t);
 }
 
-template <int K>
-static cudaError_t launch_tiled_k(const BitsLattice& in, uint32_t* out, const RngParams& rng,
-                                  uint32_t sweep0, const RecordSlots& slots,
-                                  unsigned long long* rec, int n_ty, int Tw, int grid, int block,
-                                  cudaStream_t s) {
-  const size_t smem = tiled_smem_bytes(in.L, K, n_ty, Tw);
-  cudaError_t e = cudaFuncSetAttribute(k_tiled_bits<K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_tiled_bits<K><<<grid, block, smem, s>>>(in.planes, out, in.L, in.Wc, n_ty, Tw, sweep0, rng,
-                                             slots, rec);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_tiled_sweep_bits(const BitsLattice& in, uint32_t* out, const RngParams& rng,
                                     uint32_t sweep0, int k, const RecordSlots& slots,
@@ -634,14 +237,14 @@ cudaError_t launch_tiled_sweep_bits(const BitsLattice& in, uint32_t* out, const 
   if (block <= 0) block = 256;
   if (grid <= 0 || grid > n_tiles) grid = n_tiles;
   switch (k) {
-    case 1: return launch_tiled_k<1>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
-    case 2: return launch_tiled_k<2>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
-    case 3: return launch_tiled_k<3>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
-    case 4: return launch_tiled_k<4>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
-    case 5: return launch_tiled_k<5>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
-    case 6: return launch_tiled_k<6>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
-    case 7: return launch_tiled_k<7>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
-    case 8: return launch_tiled_k<8>(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 1: return launch_tiled_k1(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 2: return launch_tiled_k2(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 3: return launch_tiled_k3(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 4: return launch_tiled_k4(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 5: return launch_tiled_k5(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 6: return launch_tiled_k6(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 7: return launch_tiled_k7(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
+    case 8: return launch_tiled_k8(in, out, rng, sweep0, slots, rec, n_ty, Tw, grid, block, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -651,56 +254,28 @@ size_t tiled32_smem_bytes(int L, int k, int n_tile_rows, int tile_words) {
   return 2ull * (size_t)(Ty_max + 4 * k) * (size_t)(tile_words + 8) * sizeof(uint32_t);
 }
 
-template <int K, int TWW>
-static cudaError_t launch_tiled32_k(const BitsLattice& in, uint32_t* out, const RngParams& rng,
-                                    uint32_t sweep0, const RecordSlots& slots,
-                                    unsigned long long* rec, int n_ty, int grid, cudaStream_t s) {
-  const size_t smem = tiled32_smem_bytes(in.L, K, n_ty, 32 * TWW);
-  static DeviceCache configured;  // per instantiation and device
-  if ((long long)smem > configured.get()) {
-    cudaError_t e = cudaFuncSetAttribute(k_tiled32_bits<K, TWW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured.set((long long)smem);
-  }
-  const int n_tiles = n_ty * (in.Wc / (32 * TWW));
-  if (grid <= 0) {
-    // resident CTAs, cached per device as (shared-memory size << 20 | grid)
-    static DeviceCache occ;
-    const long long memo = occ.get();
-    if ((memo >> 20) == (long long)smem) {
-      grid = (int)(memo & 0xfffff);
-    } else {
-      int per_sm = 0, dev = 0, sms = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per_sm, k_tiled32_bits<K, TWW>, 256, smem);
-      if (e != cudaSuccess) return e;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      grid = per_sm * sms;
-      occ.set(((long long)smem << 20) | (long long)grid);
-    }
-  }
-  if (grid > n_tiles) grid = n_tiles;
-  if (grid < 1) grid = 1;
-  k_tiled32_bits<K, TWW><<<grid, 256, smem, s>>>(in.planes, out, in.L, in.Wc, n_ty, sweep0, rng,
-                                                 slots, rec);
-  return cudaGetLastError();
-}
 
 template <int TWW>
 static cudaError_t launch_tiled32_w(const BitsLattice& in, uint32_t* out, const RngParams& rng,
                                     uint32_t sweep0, int k, const RecordSlots& slots,
                                     unsigned long long* rec, int n_ty, int grid, cudaStream_t s) {
   switch (k) {
-    case 1: return launch_tiled32_k<1, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
-    case 2: return launch_tiled32_k<2, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
-    case 3: return launch_tiled32_k<3, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
-    case 4: return launch_tiled32_k<4, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
-    case 5: return launch_tiled32_k<5, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
-    case 6: return launch_tiled32_k<6, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
-    case 7: return launch_tiled32_k<7, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
-    case 8: return launch_tiled32_k<8, TWW>(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 1: return TWW == 1 ? launch_tiled32_k1_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k1_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 2: return TWW == 1 ? launch_tiled32_k2_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k2_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 3: return TWW == 1 ? launch_tiled32_k3_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k3_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 4: return TWW == 1 ? launch_tiled32_k4_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k4_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 5: return TWW == 1 ? launch_tiled32_k5_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k5_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 6: return TWW == 1 ? launch_tiled32_k6_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k6_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 7: return TWW == 1 ? launch_tiled32_k7_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k7_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
+    case 8: return TWW == 1 ? launch_tiled32_k8_w1(in, out, rng, sweep0, slots, rec, n_ty, grid, s)
+                            : launch_tiled32_k8_w2(in, out, rng, sweep0, slots, rec, n_ty, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
