@@ -135,6 +135,11 @@ def measured_peaks() -> dict:
 # ---------------------------------------------------------------------------
 # roofline model of the dominant kernel
 # ---------------------------------------------------------------------------
+# DRAM bytes (read + write) of one launch of the benchmark kernel shape, from an
+# ncu capture of the current kernel (profiles/k_tiled32_bits_L16384_k2.md):
+# 33.70 MB read + 0.66 MB written per launch (2 sweeps) after ncu's cache flush.
+# Reported only for that shape; any other shape reports null.
+NCU_TRAFFIC = {"shape": (2, 228, 64), "bytes_per_launch": 33.70e6 + 0.66e6}
 # Algorithmic integer lane-operations per site update of the bit-sliced,
 # lazily evaluated acceptance test (per 32-site word: neighbour classes and
 # update 24 ops, E[Philox blocks] = 1.95 x 40 ops, 4 x 1.95 planes x 5 ops),
@@ -335,7 +340,9 @@ def run_ours(args):
     hbm_gbs = 0.25 * sites_per_launch / (per_launch_ms * 1e6)
     roofline = {
         "bound": "alu", "achieved": alu_gops, "peak": peak, "unit": "Gop/s",
-        "frac": alu_gops / peak, "traffic": None,
+        "frac": alu_gops / peak,
+        "traffic": (NCU_TRAFFIC["bytes_per_launch"]
+                    if (cfg["k"], cfg["tile_rows"], cfg["tile_words"]) == NCU_TRAFFIC["shape"] else None),
         "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
                    if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
         "peak_source": "152 SMs x 128 INT32 lanes x median SM clock under load",
