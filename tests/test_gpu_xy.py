@@ -26,8 +26,10 @@ def _cuda():
 
 @pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("L", [2, 4, 6, 16, 64, 130])
-@pytest.mark.parametrize("beta", [0.3, 1.0 / T_PAPER, 3.0])
+@pytest.mark.parametrize("beta", [0.3, 1.0 / T_PAPER, 3.0, 25.0])
 def test_xy_bit_exact(precision, L, beta):
+    # beta = 25 drives -beta dE below -80 (the branch of the acceptance test that
+    # needs no exponential at all) as well as through the hardware-exp band
     seed, n = 100 + L, 7
     u = oracle.xy_init(L, seed, precision=precision)
     start = u.astype(np.float64).copy()
