@@ -89,6 +89,10 @@ def lib() -> ctypes.CDLL:
         L.orc_sw_threshold.restype = u32
         L.orc_sw_step.argtypes = [i32, dbl, u64, u32, u32, p, p]
         L.orc_sw_step.restype = i64
+        L.orc_wolff_seed_site.argtypes = [i32, u64, u32, u32]
+        L.orc_wolff_seed_site.restype = u32
+        L.orc_wolff_step.argtypes = [i32, dbl, u64, u32, u32, p, p, p]
+        L.orc_wolff_step.restype = i64
         L.orc_quad_neighbours.argtypes = [i32, i32, i32, i32, i32, p]
         L.orc_quad_neighbours.restype = i32
         L.orc_quad_threshold.argtypes = [i32, dbl, dbl, dbl, i32, i32, p]
@@ -368,6 +372,27 @@ def sw_steps(s: np.ndarray, beta: float, seed: int, n_steps: int, step0: int = 0
     C = np.zeros(n_steps, dtype=np.int64)
     for k in range(n_steps):
         C[k] = lib().orc_sw_step(L, float(beta), seed, replica, step0 + k, _ptr(s), _ptr(parent))
+        E[k], M[k] = energy_mag(s)
+    return E, M, C
+
+
+def wolff_seed_site(L: int, seed: int, step: int, replica: int = 0) -> int:
+    return int(lib().orc_wolff_seed_site(L, seed, replica, step))
+
+
+def wolff_steps(s: np.ndarray, beta: float, seed: int, n_steps: int, step0: int = 0,
+                replica: int = 0):
+    """n Wolff steps in place; returns (E, M, cluster size) after each step."""
+    assert s.dtype == np.int8 and s.flags["C_CONTIGUOUS"]
+    L = s.shape[0]
+    stack = np.zeros(L * L, dtype=np.uint32)
+    mark = np.zeros(L * L, dtype=np.uint8)
+    E = np.zeros(n_steps, dtype=np.int64)
+    M = np.zeros(n_steps, dtype=np.int64)
+    C = np.zeros(n_steps, dtype=np.int64)
+    for k in range(n_steps):
+        C[k] = lib().orc_wolff_step(L, float(beta), seed, replica, step0 + k, _ptr(s), _ptr(stack),
+                                    _ptr(mark))
         E[k], M[k] = energy_mag(s)
     return E, M, C
 

@@ -354,3 +354,68 @@ long long orc_sw_step(int L, double beta, uint64_t seed, uint32_t r, uint32_t st
     }
     return clusters;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Wolff single-cluster update (Wolff, PRL 62, 361 (1989)), the other      */
+/* cluster method next to Swendsen-Wang.  Step n: the seed site is          */
+/* m = floor(u N / 2^32), u = word 0 of Philox(0, n, r, WOLFF_SEED << 16);   */
+/* a bond b = 2 (y L + x) + dir between equal spins is active iff           */
+/* u < floor((1 - exp(-2 beta)) 2^32), u = word (b & 3) of                  */
+/* Philox(b >> 2, n, r, WOLFF_BOND << 16); the cluster of active bonds       */
+/* containing the seed flips.  The cluster is a connected component, so it  */
+/* does not depend on the order in which it is grown.                       */
+/* ---------------------------------------------------------------------- */
+enum { ORC_TAG_WOLFF_SEED = 16, ORC_TAG_WOLFF_BOND = 17 };
+
+static int wolff_bond_active(uint64_t seed, uint32_t r, uint32_t step, uint32_t thr, uint32_t bond)
+{
+    uint32_t o[4];
+    orc_block(seed, bond >> 2, step, r, ORC_TAG_WOLFF_BOND, 0, 0, o);
+    return o[bond & 3] < thr;
+}
+
+uint32_t orc_wolff_seed_site(int L, uint64_t seed, uint32_t r, uint32_t step)
+{
+    uint32_t o[4];
+    orc_block(seed, 0, step, r, ORC_TAG_WOLFF_SEED, 0, 0, o);
+    return (uint32_t)(((uint64_t)o[0] * (uint64_t)((uint32_t)L * (uint32_t)L)) >> 32);
+}
+
+/* One Wolff step in place; stack and mark are scratch of L*L entries.
+ * Returns the cluster size. */
+long long orc_wolff_step(int L, double beta, uint64_t seed, uint32_t r, uint32_t step, int8_t *s,
+                         uint32_t *stack, uint8_t *mark)
+{
+    const uint32_t N = (uint32_t)L * (uint32_t)L;
+    const uint32_t thr = orc_sw_threshold(beta);
+    memset(mark, 0, N);
+    uint32_t m = orc_wolff_seed_site(L, seed, r, step);
+    long long top = 0, size = 0;
+    const int8_t s0 = s[m];
+    stack[top++] = m;
+    mark[m] = 1;
+    while (top > 0) {
+        uint32_t a = stack[--top];
+        ++size;
+        int x = (int)(a % (uint32_t)L), y = (int)(a / (uint32_t)L);
+        /* the four bonds of site a: its own (to x+1, to y+1) and those of its
+         * left and lower neighbours (from x-1, from y-1) */
+        int xs[4] = {(x + 1) % L, x, (x + L - 1) % L, x};
+        int ys[4] = {y, (y + 1) % L, y, (y + L - 1) % L};
+        uint32_t bonds[4];
+        bonds[0] = 2 * a;
+        bonds[1] = 2 * a + 1;
+        bonds[2] = 2 * (uint32_t)(y * L + xs[2]);
+        bonds[3] = 2 * (uint32_t)(ys[3] * L + x) + 1;
+        for (int k = 0; k < 4; ++k) {
+            uint32_t b = (uint32_t)(ys[k] * L + xs[k]);
+            if (mark[b] || s[b] != s0) continue;
+            if (!wolff_bond_active(seed, r, step, thr, bonds[k])) continue;
+            mark[b] = 1;
+            stack[top++] = b;
+        }
+    }
+    for (uint32_t i = 0; i < N; ++i)
+        if (mark[i]) s[i] = (int8_t)-s[i];
+    return size;
+}
