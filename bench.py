@@ -673,10 +673,11 @@ def run_xy(args):
 
 
 def run_sw(args):
-    """Swendsen-Wang cluster steps against single-site Metropolis at beta_c:
-    independent |M| and E samples per second at L = 128 and 256 (tau_int from
-    the recorded series; SW alone at L = 1024), plus site throughput of one
-    cluster step at L = 4096 and 16384."""
+    """Cluster steps (Swendsen-Wang, Wolff) against single-site Metropolis at
+    beta_c: independent |M| and E samples per second at L = 128 and 256 (tau_int
+    from the recorded series; the cluster methods alone at L = 1024), plus the
+    time of one cluster step at L = 4096 and 16384 (Wolff also at beta = 0.3,
+    where its clusters are small and growth from the seed finds them)."""
     import numpy as np
     import torch
 
@@ -690,8 +691,10 @@ def run_sw(args):
 
     def chain(L, mode, n, therm):
         with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=500 + L) as lat:
-            step = lat.sweep if mode == "metropolis" else lat.sw_step
-            step(therm)
+            step = {"metropolis": lat.sweep, "sw": lat.sw_step, "wolff": lat.wolff_step}[mode]
+            # Wolff from a hot start flips tiny clusters for a long time: bring the
+            # lattice to equilibrium with Swendsen-Wang steps first
+            (lat.sw_step if mode == "wolff" else step)(therm)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -700,41 +703,66 @@ def run_sw(args):
             e1.synchronize()
             ms = e0.elapsed_time(e1)
             E, M = lat.series(n)
+            extra = {}
+            if mode == "wolff":
+                w = lat.wolff_stats()
+                extra = {"mean_cluster_fraction": w["flipped"] / (n * L * L),
+                         "steps_grown": w["grown"], "steps_labelled": w["labelled"]}
         tm = stats.tau_int(np.abs(M).astype(float))
         te = stats.tau_int(E.astype(float))
         per_s = n / (ms / 1e3)
         return {"steps": n, "steps_per_s": per_s, "tau_int_absM": tm, "tau_int_E": te,
                 "indep_samples_per_s_absM": per_s / (2 * tm),
                 "indep_samples_per_s_E": per_s / (2 * te), "run_over_tau_absM": n / tm,
-                "energy_per_site": float(np.mean(E)) / (L * L)}
+                "energy_per_site": float(np.mean(E)) / (L * L), **extra}
 
     rows = []
     for L in (128, 256):
         met = chain(L, "metropolis", args.chain_sweeps, args.thermalise)
         sw = chain(L, "sw", args.sw_steps, 200)
-        rows.append({"L": L, "metropolis": met, "sw": sw,
+        wo = chain(L, "wolff", args.sw_steps, 200)
+        rows.append({"L": L, "metropolis": met, "sw": sw, "wolff": wo,
                      "gain_indep_samples_absM": sw["indep_samples_per_s_absM"]
+                     / met["indep_samples_per_s_absM"],
+                     "wolff_gain_indep_samples_absM": wo["indep_samples_per_s_absM"]
                      / met["indep_samples_per_s_absM"]})
     # Metropolis needs runs of ~10^3 tau_int(|M|) ~ L^2.2 sweeps beyond L = 256
-    rows.append({"L": 1024, "sw": chain(1024, "sw", args.sw_steps, 200)})
+    rows.append({"L": 1024, "sw": chain(1024, "sw", args.sw_steps, 200),
+                 "wolff": chain(1024, "wolff", args.sw_steps, 200)})
     thr = {}
-    for L in (4096, 16384):
-        with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=9) as lat:
-            lat.sw_step(3)
+
+    def step_time(L, b, mode, n):
+        with ising.Lattice(L, b, ising.ISING_LAYOUT_BITS, stream=stream, seed=9) as lat:
+            step = lat.sw_step if mode == "sw" else lat.wolff_step
+            lat.sw_step(30)  # equilibrium clusters (a hot start has tiny ones)
+            step(3)
+            f0 = lat.wolff_stats()["flipped"] if mode == "wolff" else 0
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lat.sw_step(10)
+            step(n)
             e1.record(stream)
             e1.synchronize()
-            thr["L%d" % L] = {"ms_per_step": e0.elapsed_time(e1) / 10,
-                              "site_updates_per_ns": L * L * 10 / (e0.elapsed_time(e1) * 1e6)}
-    line = {"metric": "independent samples/s at beta_c, Swendsen-Wang vs Metropolis",
+            ms = e0.elapsed_time(e1)
+            r = {"ms_per_step": ms / n, "site_updates_per_ns": L * L * n / (ms * 1e6)}
+            if mode == "wolff":
+                w = lat.wolff_stats()
+                r.update({"sites_flipped_per_ns": (w["flipped"] - f0) / (ms * 1e6),
+                          "mean_cluster_fraction": (w["flipped"] - f0) / (n * L * L),
+                          "steps_grown": w["grown"], "steps_labelled": w["labelled"]})
+            return r
+
+    for L in (4096, 16384):
+        thr["L%d" % L] = step_time(L, beta, "sw", 10)
+        thr["wolff_L%d" % L] = step_time(L, beta, "wolff", 10)
+        thr["wolff_beta0.3_L%d" % L] = step_time(L, 0.3, "wolff", 200)
+    line = {"metric": "independent samples/s at beta_c, cluster steps vs Metropolis",
             "value": rows[1]["sw"]["indep_samples_per_s_absM"],
             "unit": "independent |M| samples/s (SW, L=256, beta_c)", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "dtype": "u32",
-            "config": {"workload": "2D Ising at beta_c: Swendsen-Wang cluster steps vs "
-                                   "checkerboard Metropolis sweeps, L in {128, 256} (SW also 1024)",
+            "config": {"workload": "2D Ising at beta_c: Swendsen-Wang and Wolff cluster steps vs "
+                                   "checkerboard Metropolis sweeps, L in {128, 256} (cluster steps "
+                                   "also 1024)",
                        "sw_steps": args.sw_steps, "metropolis_sweeps": args.chain_sweeps},
             "per_size": rows, "sw_throughput": thr}
     if rank == 0:

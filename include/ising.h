@@ -313,6 +313,31 @@ int ising_sweep_blocks(ising_ctx* ctx, int n_sweeps, int measure_every, int bloc
  * rejected with ISING_EINVAL.  Async. */
 int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);
 
+/* Wolff single-cluster steps (Wolff, PRL 62, 361 (1989)) on the packed layout:
+ * the paper's Discussion names cluster algorithms as the next step for its
+ * Monte Carlo.  Step n:
+ * seed site m = floor(u N / 2^32), u = word 0 of Philox(0, n, replica, 16 << 16);
+ * a bond b = 2 (y L + x) + dir between equal spins is active iff
+ * u < floor((1 - e^{-2 beta}) 2^32), u = word (b & 3) of
+ * Philox(b >> 2, n, replica, 17 << 16); the connected cluster of active bonds
+ * holding m flips.  Bit-identical to any sequential growth of the same cluster.
+ * The step counter n is separate from the other counters; ising_seed resets it.
+ * Shares the 5 bytes per site of scratch of ising_sw_step (allocated on first
+ * use); L = 65536 is rejected with ISING_EINVAL.  measure_every > 0 records
+ * (E, M) after every such step into the series ring.  Async. */
+int ising_wolff_step(ising_ctx* ctx, int n_steps, int measure_every);
+
+/* How a Wolff step finds its cluster: growth from the seed in one CTA while the
+ * cluster has at most max_sites sites (0..16384; 0 = never) and max_levels
+ * breadth-first levels (0 = a default that grows with L), otherwise connected
+ * components of the whole lattice.  Changes cost only, never the chain. */
+int ising_wolff_set_limits(ising_ctx* ctx, int max_sites, int max_levels);
+
+/* Sites flipped by the last Wolff step, by all steps since ising_seed, and how
+ * many steps finished by growth and by labelling (synchronises). */
+int ising_wolff_stats(ising_ctx* ctx, int64_t* last_size, int64_t* flipped, int64_t* grown,
+                      int64_t* labelled);
+
 /* Squares proposed and accepted by this context's block passes (synchronises). */
 int ising_block_stats(ising_ctx* ctx, int64_t* proposed, int64_t* accepted);
 

@@ -98,6 +98,9 @@ _PROTOS = [
     ("ising_block_stats", _i, [_p, _p, _p]),
     ("ising_sweep_blocks", _i, [_p, _i, _i, _i, _i]),
     ("ising_sw_step", _i, [_p, _i, _i]),
+    ("ising_wolff_step", _i, [_p, _i, _i]),
+    ("ising_wolff_set_limits", _i, [_p, _i, _i]),
+    ("ising_wolff_stats", _i, [_p, _p, _p, _p, _p]),
     ("ising_nn_param_count", _i, []),
     ("ising_nn_create", _i, [ctypes.POINTER(_p), _i, _i, _p]),
     ("ising_nn_set_params", _i, [_p, _p, _i]),
@@ -391,6 +394,16 @@ class Lattice:
         """n Swendsen-Wang cluster steps (packed layout only)."""
         ising_sw_step(self.ctx, n, measure_every)
 
+    def wolff_step(self, n: int, measure_every: int = 0):
+        """n Wolff single-cluster steps (packed layout only)."""
+        ising_wolff_step(self.ctx, n, measure_every)
+
+    def wolff_set_limits(self, max_sites: int, max_levels: int = 0):
+        ising_wolff_set_limits(self.ctx, max_sites, max_levels)
+
+    def wolff_stats(self) -> dict:
+        return ising_wolff_stats(self.ctx)
+
     def measure(self):
         return ising_measure(self.ctx)
 
@@ -603,6 +616,20 @@ def ising_sweep_blocks(ctx: int, n_sweeps: int, measure_every: int = 0, block: i
 
 def ising_sw_step(ctx: int, n_steps: int, measure_every: int = 0) -> None:
     _check(lib().ising_sw_step(ctx, int(n_steps), int(measure_every)))
+
+
+def ising_wolff_step(ctx: int, n_steps: int, measure_every: int = 0) -> None:
+    _check(lib().ising_wolff_step(ctx, int(n_steps), int(measure_every)))
+
+
+def ising_wolff_set_limits(ctx: int, max_sites: int, max_levels: int = 0) -> None:
+    _check(lib().ising_wolff_set_limits(ctx, int(max_sites), int(max_levels)))
+
+
+def ising_wolff_stats(ctx: int) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().ising_wolff_stats(ctx, *(ctypes.byref(x) for x in v)))
+    return dict(zip(("last_size", "flipped", "grown", "labelled"), (int(x.value) for x in v)))
 
 
 def ising_block_stats(ctx: int):

@@ -92,6 +92,9 @@ struct ising_ctx {
   uint32_t* sw_parent = nullptr;  // Swendsen-Wang scratch
   uint8_t* sw_flip = nullptr;
   int64_t sw_steps = 0;
+  WolffCtl* wolff = nullptr;  // Wolff step state (parent / mark scratch shared with Swendsen-Wang)
+  int64_t wolff_steps = 0;
+  int wolff_max_sites = kWolffMaxGrowSites, wolff_max_levels = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
@@ -131,6 +134,8 @@ void free_all(ising_ctx* c) {
   cudaFree(c->blk_stats);
   cudaFree(c->sw_parent);
   cudaFree(c->sw_flip);
+  cudaFree(c->wolff);
+  c->wolff = nullptr;
   c->sw_parent = nullptr;
   c->sw_flip = nullptr;
   c->nn_w = c->nn_w2t = nullptr;
@@ -441,7 +446,12 @@ int ising_seed(ising_ctx* c, uint64_t seed) {
   c->sweep = 0;
   c->rec_count = 0;
   c->sw_steps = 0;
+  c->wolff_steps = 0;
   cudaError_t e;
+  if (c->wolff) {
+    e = cudaMemsetAsync(c->wolff, 0, sizeof(WolffCtl), c->stream);
+    if (e) return fail(ISING_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
   if (c->layout == ISING_LAYOUT_BITS) {
     c->cur = 0;
     e = launch_init_bits(c->lat(0), c->rng(), c->stream);
@@ -805,23 +815,105 @@ int ising_sweep_blocks(ising_ctx* c, int n_sweeps, int measure_every, int block,
   return ok();
 }
 
-int ising_sw_step(ising_ctx* c, int n_steps, int measure_every) {
-  if (int st = check_ctx(c)) return st;
+namespace {
+
+// parent (L*L uint32) and mark (L*L bytes) for the cluster steps, on first use
+int cluster_scratch(ising_ctx* c) {
+  if (c->sw_parent) return ISING_OK;
+  void* p = nullptr;
+  if (int st = dev_alloc(&p, (size_t)c->N() * sizeof(uint32_t))) return st;
+  c->sw_parent = (uint32_t*)p;
+  if (int st = dev_alloc(&p, (size_t)c->N())) return st;
+  c->sw_flip = (uint8_t*)p;
+  return ISING_OK;
+}
+
+// floor((1 - e^{-2 beta}) 2^32), clamped: the bond probability of both cluster methods
+uint32_t bond_threshold(double beta) {
+  const double pb = 1.0 - std::exp(-2.0 * beta);
+  const double tf = std::floor(pb * 4294967296.0);
+  return tf >= 4294967295.0 ? 0xffffffffu : (tf <= 0.0 ? 0u : (uint32_t)tf);
+}
+
+int cluster_checks(ising_ctx* c, int64_t counter, int n_steps, int measure_every) {
   if (c->layout != ISING_LAYOUT_BITS) return fail(ISING_EINVAL, "cluster steps need the packed layout");
   if (n_steps < 0 || measure_every < 0) return fail(ISING_EINVAL, "negative count");
-  if (c->sw_steps + n_steps >= ((int64_t)1 << 32)) return fail(ISING_EINVAL, "step counter overflow");
+  if (counter + n_steps >= ((int64_t)1 << 32)) return fail(ISING_EINVAL, "step counter overflow");
   if ((int64_t)c->L * c->L >= ((int64_t)1 << 32)) return fail(ISING_EINVAL, "lattice too large");
-  NvtxRange nvtx("ising_sw_step");
-  if (!c->sw_parent) {
-    void* p = nullptr;
-    if (int st = dev_alloc(&p, (size_t)c->N() * sizeof(uint32_t))) return st;
-    c->sw_parent = (uint32_t*)p;
-    if (int st = dev_alloc(&p, (size_t)c->N())) return st;
-    c->sw_flip = (uint8_t*)p;
+  return ISING_OK;
+}
+
+int record_after_step(ising_ctx* c, int64_t t, int measure_every) {
+  if (measure_every > 0 && (t + 1) % measure_every == 0) {
+    const int64_t slot = c->rec_count % kRecCap;
+    if (int st = zero_records(c, c->rec_count, 1)) return st;
+    if (int st = launch_result(c, launch_measure_bits(c->lat(c->cur), c->rec + 2 * slot, c->stream), "measure"))
+      return st;
+    ++c->rec_count;
   }
-  const double pb = 1.0 - std::exp(-2.0 * c->beta);
-  const double tf = std::floor(pb * 4294967296.0);
-  const uint32_t thr = tf >= 4294967295.0 ? 0xffffffffu : (tf <= 0.0 ? 0u : (uint32_t)tf);
+  return ISING_OK;
+}
+
+}  // namespace
+
+int ising_wolff_set_limits(ising_ctx* c, int max_sites, int max_levels) {
+  if (int st = check_ctx(c)) return st;
+  if (max_sites < 0 || max_sites > kWolffMaxGrowSites)
+    return fail(ISING_EINVAL, "max_sites must be in 0..%d", kWolffMaxGrowSites);
+  if (max_levels < 0) return fail(ISING_EINVAL, "max_levels must be >= 0");
+  c->wolff_max_sites = max_sites;
+  c->wolff_max_levels = max_levels;
+  return ok();
+}
+
+int ising_wolff_step(ising_ctx* c, int n_steps, int measure_every) {
+  if (int st = check_ctx(c)) return st;
+  if (int st = cluster_checks(c, c->wolff_steps, n_steps, measure_every)) return st;
+  NvtxRange nvtx("ising_wolff_step");
+  if (int st = cluster_scratch(c)) return st;
+  if (!c->wolff) {
+    void* p = nullptr;
+    if (int st = dev_alloc(&p, sizeof(WolffCtl))) return st;
+    c->wolff = (WolffCtl*)p;
+    cudaError_t e = cudaMemsetAsync(c->wolff, 0, sizeof(WolffCtl), c->stream);
+    if (e) return fail(ISING_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  const uint32_t thr = bond_threshold(c->beta);
+  const RngParams rng = c->rng();
+  // default level bound: growth may take about as long as labelling the lattice
+  const int levels = c->wolff_max_levels > 0 ? c->wolff_max_levels
+                                             : (int)std::min<int64_t>(4096, 32 + (c->N() >> 16));
+  for (int k = 0; k < n_steps; ++k) {
+    const int64_t t = c->wolff_steps;
+    Timed tm(c);
+    cudaError_t e = launch_wolff_step(c->lat(c->cur), (uint32_t)t, thr, rng, c->sw_parent, c->sw_flip,
+                                      c->wolff_max_sites, levels, c->wolff, c->stream);
+    if (int st = launch_result(c, e, "Wolff step")) return st;
+    c->launches += 5;  // growth, two labelling kernels, resolve, apply
+    if (int st = record_after_step(c, t, measure_every)) return st;
+    ++c->wolff_steps;
+  }
+  return ok();
+}
+
+int ising_wolff_stats(ising_ctx* c, int64_t* last_size, int64_t* flipped, int64_t* grown, int64_t* labelled) {
+  if (int st = check_ctx(c)) return st;
+  WolffCtl h{};
+  if (c->wolff)
+    if (int st = to_host_sync(c, &h, c->wolff, sizeof(h))) return st;
+  if (last_size) *last_size = h.last_size;
+  if (flipped) *flipped = (int64_t)h.flipped;
+  if (grown) *grown = (int64_t)h.grown;
+  if (labelled) *labelled = (int64_t)h.labelled;
+  return ok();
+}
+
+int ising_sw_step(ising_ctx* c, int n_steps, int measure_every) {
+  if (int st = check_ctx(c)) return st;
+  if (int st = cluster_checks(c, c->sw_steps, n_steps, measure_every)) return st;
+  NvtxRange nvtx("ising_sw_step");
+  if (int st = cluster_scratch(c)) return st;
+  const uint32_t thr = bond_threshold(c->beta);
   const RngParams rng = c->rng();
   for (int k = 0; k < n_steps; ++k) {
     const int64_t t = c->sw_steps;
@@ -830,14 +922,7 @@ int ising_sw_step(ising_ctx* c, int n_steps, int measure_every) {
                                    c->stream);
     if (int st = launch_result(c, e, "cluster step")) return st;
     c->launches += 4;  // four kernels per cluster step
-    if (measure_every > 0 && (t + 1) % measure_every == 0) {
-      const int64_t slot = c->rec_count % kRecCap;
-      if (int st = zero_records(c, c->rec_count, 1)) return st;
-      if (int st = launch_result(c, launch_measure_bits(c->lat(c->cur), c->rec + 2 * slot, c->stream),
-                                 "measure"))
-        return st;
-      ++c->rec_count;
-    }
+    if (int st = record_after_step(c, t, measure_every)) return st;
     ++c->sw_steps;
   }
   return ok();

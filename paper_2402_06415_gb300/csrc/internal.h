@@ -153,6 +153,33 @@ cudaError_t nn_batch_block_pass(uint32_t* spins, const long long* off, const int
 cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
                            const RngParams& rng, uint32_t* parent, uint8_t* flip, cudaStream_t s);
 
+// Connected components of the active bonds (sw.cu): bond b active iff its
+// spins agree and word (b & 3) of Philox(b >> 2, step, replica, bond_tag << 16)
+// is below thr.  Leaves a forest in parent (tiled path: every site points at a
+// local root, mark = 2 at local roots); skipped when gate is non-null and *gate == 0.
+bool sw_tiled(int L);
+cudaError_t launch_cluster_labels(const BitsLattice& lat, uint32_t step, uint32_t thr, uint32_t bond_tag,
+                                  const RngParams& rng, uint32_t* parent, uint8_t* mark,
+                                  const uint32_t* gate, cudaStream_t s);
+
+// Wolff single-cluster step state on the device (wolff.cu).
+struct WolffCtl {
+  uint32_t need_label;   // 1: growth gave up, the labelling kernels run
+  uint32_t seed_site;    // this step's seed
+  uint32_t last_size;    // sites flipped by the last step
+  uint32_t gave_up_run;  // consecutive steps without a completed growth
+  unsigned long long flipped;   // sites flipped, all steps
+  unsigned long long grown;     // steps completed by growth
+  unsigned long long labelled;  // steps completed by labelling
+};
+constexpr int kWolffMaxGrowSites = 16384;
+size_t wolff_grow_smem(int max_sites);
+// One Wolff step: growth from the seed bounded by max_sites (0: never grow)
+// and max_levels, then (gated on ctl->need_label) labelling and the flip.
+cudaError_t launch_wolff_step(const BitsLattice& lat, uint32_t step, uint32_t thr, const RngParams& rng,
+                              uint32_t* parent, uint8_t* mark, int max_sites, int max_levels, WolffCtl* ctl,
+                              cudaStream_t s);
+
 // Sets the message returned by ising_last_error() on the calling thread.
 void set_last_error(const char* msg);
 

@@ -69,7 +69,12 @@ __device__ __forceinline__ void unite(uint32_t* parent, uint32_t a, uint32_t b) 
   }
 }
 
-__global__ void k_sw_init(uint32_t* __restrict__ parent, long long N) {
+// Labelling kernels may be gated on a device flag (Wolff steps label the
+// lattice only when the bounded growth from the seed gave up); null = always run.
+__device__ __forceinline__ bool gated_off(const uint32_t* gate) { return gate && *gate == 0; }
+
+__global__ void k_sw_init(uint32_t* __restrict__ parent, long long N, const uint32_t* gate) {
+  if (gated_off(gate)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x)
     parent[i] = (uint32_t)i;
@@ -80,11 +85,12 @@ __global__ void k_sw_init(uint32_t* __restrict__ parent, long long N) {
 __global__ void __launch_bounds__(256) k_sw_bonds(const uint32_t* __restrict__ planes, int L,
                                                   int Wc, uint32_t step, uint32_t thr,
                                                   RngParams rng, uint32_t* __restrict__ parent,
-                                                  FastDiv fL) {
+                                                  FastDiv fL, uint32_t bond_tag, const uint32_t* gate) {
+  if (gated_off(gate)) return;
   const long long N = (long long)L * L;
   for (long long pr = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * pr < N;
        pr += (long long)gridDim.x * blockDim.x) {
-    const uint4 r = philox10_rk(make_uint4((uint32_t)pr, step, rng.replica, kTagSWBond << 16),
+    const uint4 r = philox10_rk(make_uint4((uint32_t)pr, step, rng.replica, bond_tag << 16),
                                 rng.rk0, rng.rk1);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -184,7 +190,9 @@ __device__ __forceinline__ void sunite(uint32_t* lab, uint32_t a, uint32_t b) {
 __global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __restrict__ planes, int L, int Wc,
                                                            uint32_t step, uint32_t thr, RngParams rng,
                                                            uint32_t* __restrict__ parent,
-                                                           uint8_t* __restrict__ mark) {
+                                                           uint8_t* __restrict__ mark, uint32_t bond_tag,
+                                                           const uint32_t* gate) {
+  if (gated_off(gate)) return;
   __shared__ uint32_t lab[kTileSites];
   // per site: bit 0 spin, bit 1 bond li -> li + 1 active, bit 2 bond li -> li + TX
   // active (bonds inside the tile only)
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __res
   for (int pp = threadIdx.x; pp < kTileSites / 2; pp += blockDim.x) {
     const int ly = pp / (kTileX / 2), lx0 = 2 * (pp - ly * (kTileX / 2));
     const long long a0 = (long long)(y0 + ly) * L + x0 + lx0;
-    const uint4 r = philox10_rk(make_uint4((uint32_t)(a0 >> 1), step, rng.replica, kTagSWBond << 16),
+    const uint4 r = philox10_rk(make_uint4((uint32_t)(a0 >> 1), step, rng.replica, bond_tag << 16),
                                 rng.rk0, rng.rk1);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -323,7 +331,9 @@ __global__ void __launch_bounds__(256) k_sw_apply2(uint32_t* __restrict__ planes
 // dir 1 from the last row; periodic), united in the global forest.
 __global__ void __launch_bounds__(256) k_sw_edges(const uint32_t* __restrict__ planes, int L, int Wc,
                                                   uint32_t step, uint32_t thr, RngParams rng,
-                                                  uint32_t* __restrict__ parent) {
+                                                  uint32_t* __restrict__ parent, uint32_t bond_tag,
+                                                  const uint32_t* gate) {
+  if (gated_off(gate)) return;
   const int tiles_x = L / kTileX;
   const long long n_tiles = (long long)tiles_x * (L / kTileY);
   const long long total = n_tiles * (kTileX + kTileY);
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(256) k_sw_edges(const uint32_t* __restrict__ p
     const int yn = dir == 0 ? y : (y + 1 == L ? 0 : y + 1);
     if (bit_at(planes, L, Wc, x, y) != bit_at(planes, L, Wc, xn, yn)) continue;
     const long long a = (long long)y * L + x;
-    const uint4 r = philox10_rk(make_uint4((uint32_t)(a >> 1), step, rng.replica, kTagSWBond << 16),
+    const uint4 r = philox10_rk(make_uint4((uint32_t)(a >> 1), step, rng.replica, bond_tag << 16),
                                 rng.rk0, rng.rk1);
     const int wsel = 2 * (int)(a & 1) + dir;
     const uint32_t u = wsel == 0 ? r.x : (wsel == 1 ? r.y : (wsel == 2 ? r.z : r.w));
@@ -364,22 +374,39 @@ int grid_of(long long items) {
 
 }  // namespace
 
+bool sw_tiled(int L) { return L % kTileX == 0 && L % kTileY == 0 && L >= 2048; }
+
+cudaError_t launch_cluster_labels(const BitsLattice& lat, uint32_t step, uint32_t thr, uint32_t bond_tag,
+                                  const RngParams& rng, uint32_t* parent, uint8_t* mark,
+                                  const uint32_t* gate, cudaStream_t s) {
+  const long long N = (long long)lat.L * lat.L;
+  cudaError_t e;
+  // tiles only pay when there are enough of them to fill the GPU (>= 512 CTAs)
+  if (sw_tiled(lat.L)) {
+    const long long tiles = (long long)(lat.L / kTileX) * (lat.L / kTileY);
+    k_sw_local<<<(unsigned)tiles, kTileThreads, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
+                                                        mark, bond_tag, gate);
+    e = cudaGetLastError();
+    if (e) return e;
+    k_sw_edges<<<grid_of(tiles * (kTileX + kTileY)), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng,
+                                                                  parent, bond_tag, gate);
+    return cudaGetLastError();
+  }
+  k_sw_init<<<grid_of(N), 256, 0, s>>>(parent, N, gate);
+  e = cudaGetLastError();
+  if (e) return e;
+  k_sw_bonds<<<grid_of((N + 1) / 2), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
+                                                  make_fastdiv((uint32_t)lat.L), bond_tag, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
                            const RngParams& rng, uint32_t* parent, uint8_t* flip,
                            cudaStream_t s) {
   const long long N = (long long)lat.L * lat.L;
-  cudaError_t e;
-  // tiles only pay when there are enough of them to fill the GPU (>= 512 CTAs)
-  if (lat.L % kTileX == 0 && lat.L % kTileY == 0 && lat.L >= 2048) {
-    const long long tiles = (long long)(lat.L / kTileX) * (lat.L / kTileY);
-    k_sw_local<<<(unsigned)tiles, kTileThreads, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
-                                                        flip);
-    e = cudaGetLastError();
-    if (e) return e;
-    k_sw_edges<<<grid_of(tiles * (kTileX + kTileY)), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng,
-                                                                  parent);
-    e = cudaGetLastError();
-    if (e) return e;
+  cudaError_t e = launch_cluster_labels(lat, step, thr, kTagSWBond, rng, parent, flip, nullptr, s);
+  if (e) return e;
+  if (sw_tiled(lat.L)) {
     k_sw_resolve<<<grid_of(N), 256, 0, s>>>(parent, flip, N, step, rng);
     e = cudaGetLastError();
     if (e) return e;
@@ -387,14 +414,6 @@ cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
         lat.planes, lat.L, lat.Wc, parent, flip, make_fastdiv((uint32_t)lat.L * (uint32_t)lat.Wc),
         make_fastdiv((uint32_t)lat.Wc));
     return cudaGetLastError();
-  } else {
-    k_sw_init<<<grid_of(N), 256, 0, s>>>(parent, N);
-    e = cudaGetLastError();
-    if (e) return e;
-    k_sw_bonds<<<grid_of((N + 1) / 2), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
-                                                    make_fastdiv((uint32_t)lat.L));
-    e = cudaGetLastError();
-    if (e) return e;
   }
   k_sw_roots<<<grid_of(N), 256, 0, s>>>(parent, N, step, rng, flip);
   e = cudaGetLastError();

@@ -1,0 +1,125 @@
+"""Wolff single-cluster step on the GPU against the CPU oracle.
+
+A step is fixed by (seed, step, replica, spins): the seed site and the bonds
+come from the counter-based generator and the flipped cluster is the seed's
+connected component, so both ways the GPU finds it (bounded growth from the
+seed in one CTA, or connected components of the whole lattice) must give the
+oracle's configuration bit for bit, and the same cluster size.  The limits
+parametrise which way runs: growth only, labelling only, and a mix in which
+growth gives up part way.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2402_06415_gb300 as ising
+
+pytestmark = pytest.mark.gpu
+
+BETA_C = 0.5 * np.log(1.0 + np.sqrt(2.0))
+
+# (max_sites, max_levels): default; never grow; grow with generous bounds; tiny bounds
+LIMITS = {"default": None, "label": (0, 0), "grow": (16384, 100000), "tiny": (64, 3)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    oracle.build()
+    ising.lib()
+
+
+def _run(L, beta, seed, n, limits, replica=0):
+    s = oracle.init(L, seed, replica=replica)
+    sizes = []
+    with ising.Lattice(L, beta, seed=seed, replica=replica) as lat:
+        lat.set_spins(s)
+        if LIMITS[limits] is not None:
+            lat.wolff_set_limits(*LIMITS[limits])
+        for _ in range(n):
+            lat.wolff_step(1, 1)
+            sizes.append(lat.wolff_stats()["last_size"])
+        got = lat.spins()
+        E, M = lat.series(n)
+        st = lat.wolff_stats()
+    E_ref, M_ref, C_ref = oracle.wolff_steps(s, beta, seed, n, replica=replica)
+    assert np.array_equal(got, s)
+    assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
+    assert sizes == list(C_ref)
+    assert st["grown"] + st["labelled"] == n
+    assert st["flipped"] == int(C_ref.sum())
+    return st
+
+
+@pytest.mark.parametrize("limits", list(LIMITS))
+@pytest.mark.parametrize("L", [4, 6, 62, 64, 130, 256])
+@pytest.mark.parametrize("beta", [1e-9, 0.3, BETA_C, 0.7, 50.0])
+def test_wolff_bit_exact(L, beta, limits):
+    st = _run(L, beta, 0xF00D0000 + L, 8, limits, replica=1)
+    if limits == "label":
+        assert st["grown"] == 0
+    if limits == "grow" and L * L <= 16384 // 4:
+        assert st["labelled"] == 0
+
+
+@pytest.mark.parametrize("limits", ["default", "label", "tiny"])
+@pytest.mark.parametrize("L,beta", [(2048, BETA_C), (2560, 0.3), (2048, 0.7)])
+def test_wolff_tiled_labelling_bit_exact(L, beta, limits):
+    """Lattices of >= 2048 sites a side that are multiples of the 128 x 64 tile
+    label through the shared-memory tiles."""
+    _run(L, beta, 60 + L, 4, limits)
+
+
+def test_wolff_growth_used_away_from_criticality():
+    """At beta = 0.3 clusters are small: every step finishes by growth."""
+    st = _run(1024, 0.3, 9, 40, "default")
+    assert st["labelled"] == 0 and st["grown"] == 40
+
+
+def test_wolff_counter_and_seed_reset():
+    L, beta, seed = 96, BETA_C, 5
+    s = oracle.init(L, seed)
+    with ising.Lattice(L, beta, seed=seed) as lat:
+        lat.wolff_step(3)
+        lat.sweep(2)
+        lat.wolff_step(2)
+        got = lat.spins()
+        lat.seed(seed)  # back to the start: fresh spins and step counter
+        assert lat.wolff_stats()["flipped"] == 0
+        lat.wolff_step(3)
+        again = lat.spins()
+    t = s.copy()
+    oracle.wolff_steps(t, beta, seed, 3)
+    ref3 = t.copy()
+    oracle.sweep(t, beta, seed, 2)
+    oracle.wolff_steps(t, beta, seed, 2, step0=3)
+    assert np.array_equal(got, t)
+    assert np.array_equal(again, ref3)
+
+
+def test_wolff_large_lattice_steps():
+    """A 4096^2 lattice (16.8 M sites) at beta_c: eight steps bit for bit."""
+    L, seed, n = 4096, 8, 8
+    s = oracle.init(L, seed)
+    with ising.Lattice(L, BETA_C, seed=seed) as lat:
+        lat.wolff_step(n, 1)
+        got = lat.spins()
+        E, M = lat.series(n)
+    E_ref, M_ref, _ = oracle.wolff_steps(s, BETA_C, seed, n)
+    assert np.array_equal(got, s)
+    assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
+
+
+def test_wolff_rejects_bad_arguments():
+    with ising.Lattice(16, 0.4) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.wolff_set_limits(16385)
+        with pytest.raises(ising.IsingError):
+            lat.wolff_set_limits(-1)
+        with pytest.raises(ising.IsingError):
+            lat.wolff_step(-1)
+    with ising.Lattice(16, 0.4, ising.ISING_LAYOUT_I8) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.wolff_step(1)
