@@ -313,6 +313,16 @@ int ising_sweep_blocks(ising_ctx* ctx, int n_sweeps, int measure_every, int bloc
  * rejected with ISING_EINVAL.  Async. */
 int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);
 
+/* How cluster steps (ising_sw_step, ising_wolff_step) run: AUTO = one
+ * persistent cooperative kernel per call for L < 2048 (three grid-barrier
+ * phases per step: reset, unions, flips; barrier waits give up after about 2 s
+ * and later synchronising calls then fail with ISING_ETIMEOUT), a few kernels
+ * per step from L = 2048 (tiled labelling in shared memory; Wolff first tries
+ * growth from the seed).  KERNELS / PERSISTENT force one way.  The chain is
+ * the same either way, bit for bit. */
+enum { ISING_CLUSTER_AUTO = 0, ISING_CLUSTER_KERNELS = 1, ISING_CLUSTER_PERSISTENT = 2 };
+int ising_cluster_set_mode(ising_ctx* ctx, int mode);
+
 /* Wolff single-cluster steps (Wolff, PRL 62, 361 (1989)) on the packed layout:
  * the paper's Discussion names cluster algorithms as the next step for its
  * Monte Carlo.  Step n:
@@ -327,10 +337,11 @@ int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);
  * (E, M) after every such step into the series ring.  Async. */
 int ising_wolff_step(ising_ctx* ctx, int n_steps, int measure_every);
 
-/* How a Wolff step finds its cluster: growth from the seed in one CTA while the
- * cluster has at most max_sites sites (0..16384; 0 = never) and max_levels
- * breadth-first levels (0 = a default that grows with L), otherwise connected
- * components of the whole lattice.  Changes cost only, never the chain. */
+/* How a Wolff step of the kernel path (ising_cluster_set_mode) finds its
+ * cluster: growth from the seed in one CTA while the cluster has at most
+ * max_sites sites (0..16384; 0 = never) and max_levels breadth-first levels
+ * (0 = a default that grows with L), otherwise connected components of the
+ * whole lattice.  Changes cost only, never the chain. */
 int ising_wolff_set_limits(ising_ctx* ctx, int max_sites, int max_levels);
 
 /* Sites flipped by the last Wolff step, by all steps since ising_seed, and how

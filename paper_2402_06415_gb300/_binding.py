@@ -24,6 +24,9 @@ ISING_EINTERNAL = -5
 
 ISING_LAYOUT_I8 = 0
 ISING_LAYOUT_BITS = 1
+ISING_CLUSTER_AUTO = 0
+ISING_CLUSTER_KERNELS = 1
+ISING_CLUSTER_PERSISTENT = 2
 
 ISING_KERNEL_AUTO = 0
 ISING_KERNEL_HALF = 1
@@ -99,6 +102,7 @@ _PROTOS = [
     ("ising_sweep_blocks", _i, [_p, _i, _i, _i, _i]),
     ("ising_sw_step", _i, [_p, _i, _i]),
     ("ising_wolff_step", _i, [_p, _i, _i]),
+    ("ising_cluster_set_mode", _i, [_p, _i]),
     ("ising_wolff_set_limits", _i, [_p, _i, _i]),
     ("ising_wolff_stats", _i, [_p, _p, _p, _p, _p]),
     ("ising_nn_param_count", _i, []),
@@ -397,6 +401,10 @@ class Lattice:
     def wolff_step(self, n: int, measure_every: int = 0):
         """n Wolff single-cluster steps (packed layout only)."""
         ising_wolff_step(self.ctx, n, measure_every)
+
+    def cluster_set_mode(self, mode: int):
+        """ISING_CLUSTER_AUTO / _KERNELS / _PERSISTENT for sw_step and wolff_step."""
+        _check(lib().ising_cluster_set_mode(self.ctx, int(mode)))
 
     def wolff_set_limits(self, max_sites: int, max_levels: int = 0):
         ising_wolff_set_limits(self.ctx, max_sites, max_levels)

@@ -95,6 +95,8 @@ struct ising_ctx {
   WolffCtl* wolff = nullptr;  // Wolff step state (parent / mark scratch shared with Swendsen-Wang)
   int64_t wolff_steps = 0;
   int wolff_max_sites = kWolffMaxGrowSites, wolff_max_levels = 0;
+  int cluster_mode = ISING_CLUSTER_AUTO;
+  GridCtl* cluster_gctl = nullptr;  // barrier of the persistent cluster kernel
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
@@ -135,7 +137,9 @@ void free_all(ising_ctx* c) {
   cudaFree(c->sw_parent);
   cudaFree(c->sw_flip);
   cudaFree(c->wolff);
+  cudaFree(c->cluster_gctl);
   c->wolff = nullptr;
+  c->cluster_gctl = nullptr;
   c->sw_parent = nullptr;
   c->sw_flip = nullptr;
   c->nn_w = c->nn_w2t = nullptr;
@@ -338,6 +342,12 @@ int to_host_sync(ising_ctx* c, void* dst, const void* src, size_t bytes) {
   if (fault("copy")) return fail(ISING_ECUDA, "device-to-host copy failed (injected)");
   CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->cluster_gctl) {
+    // a grid barrier of the persistent cluster kernel that gave up stays recorded until the next seed
+    int status = 0;
+    CUDA_TRY(cudaMemcpy(&status, &c->cluster_gctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) return fail(ISING_ETIMEOUT, "grid barrier timed out in the persistent cluster kernel");
+  }
   return ISING_OK;
 }
 
@@ -450,6 +460,10 @@ int ising_seed(ising_ctx* c, uint64_t seed) {
   cudaError_t e;
   if (c->wolff) {
     e = cudaMemsetAsync(c->wolff, 0, sizeof(WolffCtl), c->stream);
+    if (e) return fail(ISING_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  if (c->cluster_gctl) {
+    e = cudaMemsetAsync(c->cluster_gctl, 0, sizeof(GridCtl), c->stream);
     if (e) return fail(ISING_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
   if (c->layout == ISING_LAYOUT_BITS) {
@@ -843,6 +857,33 @@ int cluster_checks(ising_ctx* c, int64_t counter, int n_steps, int measure_every
   return ISING_OK;
 }
 
+// Whether cluster steps on this context run as one persistent kernel per call.
+bool cluster_persistent(const ising_ctx* c) {
+  if (c->cluster_mode == ISING_CLUSTER_PERSISTENT) return true;
+  if (c->cluster_mode == ISING_CLUSTER_KERNELS) return false;
+  return !sw_tiled(c->L);
+}
+
+// n persistent-kernel cluster steps from step0, records included.
+int cluster_persist_run(ising_ctx* c, bool wolff, int64_t step0, int n, int measure_every) {
+  if (n <= 0) return ISING_OK;
+  if (!c->cluster_gctl) {
+    void* p = nullptr;
+    if (int st = dev_alloc(&p, sizeof(GridCtl))) return st;
+    c->cluster_gctl = (GridCtl*)p;
+    CUDA_TRY(cudaMemsetAsync(c->cluster_gctl, 0, sizeof(GridCtl), c->stream));
+  }
+  Timed tm(c);
+  cudaError_t e = launch_cluster_persist(c->lat(c->cur), wolff, (uint32_t)step0, n, measure_every,
+                                         bond_threshold(c->beta), c->rng(), c->sw_parent, c->rec,
+                                         c->rec_count % kRecCap, kRecCap, c->cluster_gctl, c->wolff, c->sms,
+                                         c->stream);
+  if (int st = launch_result(c, e, "persistent cluster steps")) return st;
+  if (measure_every > 0)
+    c->rec_count += (step0 + n) / measure_every - step0 / measure_every;
+  return ISING_OK;
+}
+
 int record_after_step(ising_ctx* c, int64_t t, int measure_every) {
   if (measure_every > 0 && (t + 1) % measure_every == 0) {
     const int64_t slot = c->rec_count % kRecCap;
@@ -855,6 +896,13 @@ int record_after_step(ising_ctx* c, int64_t t, int measure_every) {
 }
 
 }  // namespace
+
+int ising_cluster_set_mode(ising_ctx* c, int mode) {
+  if (int st = check_ctx(c)) return st;
+  if (mode < ISING_CLUSTER_AUTO || mode > ISING_CLUSTER_PERSISTENT) return fail(ISING_EINVAL, "unknown cluster mode");
+  c->cluster_mode = mode;
+  return ok();
+}
 
 int ising_wolff_set_limits(ising_ctx* c, int max_sites, int max_levels) {
   if (int st = check_ctx(c)) return st;
@@ -877,6 +925,11 @@ int ising_wolff_step(ising_ctx* c, int n_steps, int measure_every) {
     c->wolff = (WolffCtl*)p;
     cudaError_t e = cudaMemsetAsync(c->wolff, 0, sizeof(WolffCtl), c->stream);
     if (e) return fail(ISING_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+  }
+  if (cluster_persistent(c)) {
+    if (int st = cluster_persist_run(c, true, c->wolff_steps, n_steps, measure_every)) return st;
+    c->wolff_steps += n_steps;
+    return ok();
   }
   const uint32_t thr = bond_threshold(c->beta);
   const RngParams rng = c->rng();
@@ -913,6 +966,11 @@ int ising_sw_step(ising_ctx* c, int n_steps, int measure_every) {
   if (int st = cluster_checks(c, c->sw_steps, n_steps, measure_every)) return st;
   NvtxRange nvtx("ising_sw_step");
   if (int st = cluster_scratch(c)) return st;
+  if (cluster_persistent(c)) {
+    if (int st = cluster_persist_run(c, false, c->sw_steps, n_steps, measure_every)) return st;
+    c->sw_steps += n_steps;
+    return ok();
+  }
   const uint32_t thr = bond_threshold(c->beta);
   const RngParams rng = c->rng();
   for (int k = 0; k < n_steps; ++k) {

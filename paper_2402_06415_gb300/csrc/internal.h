@@ -43,6 +43,15 @@ struct RngParams {
   uint32_t tm4[32], tm8[32];
 };
 
+// Barrier state of a persistent cooperative kernel (ising_device.cuh's
+// grid_sync_bounded): arrival count, generation, time-out status.
+struct GridCtl {
+  unsigned int count;
+  unsigned int gen;
+  int status;
+  int pad;
+};
+
 // Per-device memo for launch settings that CUDA keeps per device (a kernel's
 // dynamic shared-memory limit, its occupancy): one slot per device ordinal,
 // atomic so concurrent host threads may race on it harmlessly.
@@ -179,6 +188,17 @@ size_t wolff_grow_smem(int max_sites);
 cudaError_t launch_wolff_step(const BitsLattice& lat, uint32_t step, uint32_t thr, const RngParams& rng,
                               uint32_t* parent, uint8_t* mark, int max_sites, int max_levels, WolffCtl* ctl,
                               cudaStream_t s);
+
+// Cluster steps as one persistent cooperative kernel (cluster_persist.cu):
+// n_steps Swendsen-Wang (wolff = false) or Wolff steps from step0, each a
+// connected-component labelling of the whole lattice; records (E, M) after
+// step t when (t + 1) % measure_every == 0 into rec slots (rec0 + k) % rec_cap.
+// Grid barriers give up after kClusterSpinLimit cycles and set gctl->status.
+constexpr long long kClusterSpinLimit = 4000000000LL;  // ~2 s of SM clock per barrier
+cudaError_t launch_cluster_persist(const BitsLattice& lat, bool wolff, uint32_t step0, int n_steps,
+                                   int measure_every, uint32_t thr, const RngParams& rng, uint32_t* parent,
+                                   unsigned long long* rec, long long rec0, long long rec_cap, GridCtl* gctl,
+                                   WolffCtl* wctl, int sms, cudaStream_t s);
 
 // Sets the message returned by ising_last_error() on the calling thread.
 void set_last_error(const char* msg);

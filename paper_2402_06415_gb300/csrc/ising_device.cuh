@@ -15,6 +15,8 @@
 #pragma once
 #include <cstdint>
 
+#include "internal.h"
+
 namespace ising {
 
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
@@ -175,12 +177,7 @@ __device__ __forceinline__ bool bounded_wait_while_eq(const volatile unsigned in
 // generation counter + arrival count in global memory, a tight bounded spin
 // (clock64 budget `limit`).  On time-out it records 1 in ctl->status; every
 // thread of the CTA gets the same answer (read once into shared memory).
-struct GridCtl {
-  unsigned int count;
-  unsigned int gen;
-  int status;
-  int pad;
-};
+// (GridCtl itself, a plain struct the host allocates, is in internal.h.)
 
 __device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
   unsigned int old;

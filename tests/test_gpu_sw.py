@@ -25,13 +25,15 @@ def _cuda():
     ising.lib()
 
 
+@pytest.mark.parametrize("mode", [ising.ISING_CLUSTER_KERNELS, ising.ISING_CLUSTER_PERSISTENT])
 @pytest.mark.parametrize("L", [4, 6, 62, 64, 128, 130, 256, 384])
 @pytest.mark.parametrize("beta", [1e-9, 0.3, BETA_C, 0.7, 50.0])
-def test_sw_bit_exact(L, beta):
+def test_sw_bit_exact(L, beta, mode):
     seed, n = 0xBEEF0000 + L, 6
     s = oracle.init(L, seed)
     with ising.Lattice(L, beta, seed=seed) as lat:
         lat.set_spins(s)
+        lat.cluster_set_mode(mode)
         lat.sw_step(n, 1)
         got = lat.spins()
         E, M = lat.series(n)
@@ -56,6 +58,25 @@ def test_sw_after_metropolis_and_replica():
     oracle.sweep(s, beta, seed, 2, t0=4, replica=3)
     oracle.sw_steps(s, beta, seed, 1, step0=5, replica=3)
     assert np.array_equal(got, s)
+
+
+@pytest.mark.parametrize("L", [10, 96, 1000])
+def test_sw_persistent_sparse_records_and_resume(L):
+    """Persistent and kernel calls in turn on one step counter; records every
+    fourth step, starting mid-run."""
+    beta, seed = BETA_C, 70 + L
+    s = oracle.init(L, seed)
+    with ising.Lattice(L, beta, seed=seed) as lat:
+        for mode, n in [(ising.ISING_CLUSTER_PERSISTENT, 5), (ising.ISING_CLUSTER_KERNELS, 2),
+                        (ising.ISING_CLUSTER_PERSISTENT, 11)]:
+            lat.cluster_set_mode(mode)
+            lat.sw_step(n, 4)
+        got = lat.spins()
+        E, M = lat.series(18 // 4)
+    E_ref, M_ref, _ = oracle.sw_steps(s, beta, seed, 18)
+    assert np.array_equal(got, s)
+    idx = [t for t in range(18) if (t + 1) % 4 == 0]
+    assert np.array_equal(E, E_ref[idx]) and np.array_equal(M, M_ref[idx])
 
 
 @pytest.mark.parametrize("L,beta", [(2048, BETA_C), (2560, 0.3), (2048, 0.7)])

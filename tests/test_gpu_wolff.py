@@ -18,8 +18,11 @@ pytestmark = pytest.mark.gpu
 
 BETA_C = 0.5 * np.log(1.0 + np.sqrt(2.0))
 
-# (max_sites, max_levels): default; never grow; grow with generous bounds; tiny bounds
-LIMITS = {"default": None, "label": (0, 0), "grow": (16384, 100000), "tiny": (64, 3)}
+KERNELS, PERSISTENT = ising.ISING_CLUSTER_KERNELS, ising.ISING_CLUSTER_PERSISTENT
+# (mode, (max_sites, max_levels)): the persistent kernel; the kernel path with the
+# default bounds, never growing, growing with generous bounds, tiny bounds
+LIMITS = {"persistent": (PERSISTENT, None), "default": (KERNELS, None), "label": (KERNELS, (0, 0)),
+          "grow": (KERNELS, (16384, 100000)), "tiny": (KERNELS, (64, 3))}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,8 +39,10 @@ def _run(L, beta, seed, n, limits, replica=0):
     sizes = []
     with ising.Lattice(L, beta, seed=seed, replica=replica) as lat:
         lat.set_spins(s)
-        if LIMITS[limits] is not None:
-            lat.wolff_set_limits(*LIMITS[limits])
+        mode, lim = LIMITS[limits]
+        lat.cluster_set_mode(mode)
+        if lim is not None:
+            lat.wolff_set_limits(*lim)
         for _ in range(n):
             lat.wolff_step(1, 1)
             sizes.append(lat.wolff_stats()["last_size"])
@@ -58,13 +63,13 @@ def _run(L, beta, seed, n, limits, replica=0):
 @pytest.mark.parametrize("beta", [1e-9, 0.3, BETA_C, 0.7, 50.0])
 def test_wolff_bit_exact(L, beta, limits):
     st = _run(L, beta, 0xF00D0000 + L, 8, limits, replica=1)
-    if limits == "label":
+    if limits in ("label", "persistent"):
         assert st["grown"] == 0
     if limits == "grow" and L * L <= 16384 // 4:
         assert st["labelled"] == 0
 
 
-@pytest.mark.parametrize("limits", ["default", "label", "tiny"])
+@pytest.mark.parametrize("limits", ["default", "label", "tiny", "persistent"])
 @pytest.mark.parametrize("L,beta", [(2048, BETA_C), (2560, 0.3), (2048, 0.7)])
 def test_wolff_tiled_labelling_bit_exact(L, beta, limits):
     """Lattices of >= 2048 sites a side that are multiples of the 128 x 64 tile
@@ -73,7 +78,8 @@ def test_wolff_tiled_labelling_bit_exact(L, beta, limits):
 
 
 def test_wolff_growth_used_away_from_criticality():
-    """At beta = 0.3 clusters are small: every step finishes by growth."""
+    """At beta = 0.3 clusters are small: on the kernel path every step
+    finishes by growth."""
     st = _run(1024, 0.3, 9, 40, "default")
     assert st["labelled"] == 0 and st["grown"] == 40
 
@@ -99,6 +105,26 @@ def test_wolff_counter_and_seed_reset():
     assert np.array_equal(again, ref3)
 
 
+@pytest.mark.parametrize("L", [6, 64, 200])
+def test_wolff_paths_interleaved_and_sparse_records(L):
+    """Persistent and kernel steps in turn (one step counter), records every
+    third step starting mid-run: the series holds the oracle's E, M at steps
+    t with (t + 1) % 3 == 0."""
+    beta, seed = BETA_C, 31 + L
+    s = oracle.init(L, seed)
+    with ising.Lattice(L, beta, seed=seed) as lat:
+        for k, (mode, n) in enumerate([(PERSISTENT, 4), (KERNELS, 3), (PERSISTENT, 7), (KERNELS, 1),
+                                       (PERSISTENT, 5)]):
+            lat.cluster_set_mode(mode)
+            lat.wolff_step(n, 3)
+        got = lat.spins()
+        E, M = lat.series(20 // 3)
+    E_ref, M_ref, _ = oracle.wolff_steps(s, beta, seed, 20)
+    assert np.array_equal(got, s)
+    idx = [t for t in range(20) if (t + 1) % 3 == 0]
+    assert np.array_equal(E, E_ref[idx]) and np.array_equal(M, M_ref[idx])
+
+
 def test_wolff_large_lattice_steps():
     """A 4096^2 lattice (16.8 M sites) at beta_c: eight steps bit for bit."""
     L, seed, n = 4096, 8, 8
@@ -120,6 +146,8 @@ def test_wolff_rejects_bad_arguments():
             lat.wolff_set_limits(-1)
         with pytest.raises(ising.IsingError):
             lat.wolff_step(-1)
+        with pytest.raises(ising.IsingError):
+            lat.cluster_set_mode(3)
     with ising.Lattice(16, 0.4, ising.ISING_LAYOUT_I8) as lat:
         with pytest.raises(ising.IsingError):
             lat.wolff_step(1)
