@@ -875,7 +875,7 @@ int cluster_persist_run(ising_ctx* c, bool wolff, int64_t step0, int n, int meas
   }
   Timed tm(c);
   cudaError_t e = launch_cluster_persist(c->lat(c->cur), wolff, (uint32_t)step0, n, measure_every,
-                                         bond_threshold(c->beta), c->rng(), c->sw_parent, c->rec,
+                                         bond_threshold(c->beta), c->rng(), c->sw_parent, c->sw_flip, c->rec,
                                          c->rec_count % kRecCap, kRecCap, c->cluster_gctl, c->wolff, c->sms,
                                          c->stream);
   if (int st = launch_result(c, e, "persistent cluster steps")) return st;

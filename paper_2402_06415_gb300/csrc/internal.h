@@ -197,7 +197,8 @@ cudaError_t launch_wolff_step(const BitsLattice& lat, uint32_t step, uint32_t th
 constexpr long long kClusterSpinLimit = 4000000000LL;  // ~2 s of SM clock per barrier
 cudaError_t launch_cluster_persist(const BitsLattice& lat, bool wolff, uint32_t step0, int n_steps,
                                    int measure_every, uint32_t thr, const RngParams& rng, uint32_t* parent,
-                                   unsigned long long* rec, long long rec0, long long rec_cap, GridCtl* gctl,
+                                   uint8_t* mark, unsigned long long* rec, long long rec0, long long rec_cap,
+                                   GridCtl* gctl,
                                    WolffCtl* wctl, int sms, cudaStream_t s);
 
 // Sets the message returned by ising_last_error() on the calling thread.
