@@ -1,8 +1,8 @@
 // Cluster steps (Swendsen-Wang and Wolff) as one persistent cooperative
-// kernel per call, for lattices below the tiled-labelling size.  Below L = 2048
-// a step's kernels each have little work and the step is bound by launch
-// latency; here every CTA stays resident and a step is three phases between
-// bounded grid barriers:
+// kernel per call, for small lattices (by default L < 512), where a step's
+// kernels each have little work and the step is bound by launch latency; here
+// every CTA stays resident and a step is three phases between bounded grid
+// barriers:
 //   1. one warp per row draws the row's bonds and labels its horizontal runs
 //      (each site's parent = the first site of its run, by a warp max-scan, no
 //      atomics), and the previous step's observables are summed;
