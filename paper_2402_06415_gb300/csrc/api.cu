@@ -857,14 +857,14 @@ int cluster_checks(ising_ctx* c, int64_t counter, int n_steps, int measure_every
   return ISING_OK;
 }
 
-constexpr int kClusterPersistMaxL = 512;
+constexpr int kClusterPersistMaxL = 768;
 
 // Whether cluster steps on this context run as one persistent kernel per call.
 bool cluster_persistent(const ising_ctx* c) {
   if (c->cluster_mode == ISING_CLUSTER_PERSISTENT) return true;
   if (c->cluster_mode == ISING_CLUSTER_KERNELS) return false;
-  // measured on GB300 at beta_c: one launch wins up to L = 256 (48 vs 64 us per
-  // step), the kernel-per-phase path from L = 1024 (137 vs 189 us)
+  // measured on GB300 at beta_c: one launch wins up to L = 512 (70 vs 76 us per
+  // step), the kernel-per-phase path at L = 1024 (137 vs 189 us)
   return c->L < kClusterPersistMaxL;
 }
 

@@ -1,5 +1,5 @@
 // Cluster steps (Swendsen-Wang and Wolff) as one persistent cooperative
-// kernel per call, for small lattices (by default L < 512), where a step's
+// kernel per call, for small lattices (by default L < 768), where a step's
 // kernels each have little work and the step is bound by launch latency; here
 // every CTA stays resident and a step is three phases between bounded grid
 // barriers:
@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kPersistThreads)
         const int y = (int)row, yn = y + 1 == L ? 0 : y + 1;
         const int x0 = lane * k;
         const uint32_t base = (uint32_t)y * (uint32_t)L;
+        unsigned long long hbits = 0;  // bonds to x+1 of the lane's first 64 sites, in registers
         for (int q = 0; q < k && x0 + q < L; q += 2) {
           const int x = x0 + q;
           const uint4 r = philox10_rk(make_uint4((base + (uint32_t)x) >> 1, t, rng.replica, bond_tag << 16),
@@ -144,10 +145,13 @@ __global__ void __launch_bounds__(kPersistThreads)
           const bool h1 = r.z < thr && s1 == s2, v1 = r.w < thr && s1 == d1;
           mark[base + x] = (uint8_t)((h0 ? 2u : 0u) | (v0 ? 4u : 0u));
           mark[base + x + 1] = (uint8_t)((h1 ? 2u : 0u) | (v1 ? 4u : 0u));
+          if (q < 64) hbits |= ((unsigned long long)h0 | ((unsigned long long)h1 << 1)) << q;
         }
         const int nq = max(0, min(k, L - x0));  // sites of this lane
-        // bond x -> x + 1 of this lane's sites, from its own mark[] stores above
-        auto hb = [&](int q) { return (mark[base + x0 + q] & 2u) != 0; };
+        // bond x -> x + 1 of this lane's sites: registers, or (past 64 sites a
+        // lane, L >= 2048) this thread's own mark[] stores above
+        const uint8_t* own = mark + base + x0;
+        auto hb = [hbits, own](int q) { return q < 64 ? ((hbits >> q) & 1ull) != 0 : (own[q] & 2u) != 0; };
         // whether the previous lane's last bond to the right is active (then this
         // lane's first site continues that run)
         const bool open_right = nq > 0 && hb(nq - 1);
@@ -485,7 +489,8 @@ cudaError_t launch_cluster_persist(const BitsLattice& lat, bool wolff, uint32_t 
     per_sm = b > 0 ? b : 1;
     occ[wolff].set(per_sm);
   }
-  const long long want = (N / 2 + kPersistThreads - 1) / kPersistThreads;
+  // one thread per site in the union and flip phases (one warp per 32-site word)
+  const long long want = (N + kPersistThreads - 1) / kPersistThreads;
   const long long grid = std::max(1LL, std::min(want, per_sm * sms));
   cudaError_t e = cudaMemsetAsync(&gctl->count, 0, sizeof(unsigned int), s);
   if (e) return e;
