@@ -314,11 +314,11 @@ int ising_sweep_blocks(ising_ctx* ctx, int n_sweeps, int measure_every, int bloc
 int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);
 
 /* How cluster steps (ising_sw_step, ising_wolff_step) run: AUTO = one
- * persistent launch per call for L < 512 (up to 64 x 64 sites one CTA with the
+ * persistent launch per call for L < 768 (up to 64 x 64 sites one CTA with the
  * lattice in shared memory, else a cooperative grid with three bounded
  * grid-barrier phases per step: runs, unions, flips; a barrier wait gives up
  * after about 2 s and later synchronising calls then fail with ISING_ETIMEOUT),
- * a few kernels per step from L = 512 (from L = 2048 with tiled labelling in
+ * a few kernels per step from L = 768 (from L = 2048 with tiled labelling in
  * shared memory; Wolff first tries growth from the seed).  KERNELS /
  * PERSISTENT force one way.  The chain is the same either way, bit for bit. */
 enum { ISING_CLUSTER_AUTO = 0, ISING_CLUSTER_KERNELS = 1, ISING_CLUSTER_PERSISTENT = 2 };

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kPersistThreads)
         }
         const int nq = max(0, min(k, L - x0));  // sites of this lane
         // bond x -> x + 1 of this lane's sites: registers, or (past 64 sites a
-        // lane, L >= 2048) this thread's own mark[] stores above
+        // lane, L > 2048) this thread's own mark[] stores above
         const uint8_t* own = mark + base + x0;
         auto hb = [hbits, own](int q) { return q < 64 ? ((hbits >> q) & 1ull) != 0 : (own[q] & 2u) != 0; };
         // whether the previous lane's last bond to the right is active (then this
