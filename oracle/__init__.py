@@ -23,7 +23,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ising_oracle.c")
 _SRCS = [_SRC, os.path.join(_HERE, "xy_oracle.c"), os.path.join(_HERE, "quad_oracle.c"),
-         os.path.join(_HERE, "xyfix_oracle.c")]
+         os.path.join(_HERE, "xyfix_oracle.c"), os.path.join(_HERE, "ising_oracle_omp.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -42,7 +42,11 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
            "-o", tmp, *_SRCS, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP only spreads the timing build's rows (ising_oracle_omp.c) over
+    # threads; without it that file compiles serially.
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -79,6 +83,10 @@ def lib() -> ctypes.CDLL:
         L.orc_half_sweep.restype = None
         L.orc_sweep.argtypes = [i32, dbl, u64, u32, u32, i32, i32, p, p, p]
         L.orc_sweep.restype = i32
+        L.orc_sweep_omp.argtypes = [i32, dbl, u64, u32, u32, i32, i32, p, p, p]
+        L.orc_sweep_omp.restype = i32
+        L.orc_omp_threads.argtypes = []
+        L.orc_omp_threads.restype = i32
         L.orc_accept_count.argtypes = [i32, u32, u32]
         L.orc_accept_count.restype = u64
         L.orc_n_anti_all.argtypes = [i32, i32, p, p]
@@ -247,6 +255,28 @@ def sweep(s: np.ndarray, beta: float, seed: int, n_sweeps: int, t0: int = 0,
         raise ValueError("oracle sweep rejected its arguments")
     assert got == n_rec
     return E[:n_rec], M[:n_rec]
+
+
+def sweep_omp(s: np.ndarray, beta: float, seed: int, n_sweeps: int, t0: int = 0,
+              replica: int = 0, measure_every: int = 1):
+    """:func:`sweep` with the rows of each colour spread over OpenMP threads
+    (timing build of the same steps; equal to :func:`sweep` bit for bit)."""
+    assert s.dtype == np.int8 and s.flags["C_CONTIGUOUS"] and s.shape[0] == s.shape[1]
+    L = s.shape[0]
+    n_rec = sum(1 for t in range(t0, t0 + n_sweeps) if (t + 1) % measure_every == 0)
+    E = np.zeros(max(n_rec, 1), dtype=np.int64)
+    M = np.zeros(max(n_rec, 1), dtype=np.int64)
+    got = lib().orc_sweep_omp(L, float(beta), seed, replica, t0, n_sweeps, measure_every,
+                              _ptr(s), _ptr(E), _ptr(M))
+    if got < 0:
+        raise ValueError("oracle sweep rejected its arguments")
+    assert got == n_rec
+    return E[:n_rec], M[:n_rec]
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP timing sweep uses (1 without OpenMP)."""
+    return int(lib().orc_omp_threads())
 
 
 # ---------------------------------------------------------------------------
