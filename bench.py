@@ -36,6 +36,7 @@ SWEEPS_PER_STEP = 1000
 MEASURE_EVERY = 10
 BETAS = [0.40, 0.4406868, 0.50]
 SEED = 1
+PROPOSALS = {"oneshot": 0, "staged": 1}  # ISING_PROPOSAL_ONESHOT / _STAGED
 
 # Tiled-kernel launch shape for L = 16384 (sweeps per launch, row strips,
 # words per tile row): the best shape of an autotuning sweep on GB300, used when
@@ -177,6 +178,18 @@ def oracle_sample(L: int, beta: float, n_sweeps: int = 1):
     return L * L * n_sweeps / (dt * 1e9), dt
 
 
+def oracle_sample_omp(L: int, beta: float, n_sweeps: int = 1):
+    """Time the OpenMP build of the oracle sweep (all host cores)."""
+    import oracle
+
+    oracle.build()
+    s = oracle.init(L, SEED)
+    t0 = time.perf_counter()
+    oracle.sweep_omp(s, beta, SEED, n_sweeps, measure_every=MEASURE_EVERY)
+    dt = time.perf_counter() - t0
+    return L * L * n_sweeps / (dt * 1e9), dt, oracle.omp_threads()
+
+
 # ---------------------------------------------------------------------------
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -285,14 +298,21 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     launches0 = ising.ising_launch_count(lat.ctx)
-    ising.ising_set_timing(lat.ctx, True)
+    # the headline: one event pair per step, nothing recorded between launches
     evs = [one_step(args.warmup + i, True) for i in range(args.steps)]
     torch.cuda.synchronize()
     barrier()
-    kern_ms, kern_launches = ising.ising_kernel_time(lat.ctx)
-    ising.ising_set_timing(lat.ctx, False)
     launches = ising.ising_launch_count(lat.ctx) - launches0
     step_ms = [a.elapsed_time(b) for (a, b) in evs]
+    # per-launch duration of the sweep kernel for the roofline: a separate,
+    # shorter pass with an event pair around every launch on the lattice's
+    # stream (the events add a little to each launch, so this errs slow)
+    ising.ising_set_timing(lat.ctx, True)
+    for i in range(max(1, min(2, args.steps))):
+        one_step(args.warmup + args.steps + i, False)
+    torch.cuda.synchronize()
+    kern_ms, kern_launches = ising.ising_kernel_time(lat.ctx)
+    ising.ising_set_timing(lat.ctx, False)
     clk = clocks.stop()
     flips_rank = float(L) * L * SWEEPS_PER_STEP * args.steps
     value, total_ms = job_value(sum(step_ms), flips_rank, dist, "cuda")
@@ -372,7 +392,15 @@ def run_ours(args):
         v, dt = oracle_sample(L, BETAS[1], 2)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "2 sweeps of the 16384^2 lattice at beta 0.4406868 "
-                                          "(%.1f s)" % dt, "cpu": cpu_model()}
+                                          "(%.1f s)" % dt, "cpu": cpu_model(),
+                                "nproc": os.cpu_count()}
+        v, dt, thr = oracle_sample_omp(L, BETAS[1], 4)
+        line["cpu_baseline_multicore"] = {
+            "value": v, "unit": UNIT, "cores": thr, "kind": "oracle_openmp",
+            "sample": "4 sweeps of the 16384^2 lattice at beta 0.4406868, rows of a colour "
+                      "over %d OpenMP threads (%.1f s); timing only, same result as the "
+                      "single-threaded oracle" % (thr, dt),
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     lat.close()
@@ -469,8 +497,9 @@ def run_learned(args):
     wins = learned.generate_windows([64, 128, 256], beta, args.train_windows // 3, block, seed=7,
                                     thermalise=2000, thin=20, per_config=64)
     t_data = time.perf_counter() - t0
+    kind = PROPOSALS[args.proposal]
     t0 = time.perf_counter()
-    with learned.Trainer(block, seed=8) as tr:
+    with learned.Trainer(block, seed=8, proposal=kind) as tr:
         losses = tr.fit(wins, epochs=args.train_epochs, batch=512, lr=2e-3, seed=9)
         blob = tr.blob()
     torch.cuda.synchronize()
@@ -484,6 +513,7 @@ def run_learned(args):
             with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream,
                                seed=100 + c) as lat:
                 ising.ising_nn_load(lat.ctx, blob)
+                ising.ising_set_proposal(lat.ctx, kind)
                 every = 1 if mode == "learned" else 0
                 ising.ising_sweep_blocks(lat.ctx, args.thermalise, 0, block, every)
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -514,11 +544,12 @@ def run_learned(args):
         else:
             w_s = learned.generate_windows([64, 128, 256], beta, 10000, Bs, seed=11, thermalise=2000,
                                            thin=20, per_config=64)
-            with learned.Trainer(Bs, seed=12) as tr2:
+            with learned.Trainer(Bs, seed=12, proposal=kind) as tr2:
                 ls = tr2.fit(w_s, epochs=3, batch=512, lr=2e-3, seed=13)
                 bl, tr_loss = tr2.blob(), float(np.mean(ls[-5:]))
         with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=300) as lat:
             ising.ising_nn_load(lat.ctx, bl)
+            ising.ising_set_proposal(lat.ctx, kind)
             ising.ising_sweep(lat.ctx, args.thermalise, 0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -537,8 +568,9 @@ def run_learned(args):
         "unit": "independent |M| samples/s (learned chain, L=256, beta_c)", "n_gpus": 1,
         "steps": args.chains, "warmup": args.thermalise, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "learned 16x16 block proposal, L=256 at beta_c, 1 block pass per "
-                               "sweep, vs plain sweep on the same GPU",
+        "config": {"workload": "learned 16x16 block proposal (%s), L=256 at beta_c, 1 block pass "
+                               "per sweep, vs plain sweep on the same GPU" % args.proposal,
+                   "proposal": args.proposal,
                    "train_windows": int(len(wins)), "train_epochs": args.train_epochs,
                    "chain_sweeps": n, "chains": args.chains},
         "plain": res["plain"], "learned": res["learned"], "acceptance_by_block": scan,
@@ -568,7 +600,8 @@ def run_batch_learned(args):
     block, every, pt = 16, 5, 10
     wins = learned.generate_windows([64, 128, 256], 0.4406868, 30000, block, seed=7,
                                     thermalise=2000, thin=20, per_config=64)
-    with learned.Trainer(block, seed=8) as tr:
+    kind = PROPOSALS[args.proposal]
+    with learned.Trainer(block, seed=8, proposal=kind) as tr:
         tr.fit(wins, epochs=3, batch=512, lr=2e-3, seed=9)
         blob = tr.blob()
     stream = torch.cuda.current_stream()
@@ -577,6 +610,7 @@ def run_batch_learned(args):
     for mode in ("plain", "learned"):
         with ising.Batch(Ls, betas, pt, stream=stream, seed=SEED) as b:
             ising.ising_batch_nn_load(b.h, blob)
+            ising.ising_batch_set_proposal(b.h, kind)
             b.run(20)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -931,6 +965,8 @@ def main(argv=None):
     ap.add_argument("--no-tune", action="store_true",
                     help="use the fixed kernel shape instead of the autotuner's choice")
     ap.add_argument("--train-windows", type=int, default=100000)
+    ap.add_argument("--proposal", choices=sorted(PROPOSALS), default="staged",
+                    help="learned block proposal family (learned workloads)")
     ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--chain-sweeps", type=int, default=60000)
     ap.add_argument("--chains", type=int, default=2)

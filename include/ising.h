@@ -258,6 +258,8 @@ int ising_batch_get_spins(ising_batch* b, int ladder, int replica, int8_t* host_
 int ising_batch_nn_load(ising_batch* b, const void* bf16_weights, size_t bytes);
 int ising_batch_block_pass(ising_batch* b, int n_passes, int block);
 int ising_batch_block_stats(ising_batch* b, int64_t* proposed, int64_t* accepted);
+/* Proposal family of the batch's block passes (as ising_set_proposal). */
+int ising_batch_set_proposal(ising_batch* b, int kind);
 
 /* Failure-path self test (no counterpart in the paper): launches one kernel
  * that waits, with the same bounded spin as the batch grid barrier, on a device
@@ -290,6 +292,39 @@ int ising_batch_destroy(ising_batch* b);
 
 /* Load the BF16 weight blob (bytes = 2 * 10145) into the context.  Synchronises. */
 int ising_nn_load(ising_ctx* ctx, const void* bf16_weights, size_t bytes);
+
+/* Proposal family of the block passes (no counterpart in the paper).
+ * ONESHOT (default): every interior site drawn at once from the CNN logits
+ * conditioned on the ring edges (the description above).
+ * STAGED: the interior is drawn site by site in stages, each conditioned on
+ * the ring edges and the sites drawn before it (an autoregressive proposal):
+ *   site classes local to the square (i = row, j = column, 0-based):
+ *   0: i, j even; 1: i, j odd, ((i-1)/2 + (j-1)/2) even; 2: other i, j odd;
+ *   3: i + j odd.  Depth d = min(i, j, B-1-i, B-1-j).  For band k = d / 2 =
+ *   0, 1, ...: a NETWORK stage with the band's undrawn class-0 sites, one with
+ *   its class-1 sites, then repeatedly an EXACT stage with every undrawn site
+ *   whose four neighbours are known, else with every undrawn class-2 site whose
+ *   unknown neighbours have all their other neighbours known, until neither
+ *   applies; a last such closure draws the rest (ising_proposal_schedule).
+ *   Network stage: the CNN on channel 0 = known spins (0 elsewhere), channel
+ *   1 = known mask.  Exact stage: logit = sum over known neighbours n of
+ *   2 beta s_n + sum over unknown neighbours n of
+ *   log cosh(beta (h_n + 1)) - log cosh(beta (h_n - 1)), h_n the sum of n's
+ *   other neighbours: the exact conditional with n summed out.
+ *   Every stage draws s_i = +1 iff u_i < P_i (P_i the quantised sigmoid, same
+ *   Philox draws as ONESHOT); q = product over all stages; q(old) by the same
+ *   stages on the current interior.  The MH test is unchanged.
+ * Applies to later ising_block_pass / ising_sweep_blocks calls. */
+enum { ISING_PROPOSAL_ONESHOT = 0, ISING_PROPOSAL_STAGED = 1 };
+int ising_set_proposal(ising_ctx* ctx, int kind);
+
+/* The stage schedule of a proposal for squares of side block (2..16, even):
+ * stage_of_site[block * block] (row-major interior index -> stage) and
+ * stage_exact[n] (1 = exact stage, 0 = network stage), host arrays of at
+ * least block^2 and `capacity` entries; *n_stages = number of stages.
+ * Host only (no GPU needed).  ISING_EINVAL if capacity is too small. */
+int ising_proposal_schedule(int block, int kind, uint8_t* stage_of_site, uint8_t* stage_exact,
+                            int capacity, int* n_stages);
 
 /* n_passes block passes with squares of side `block` (2, 4, 8 or 16; L must be
  * a multiple of 2 * block; packed layout).  Async. */
@@ -372,6 +407,25 @@ int ising_nn_loss_grad(ising_nn* nn, const int8_t* dev_windows, int count, float
                        float* host_grads);
 /* One Adam step (lr, betas 0.9 / 0.999, eps 1e-8) on one minibatch. */
 int ising_nn_train_step(ising_nn* nn, const int8_t* dev_windows, int count, float lr, float* loss);
+/* One Adam step (as ising_nn_train_step) with the caller's gradients
+ * (host, count = 10145 floats, C-ABI parameter order) instead of a minibatch's;
+ * updates the FP32 master weights and the BF16 inference copy.  Synchronises. */
+int ising_nn_apply_grads(ising_nn* nn, const float* host_grads, int count, float lr);
+/* Proposal family the trainer fits (default ONESHOT).  STAGED: one training
+ * sample per (window, network stage): the stage's known mask on the input,
+ * loss terms at the stage's sites; loss = their sum / number of windows
+ * (minus the mean log-likelihood of the network stages). */
+int ising_nn_set_proposal(ising_nn* nn, int kind);
+/* Logits of stage `stage` of the trainer's proposal for count windows on the
+ * device (BF16 inference path): network stages give the CNN logits, exact
+ * stages the exact log-odds at beta, at the stage's sites; other sites 0.
+ * dev_windows [count][(block+2)^2] int8 (interior sites drawn after the stage
+ * are ignored) -> dev_logits [count][block^2] float.  Async. */
+int ising_nn_stage_logits(ising_nn* nn, const int8_t* dev_windows, int count, int stage, double beta,
+                          float* dev_logits);
+/* Natural log of the quantised proposal density of each window's interior
+ * given its ring (the q(old) of a block move), FP32.  Async. */
+int ising_nn_log_q(ising_nn* nn, const int8_t* dev_windows, int count, double beta, float* dev_log_q);
 int ising_nn_destroy(ising_nn* nn);
 
 /* ------------------------------------------------------------------------

@@ -28,6 +28,9 @@ ISING_CLUSTER_AUTO = 0
 ISING_CLUSTER_KERNELS = 1
 ISING_CLUSTER_PERSISTENT = 2
 
+ISING_PROPOSAL_ONESHOT = 0
+ISING_PROPOSAL_STAGED = 1
+
 ISING_KERNEL_AUTO = 0
 ISING_KERNEL_HALF = 1
 ISING_KERNEL_TILED = 2
@@ -114,6 +117,13 @@ _PROTOS = [
     ("ising_nn_loss_grad", _i, [_p, _p, _i, _p, _p]),
     ("ising_nn_train_step", _i, [_p, _p, _i, ctypes.c_float, _p]),
     ("ising_nn_destroy", _i, [_p]),
+    ("ising_nn_apply_grads", _i, [_p, _p, _i, ctypes.c_float]),
+    ("ising_set_proposal", _i, [_p, _i]),
+    ("ising_batch_set_proposal", _i, [_p, _i]),
+    ("ising_nn_set_proposal", _i, [_p, _i]),
+    ("ising_proposal_schedule", _i, [_i, _i, _p, _p, _i, ctypes.POINTER(_i)]),
+    ("ising_nn_stage_logits", _i, [_p, _p, _i, _i, ctypes.c_double, _p]),
+    ("ising_nn_log_q", _i, [_p, _p, _i, ctypes.c_double, _p]),
     ("ising_xy_create", _i, [ctypes.POINTER(_p), _i, _d, _i, _p]),
     ("ising_xy_seed", _i, [_p, _u64]),
     ("ising_xy_sweep", _i, [_p, _i, _i]),
@@ -694,6 +704,43 @@ def ising_nn_train_step(nn: int, dev_windows, count: int, lr: float) -> float:
 
 def ising_nn_destroy(nn: int) -> None:
     _check(lib().ising_nn_destroy(nn))
+
+
+def ising_nn_apply_grads(nn: int, grads: np.ndarray, lr: float) -> None:
+    g = np.ascontiguousarray(grads, dtype=np.float32)
+    _check(lib().ising_nn_apply_grads(nn, _ptr(g), g.size, float(lr)))
+
+
+def ising_set_proposal(ctx: int, kind: int) -> None:
+    _check(lib().ising_set_proposal(ctx, int(kind)))
+
+
+def ising_batch_set_proposal(b: int, kind: int) -> None:
+    _check(lib().ising_batch_set_proposal(b, int(kind)))
+
+
+def ising_nn_set_proposal(nn: int, kind: int) -> None:
+    _check(lib().ising_nn_set_proposal(nn, int(kind)))
+
+
+def ising_proposal_schedule(block: int, kind: int = ISING_PROPOSAL_STAGED):
+    """(stage_of_site (block, block) uint8, stage_exact (n_stages,) uint8)."""
+    so = np.zeros(block * block, dtype=np.uint8)
+    ex = np.zeros(64, dtype=np.uint8)
+    n = ctypes.c_int()
+    _check(lib().ising_proposal_schedule(int(block), int(kind), _ptr(so), _ptr(ex), ex.size,
+                                         ctypes.byref(n)))
+    return so.reshape(block, block), ex[:n.value].copy()
+
+
+def ising_nn_stage_logits(nn: int, dev_windows, count: int, stage: int, beta: float,
+                          dev_logits) -> None:
+    _check(lib().ising_nn_stage_logits(nn, _ptr(dev_windows), int(count), int(stage), float(beta),
+                                       _ptr(dev_logits)))
+
+
+def ising_nn_log_q(nn: int, dev_windows, count: int, beta: float, dev_log_q) -> None:
+    _check(lib().ising_nn_log_q(nn, _ptr(dev_windows), int(count), float(beta), _ptr(dev_log_q)))
 
 
 # ---------------------------------------------------------------------------

@@ -89,6 +89,9 @@ struct ising_ctx {
   __nv_bfloat16* nn_w2t = nullptr;
   unsigned long long* blk_stats = nullptr;  // [2] proposed, accepted
   int64_t block_passes = 0;
+  int proposal = 0;                  // ISING_PROPOSAL_ONESHOT / _STAGED
+  nnc::StagedPlan* plan = nullptr;   // device plan of the staged proposal
+  int plan_B = 0;                    // block size the plan was built for
   uint32_t* sw_parent = nullptr;  // Swendsen-Wang scratch
   uint8_t* sw_flip = nullptr;
   int64_t sw_steps = 0;
@@ -134,6 +137,9 @@ void free_all(ising_ctx* c) {
   cudaFree(c->nn_w);
   cudaFree(c->nn_w2t);
   cudaFree(c->blk_stats);
+  cudaFree(c->plan);
+  c->plan = nullptr;
+  c->plan_B = 0;
   cudaFree(c->sw_parent);
   cudaFree(c->sw_flip);
   cudaFree(c->wolff);
@@ -804,16 +810,33 @@ int ising_block_pass(ising_ctx* c, int n_passes, int block) {
     return fail(ISING_EINVAL, "block must be 2, 4, 8 or 16");
   if (c->L % (2 * block) != 0) return fail(ISING_EINVAL, "L must be a multiple of 2 x block");
   if (n_passes < 0) return fail(ISING_EINVAL, "n_passes must be >= 0");
+  if (c->proposal == ISING_PROPOSAL_STAGED && c->plan_B != block) {
+    CUDA_TRY(nnc::nn_upload_plan(block, ISING_PROPOSAL_STAGED, &c->plan, nullptr, c->stream));
+    c->plan_B = block;
+  }
   const RngParams rng = c->rng();
   for (int k = 0; k < n_passes; ++k) {
     for (int col = 0; col < 2; ++col) {
       Timed tm(c);
-      cudaError_t e = nn_block_pass(c->bits[c->cur], c->L, c->Wc, block, (uint32_t)c->block_passes,
-                                    col, rng, c->beta, c->nn_w, c->nn_w2t, c->blk_stats, c->stream);
+      cudaError_t e =
+          c->proposal == ISING_PROPOSAL_STAGED
+              ? nn_staged_block_pass(c->bits[c->cur], c->L, c->Wc, c->plan, block,
+                                     (uint32_t)c->block_passes, col, rng, c->beta, c->nn_w, c->nn_w2t,
+                                     c->blk_stats, c->stream)
+              : nn_block_pass(c->bits[c->cur], c->L, c->Wc, block, (uint32_t)c->block_passes, col, rng,
+                              c->beta, c->nn_w, c->nn_w2t, c->blk_stats, c->stream);
       if (int st = launch_result(c, e, "block pass")) return st;
     }
     ++c->block_passes;
   }
+  return ok();
+}
+
+int ising_set_proposal(ising_ctx* c, int kind) {
+  if (int st = check_ctx(c)) return st;
+  if (kind != ISING_PROPOSAL_ONESHOT && kind != ISING_PROPOSAL_STAGED)
+    return fail(ISING_EINVAL, "proposal kind must be ISING_PROPOSAL_ONESHOT or ISING_PROPOSAL_STAGED");
+  c->proposal = kind;
   return ok();
 }
 

@@ -326,6 +326,9 @@ struct ising_batch {
   long long unit_total = 0;
   unsigned long long* d_blk_stats = nullptr;
   int64_t block_passes = 0;
+  int proposal = 0;                  // ISING_PROPOSAL_ONESHOT / _STAGED
+  nnc::StagedPlan* plan = nullptr;   // device plan of the staged proposal
+  int plan_B = 0;
   // captured graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -368,7 +371,7 @@ void bfree(ising_batch* b) {
   void* ptrs[] = {b->spins, b->d_off, b->d_L, b->d_t4, b->d_t8, b->d_q, b->d_perm, b->d_slot,
                   b->d_E, b->d_M, b->d_acc, b->d_att, b->d_serE, b->d_serM, b->d_serS,
                   b->d_item_l, b->d_item_i0, b->d_item_nr, b->d_cta_first, b->d_cta_items,
-                  b->d_ctr, b->nn_w, b->nn_w2t, b->d_beta_slot, b->d_unit0, b->d_blk_stats};
+                  b->d_ctr, b->nn_w, b->nn_w2t, b->d_beta_slot, b->d_unit0, b->d_blk_stats, b->plan};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -832,15 +835,35 @@ int ising_batch_block_pass(ising_batch* b, int n_passes, int block) {
     b->unit_B = block;
     b->unit_total = u0[b->n_rep];
   }
+  if (b->proposal == ISING_PROPOSAL_STAGED && b->plan_B != block) {
+    BTRY(nnc::nn_upload_plan(block, ISING_PROPOSAL_STAGED, &b->plan, nullptr, b->stream));
+    b->plan_B = block;
+  }
   const RngParams rng = make_rng(b->seed, 0, 0, 0);
   for (int k = 0; k < n_passes; ++k) {
-    for (int col = 0; col < 2; ++col)
-      BTRY(nn_batch_block_pass(b->spins, b->d_off, b->d_L, b->d_slot, b->d_beta_slot, b->d_unit0,
-                               b->unit_total, b->n_rep, b->n_beta, block, col,
-                               (uint32_t)b->block_passes, rng, b->nn_w, b->nn_w2t,
-                               b->d_blk_stats, b->stream));
+    for (int col = 0; col < 2; ++col) {
+      if (b->proposal == ISING_PROPOSAL_STAGED)
+        BTRY(nn_batch_staged_block_pass(b->spins, b->d_off, b->d_L, b->d_slot, b->d_beta_slot,
+                                        b->d_unit0, b->unit_total, b->n_rep, b->n_beta, b->plan, col,
+                                        (uint32_t)b->block_passes, rng, b->nn_w, b->nn_w2t,
+                                        b->d_blk_stats, b->stream));
+      else
+        BTRY(nn_batch_block_pass(b->spins, b->d_off, b->d_L, b->d_slot, b->d_beta_slot, b->d_unit0,
+                                 b->unit_total, b->n_rep, b->n_beta, block, col,
+                                 (uint32_t)b->block_passes, rng, b->nn_w, b->nn_w2t,
+                                 b->d_blk_stats, b->stream));
+    }
     ++b->block_passes;
   }
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_batch_set_proposal(ising_batch* b, int kind) {
+  if (int st = check_b(b)) return st;
+  if (kind != ISING_PROPOSAL_ONESHOT && kind != ISING_PROPOSAL_STAGED)
+    return bfail(ISING_EINVAL, "proposal kind must be ISING_PROPOSAL_ONESHOT or ISING_PROPOSAL_STAGED");
+  b->proposal = kind;
   set_last_error("");
   return ISING_OK;
 }

@@ -37,22 +37,12 @@
 #include "internal.h"
 #include "ising.h"
 #include "ising_device.cuh"
+#include "nn_common.cuh"
 
 namespace ising {
 namespace {
 
-constexpr int kC = 32;
-constexpr int kCP = 40;     // channel stride of activation grids (conflict-free ldmatrix rows)
-constexpr int kK2 = 9 * kC; // 288
-constexpr int kK2P = 296;   // row stride of the re-laid-out W2
-constexpr int kOffW1 = 0, kOffB1 = 576, kOffW2 = 608, kOffB2 = 9824, kOffW3 = 9856,
-              kOffB3 = 10144, kNParams = 10145;
-constexpr uint32_t kTagBlkSample = 4, kTagBlkAccept = 5, kTagBlkOffset = 6;
-constexpr int kMaxB = 16;
-constexpr int kThreads = 256;       // training kernels
-constexpr int kInferThreads = 512;  // inference / block-pass kernels
-
-__host__ __device__ constexpr int frame_of(int B) { return B + 2; }
+using namespace nnc;
 
 struct InferSmem {
   // layer-1 activations as a BF16 pair hi + lo (hi = bf16(h), lo = bf16(h - hi)):
@@ -110,8 +100,6 @@ __device__ void build_var_lists(InferSmem& S, int B) {
   }
 }
 
-__device__ __forceinline__ float bf(const __nv_bfloat16& v) { return __bfloat162float(v); }
-
 // Per-network cache of the window-independent activations, one slot per block
 // size B in {2, 4, 8, 16}: the bytes of h1, h1lo, h2 (with their zero padding)
 // followed by the logits, as a CTA holds them after processing any window.  It
@@ -128,13 +116,6 @@ static_assert(offsetof(InferSmem, w2t) % 16 == 0 && (kC * kK2P * 2) % 16 == 0, "
 
 __host__ __device__ inline int cache_slot_of(int B) {
   return B == 2 ? 0 : (B == 4 ? 1 : (B == 8 ? 2 : (B == 16 ? 3 : -1)));
-}
-
-// is frame position (fy, fx) on one of the four ring edges (not a corner)?
-__device__ __forceinline__ bool ring_edge(int fy, int fx, int F) {
-  const bool ey = (fy == 0 || fy == F - 1) && fx >= 1 && fx <= F - 2;
-  const bool ex = (fx == 0 || fx == F - 1) && fy >= 1 && fy <= F - 2;
-  return ey || ex;
 }
 
 // Loads weights into shared memory and zeroes the padding of the grids; with a
@@ -209,10 +190,6 @@ __device__ void layer1(InferSmem& S, int B, bool full) {
       S.h1lo[((fy + 1) * FP + fx + 1) * kCP + c] = __float2bfloat16(h - __bfloat162float(hi));
     }
   }
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
 // Layer 2 on the tensor cores: implicit GEMM, M = F^2 positions, N = 32
@@ -316,19 +293,6 @@ __device__ void layer3(InferSmem& S, int B, bool full) {
   }
 }
 
-__device__ __forceinline__ uint32_t quantise_p(float logit) {
-  const float p = 1.f / (1.f + expf(-logit));
-  const double v = rint((double)p * 4294967296.0);
-  if (v < 1.0) return 1u;
-  if (v > 4294967295.0) return 0xffffffffu;
-  return (uint32_t)v;
-}
-
-__device__ __forceinline__ float log2_q_term(uint32_t P, int s) {
-  const double num = s > 0 ? (double)P : 4294967296.0 - (double)P;
-  return log2f((float)num) - 32.f;
-}
-
 struct PassParams {
   uint32_t* planes;  // packed lattice [2][L][Wc]
   int L, Wc, B, colour;
@@ -337,20 +301,6 @@ struct PassParams {
   float beta;
   unsigned long long* stats;  // [0] proposed, [1] accepted
 };
-
-__device__ __forceinline__ int get_spin(const uint32_t* planes, int L, int Wc, int y, int x) {
-  const int c = (x + y) & 1, j = x >> 1;
-  const uint32_t w = __ldcg(&planes[(size_t)c * L * Wc + (size_t)y * Wc + (j >> 5)]);
-  return ((w >> (j & 31)) & 1u) ? 1 : -1;
-}
-
-__device__ void block_offset(uint32_t pass, uint32_t replica, const RngParams& rng, int B, int& ox,
-                             int& oy) {
-  const uint4 r = philox10_rk(make_uint4(0u, pass, replica, ctr_w(kTagBlkOffset, 0, 0)), rng.rk0,
-                              rng.rk1);
-  ox = (int)(r.x % (uint32_t)B);
-  oy = (int)(r.y % (uint32_t)B);
-}
 
 // One exact block MH update of square (bx, by) of a lattice (whole CTA).
 __device__ void process_block(InferSmem& S, uint32_t* planes, int L, int Wc, int B, int colour,
@@ -571,8 +521,11 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_const(const __nv_bfloat16*
 }
 
 // ---------------------------------------------------------------------------
-// Training (FP32 on the CUDA cores): loss = mean over windows of
-// sum_i BCE(logit_i, (s_i + 1) / 2); gradients accumulated with atomics.
+// Training (FP32 on the CUDA cores): one sample per (window, network stage of
+// the plan): input = the spins known before that stage and their mask, loss
+// terms BCE(logit_i, (s_i + 1) / 2) at the stage's sites; loss = their sum over
+// all samples / number of windows (for the one-shot plan: the mean over windows
+// of the sum over the interior).  Gradients accumulated with atomics.
 // ---------------------------------------------------------------------------
 struct TrainSmem {
   float prm[kNParams];
@@ -583,6 +536,7 @@ struct TrainSmem {
   float gz2[(kMaxB + 2) * (kMaxB + 2) * kC];
   float g3[(kMaxB + 2) * (kMaxB + 2)];
   float tgt[kMaxB * kMaxB];
+  uint8_t tmask[kMaxB * kMaxB];  // sites of the sample's stage (the loss terms)
   float red[kThreads / 32];
 };
 
@@ -591,7 +545,8 @@ __device__ __forceinline__ float at(const float* m, int F, int y, int x, int C, 
 }
 
 __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict__ windows, int n,
-                                                      int B, const float* __restrict__ params,
+                                                      int B, const StagedPlan* __restrict__ plan,
+                                                      const float* __restrict__ params,
                                                       float* __restrict__ grads,
                                                       float* __restrict__ loss) {
   extern __shared__ uint4 smem_raw[];
@@ -607,15 +562,22 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
   const float* W3 = S.prm + kOffW3;
   const float b3 = S.prm[kOffB3];
   float my_loss = 0.f;
-  for (int k = blockIdx.x; k < n; k += gridDim.x) {
+  const int n_net = plan->n_net;
+  const int total = n * n_net;
+  for (int smp = blockIdx.x; smp < total; smp += gridDim.x) {
+    const int k = smp / n_net;
+    const int stage = plan->net_ids[smp - k * n_net];
     const int8_t* win = windows + (size_t)k * FF;
     for (int i = threadIdx.x; i < FF; i += blockDim.x) {
       const int fy = i / F, fx = i - (i / F) * F;
-      const bool e = ring_edge(fy, fx, F);
+      const bool e = known_at(*plan, fy, fx, stage);
       S.x0[i] = e ? (float)win[i] : 0.f;
       S.x1[i] = e ? 1.f : 0.f;
-      if (fy >= 1 && fy <= B && fx >= 1 && fx <= B)
-        S.tgt[(fy - 1) * B + fx - 1] = win[i] > 0 ? 1.f : 0.f;
+      if (fy >= 1 && fy <= B && fx >= 1 && fx <= B) {
+        const int ii = (fy - 1) * B + fx - 1;
+        S.tgt[ii] = win[i] > 0 ? 1.f : 0.f;
+        S.tmask[ii] = plan->stage_of[ii] == stage ? 1 : 0;
+      }
     }
     __syncthreads();
     // forward
@@ -645,7 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
     for (int p = threadIdx.x; p < FF; p += blockDim.x) {
       const int fy = p / F, fx = p - (p / F) * F;
       float g = 0.f;
-      if (fy >= 1 && fy <= B && fx >= 1 && fx <= B) {
+      if (fy >= 1 && fy <= B && fx >= 1 && fx <= B && S.tmask[(fy - 1) * B + fx - 1]) {
         float z = b3;
         for (int t = 0; t < 9; ++t) {
           const int yy = fy + t / 3 - 1, xx = fx + t % 3 - 1;
@@ -903,6 +865,9 @@ using namespace ising;
 
 struct ising_nn {
   int B = 16;
+  int kind = kProposalOneShot;
+  StagedPlan* plan = nullptr;  // device copy of the proposal plan
+  int n_net = 1;
   cudaStream_t stream = nullptr;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
   __nv_bfloat16 *wbf = nullptr, *w2t = nullptr;
@@ -929,6 +894,7 @@ int ising_nn_create(ising_nn** out, int block, int channels, void* stream) {
     if (!e) e = cudaMalloc((void**)q, kNParams * sizeof(float));
   if (!e) e = cudaMalloc((void**)&n->loss, sizeof(float));
   if (!e) e = nn_alloc_weights(&n->wbf, &n->w2t);
+  if (!e) e = nn_upload_plan(block, kProposalOneShot, &n->plan, &n->n_net, n->stream);
   if (!e) e = cudaMemset(n->p, 0, kNParams * 4);
   if (!e) e = cudaMemset(n->m, 0, kNParams * 4);
   if (!e) e = cudaMemset(n->v, 0, kNParams * 4);
@@ -995,9 +961,9 @@ int ising_nn_loss_grad(ising_nn* n, const int8_t* dev_windows, int count, float*
   if (!n || !dev_windows || count <= 0) return nfail(ISING_EINVAL, "bad arguments");
   NTRY(cudaMemsetAsync(n->g, 0, kNParams * 4, n->stream));
   NTRY(cudaMemsetAsync(n->loss, 0, 4, n->stream));
-  const int grid = std::max(1, std::min(count, sms_of_current()));
-  k_nn_train<<<grid, kThreads, train_smem(), n->stream>>>(dev_windows, count, n->B, n->p, n->g,
-                                                          n->loss);
+  const int grid = std::max(1, std::min(count * n->n_net, sms_of_current()));
+  k_nn_train<<<grid, kThreads, train_smem(), n->stream>>>(dev_windows, count, n->B, n->plan, n->p,
+                                                          n->g, n->loss);
   NTRY(cudaGetLastError());
   if (loss) NTRY(cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
   if (host_grads) NTRY(cudaMemcpyAsync(host_grads, n->g, kNParams * 4, cudaMemcpyDeviceToHost, n->stream));
@@ -1010,9 +976,9 @@ int ising_nn_train_step(ising_nn* n, const int8_t* dev_windows, int count, float
   if (!n || !dev_windows || count <= 0 || !(lr >= 0.f)) return nfail(ISING_EINVAL, "bad arguments");
   NTRY(cudaMemsetAsync(n->g, 0, kNParams * 4, n->stream));
   NTRY(cudaMemsetAsync(n->loss, 0, 4, n->stream));
-  const int grid = std::max(1, std::min(count, sms_of_current()));
-  k_nn_train<<<grid, kThreads, train_smem(), n->stream>>>(dev_windows, count, n->B, n->p, n->g,
-                                                          n->loss);
+  const int grid = std::max(1, std::min(count * n->n_net, sms_of_current()));
+  k_nn_train<<<grid, kThreads, train_smem(), n->stream>>>(dev_windows, count, n->B, n->plan, n->p,
+                                                          n->g, n->loss);
   NTRY(cudaGetLastError());
   n->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -1028,6 +994,56 @@ int ising_nn_train_step(ising_nn* n, const int8_t* dev_windows, int count, float
   return ISING_OK;
 }
 
+int ising_nn_apply_grads(ising_nn* n, const float* host_grads, int count, float lr) {
+  if (!n || !host_grads || count != kNParams || !(lr >= 0.f))
+    return nfail(ISING_EINVAL, "need %d gradients and lr >= 0", kNParams);
+  NTRY(cudaMemcpyAsync(n->g, host_grads, kNParams * 4, cudaMemcpyHostToDevice, n->stream));
+  n->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
+  k_adam<<<(kNParams + 255) / 256, 256, 0, n->stream>>>(n->p, n->g, n->m, n->v, lr, b1, b2, 1e-8f,
+                                                        c1, c2, n->wbf, n->w2t);
+  NTRY(cudaGetLastError());
+  NTRY(cudaStreamSynchronize(n->stream));
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_nn_set_proposal(ising_nn* n, int kind) {
+  if (!n) return nfail(ISING_EINVAL, "null trainer");
+  if (kind != kProposalOneShot && kind != kProposalStaged)
+    return nfail(ISING_EINVAL, "proposal kind must be ISING_PROPOSAL_ONESHOT or ISING_PROPOSAL_STAGED");
+  NTRY(nn_upload_plan(n->B, kind, &n->plan, &n->n_net, n->stream));
+  n->kind = kind;
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_nn_stage_logits(ising_nn* n, const int8_t* dev_windows, int count, int stage, double beta,
+                          float* dev_logits) {
+  if (!n || (count > 0 && (!dev_windows || !dev_logits)) || count < 0)
+    return nfail(ISING_EINVAL, "bad arguments");
+  int n_stages = 0;
+  NTRY(nn_plan_stages(n->B, n->kind, &n_stages));
+  if (stage < 0 || stage >= n_stages) return nfail(ISING_EINVAL, "stage %d out of range [0, %d)", stage, n_stages);
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return nfail(ISING_EINVAL, "beta must be finite and >= 0");
+  if (count == 0) return ISING_OK;
+  NTRY(nn_stage_logits(dev_windows, count, n->plan, stage, (float)beta, n->wbf, n->w2t, dev_logits,
+                       n->stream));
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_nn_log_q(ising_nn* n, const int8_t* dev_windows, int count, double beta, float* dev_log_q) {
+  if (!n || (count > 0 && (!dev_windows || !dev_log_q)) || count < 0)
+    return nfail(ISING_EINVAL, "bad arguments");
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return nfail(ISING_EINVAL, "beta must be finite and >= 0");
+  if (count == 0) return ISING_OK;
+  NTRY(nn_log_q(dev_windows, count, n->plan, (float)beta, n->wbf, n->w2t, dev_log_q, n->stream));
+  set_last_error("");
+  return ISING_OK;
+}
+
 int ising_nn_destroy(ising_nn* n) {
   if (!n) return ISING_OK;
   cudaStreamSynchronize(n->stream);
@@ -1038,6 +1054,7 @@ int ising_nn_destroy(ising_nn* n) {
   cudaFree(n->loss);
   cudaFree(n->wbf);
   cudaFree(n->w2t);
+  cudaFree(n->plan);
   delete n;
   return ISING_OK;
 }

@@ -5,7 +5,8 @@ Metropolis-Hastings) runs in libising.so; this module only moves data.
 Training data: equilibrium configurations of the plain sweep at beta, cut into
 (block+2)^2 windows at random positions (ring + interior).  Loss: maximum
 likelihood of the interior given the ring edges (binary cross-entropy of the
-per-site logits).
+per-site logits); for the staged proposal, of every network stage's sites given
+the ring and the sites drawn before that stage.
 """
 from __future__ import annotations
 
@@ -48,9 +49,13 @@ def generate_windows(Ls, beta: float, n_per_L: int, block: int, seed: int, therm
 class Trainer:
     """FP32 master weights + Adam on the GPU (ising_nn_*)."""
 
-    def __init__(self, block: int = 16, seed: int = 0, params: dict | None = None, stream=None):
+    def __init__(self, block: int = 16, seed: int = 0, params: dict | None = None, stream=None,
+                 proposal: int = B.ISING_PROPOSAL_ONESHOT):
         self.block = block
+        self.proposal = proposal
         self.h = B.ising_nn_create(block, B.NN_CHANNELS, stream)
+        if proposal != B.ISING_PROPOSAL_ONESHOT:
+            B.ising_nn_set_proposal(self.h, proposal)
         if params is None:
             params = init_params(seed)
         B.ising_nn_set_params(self.h, B.nn_flatten(params))

@@ -2,11 +2,11 @@
 
 * Logits of the BF16 tensor-core inference match the float64 reference with
   the same (bf16-rounded) weights to 1e-2 relative (floor 1 on the scale).
-* FP32 training loss and gradients match the float64 reference.
 * The block MH chain is exact: block passes alone (2 x 2 blocks, random
   untrained network) on a 4 x 4 lattice reproduce exact <E> and <M^2>
-  within 3 sigma; with 16 x 16 blocks on L = 64 the chain (sweeps + passes)
-  reproduces the plain chain's energy within 3 sigma.
+  within 3 sigma; with 4 x 4 blocks on L = 64 (acceptance asserted > 1 %) the
+  chain (sweeps + passes) reproduces the plain chain's energy within 3 sigma.
+* (Loss and gradients, element by element, and Adam: test_gpu_staged.py.)
 * Training on plain-sweep configurations lowers the loss and raises the block
   acceptance over the untrained network.
 """
@@ -64,25 +64,6 @@ def test_logits_match_fp32_reference(torch, block):
     assert np.abs(want).max() > 1.0  # the logits are not trivially small
 
 
-def test_loss_and_gradients_match_reference(torch):
-    block = 4
-    p32 = learned.init_params(seed=6)
-    wins = _windows(32, 24, block, seed=7)
-    with learned.Trainer(block, params=p32) as tr:
-        d = torch.from_numpy(wins).cuda()
-        loss, g = ising.ising_nn_loss_grad(tr.h, d, len(wins))
-    p64 = {k: v.astype(np.float64) for k, v in p32.items()}
-    F = block + 2
-    want_loss, want_g = cnn.loss_and_grads(p64, _frames(wins, block),
-                                           wins[:, 1:F - 1, 1:F - 1].astype(np.float64))
-    assert abs(loss - want_loss) < 1e-4 * abs(want_loss)
-    G = ising.nn_unflatten(g)
-    for k in want_g:
-        num = np.linalg.norm(G[k] - want_g[k])
-        den = np.linalg.norm(want_g[k]) + 1e-12
-        assert num / den < 1e-4, (k, num / den)
-
-
 def test_block_mh_exact_on_4x4(torch):
     """Block passes only (2 x 2 blocks at random offsets) must sample the
     Boltzmann distribution of the 4 x 4 lattice."""
@@ -109,10 +90,12 @@ def test_block_mh_exact_on_4x4(torch):
 
 
 def test_block_chain_keeps_plain_energy_L64(torch):
-    L, block, beta = 64, 16, 0.40
+    """4 x 4 one-shot blocks (an untrained network still has its proposals
+    accepted at this size): sweeps + passes keep the plain chain's energy."""
+    L, block, beta = 64, 4, 0.40
     with learned.Trainer(block, params=learned.init_params(seed=12)) as tr:
         blob = tr.blob()
-    res = {}
+    res, acc = {}, []
     for mode in ("plain", "learned"):
         Es = []
         for seed in (21, 22, 23, 24):
@@ -124,7 +107,11 @@ def test_block_chain_keeps_plain_energy_L64(torch):
                 ising.ising_sweep_blocks(lat.ctx, 1500, 1, block, every)
                 E, _ = lat.series(1500)
                 Es.append(stats.mean_and_error(E / (L * L)))
+                if mode == "learned":
+                    p, a = ising.ising_block_stats(lat.ctx)
+                    acc.append(a / p)
         res[mode] = stats.combine_runs([a for a, _ in Es], [b for _, b in Es])
+    assert min(acc) > 0.01, acc
     (a, da), (b, db) = res["plain"], res["learned"]
     assert abs(a - b) < 3 * np.hypot(da, db), res
 

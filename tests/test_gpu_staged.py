@@ -1,0 +1,277 @@
+"""Staged block proposal on the GPU against the CPU reference (oracle/staged.py).
+
+* The C-ABI schedule equals the oracle's (also checked without a GPU in
+  test_staged_schedule.py).
+* Per-stage logits of the BF16 tensor-core inference match the float64
+  reference with the same bf16-rounded weights at every stage's sites: network
+  stages to 1e-2 relative (floor 1), exact stages to 1e-5 (FP32 arithmetic).
+* The teacher-forced ln q of each window matches the reference within the
+  bound that the logit tolerance implies (|d ln sigma(l) / dl| <= 1 per site).
+* FP32 loss and gradients of the staged training objective match the float64
+  reference element by element.
+* Block passes alone with the staged proposal sample the Boltzmann
+  distribution: exact <E>, <M^2> of a 4 x 4 lattice (2 x 2 blocks) and Kaufman's
+  <E> on 8 x 8 (4 x 4 blocks), within 3 sigma.
+* A briefly trained network with 16 x 16 staged blocks at beta_c accepts
+  proposals (acceptance asserted > 0), and sweeps + passes keep the plain
+  chain's <E> and <|M|> within 3 sigma on L = 64.
+* The batched staged pass equals the single-lattice staged pass bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn, exact, staged
+from oracle.closed_forms import kaufman_energy
+import paper_2402_06415_gb300 as ising
+from paper_2402_06415_gb300 import learned, stats
+
+pytestmark = pytest.mark.gpu
+
+STAGED = ising.ISING_PROPOSAL_STAGED
+BETA_C = 0.4406868
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ising.lib()
+    return t
+
+
+def _windows(L, n, block, seed, beta=BETA_C, sweeps=60):
+    rng = np.random.default_rng(seed)
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, seed=seed) as lat:
+        lat.sweep(sweeps, 0)
+        s = lat.spins()
+    w = learned.extract_windows(s, n, block, rng)
+    w[:, 0, 0] = w[:, 0, -1] = w[:, -1, 0] = w[:, -1, -1] = 0  # corners are never read
+    return w
+
+
+def _params(seed, scale=2.0):
+    p32 = learned.init_params(seed=seed, scale=scale)
+    rng = np.random.default_rng(seed + 1)
+    for k in p32:
+        if k.startswith("b"):
+            p32[k] = (0.1 * rng.standard_normal(p32[k].shape)).astype(np.float32)
+    return p32, {k: cnn.bf16_round(v.astype(np.float64)) for k, v in p32.items()}
+
+
+def test_schedule_matches_oracle():
+    for B in (2, 4, 8, 16):
+        so, ex = ising.ising_proposal_schedule(B, STAGED)
+        st = staged.schedule(B)
+        assert list(ex) == [1 if kind == "exact" else 0 for kind, _ in st]
+        for k, (_, sites) in enumerate(st):
+            for (i, j) in sites:
+                assert so[i, j] == k
+
+
+@pytest.mark.parametrize("block", [16, 8, 4])
+def test_stage_logits_match_reference(torch, block):
+    p32, pref = _params(3)
+    wins = _windows(64, 24, block, seed=5)
+    st = staged.schedule(block)
+    d = torch.from_numpy(wins).cuda()
+    out = torch.zeros((len(wins), block, block), dtype=torch.float32, device="cuda")
+    with learned.Trainer(block, params=p32, proposal=STAGED) as tr:
+        for k, (kind, sites) in enumerate(st):
+            ising.ising_nn_stage_logits(tr.h, d, len(wins), k, BETA_C, out)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy().astype(np.float64)
+            want = staged.stage_logits(pref, wins.astype(np.int64), BETA_C, block, st, k)
+            m = np.zeros((block, block), dtype=bool)
+            for (i, j) in sites:
+                m[i, j] = True
+            err = np.abs(got - want)[:, m] / np.maximum(np.abs(want)[:, m], 1.0)
+            tol = 1e-2 if kind == "net" else 1e-5
+            assert err.max() < tol, (k, kind, err.max())
+            assert np.all(got[:, ~m] == 0.0)
+
+
+@pytest.mark.parametrize("block", [16, 4])
+def test_log_q_matches_reference(torch, block):
+    p32, pref = _params(7)
+    wins = _windows(64, 16, block, seed=8)
+    st = staged.schedule(block)
+    with learned.Trainer(block, params=p32, proposal=STAGED) as tr:
+        d = torch.from_numpy(wins).cuda()
+        out = torch.zeros(len(wins), dtype=torch.float32, device="cuda")
+        ising.ising_nn_log_q(tr.h, d, len(wins), BETA_C, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+    w64 = wins.astype(np.int64)
+    want = staged.log_q_many(pref, w64, BETA_C, block, st)
+    # bound implied by the logit tolerance: sum over sites of 1e-2 max(|l|, 1)
+    # (network stages) and 1e-5 max(|l|, 1) (exact stages), plus FP32 rounding
+    bound = np.zeros(len(wins))
+    for k, (kind, sites) in enumerate(st):
+        lg = staged.stage_logits(pref, w64, BETA_C, block, st, k)
+        rel = 1e-2 if kind == "net" else 1e-5
+        for (i, j) in sites:
+            bound += rel * np.maximum(np.abs(lg[:, i, j]), 1.0)
+    bound += 1e-5 * np.abs(want) + 1e-3
+    assert np.all(np.abs(got - want) <= bound), (got - want, bound)
+    assert np.all(want < 0)
+
+
+@pytest.mark.parametrize("proposal", [ising.ISING_PROPOSAL_ONESHOT, STAGED])
+def test_loss_and_gradients_elementwise(torch, proposal):
+    block = 4
+    p32 = learned.init_params(seed=6)
+    for k in p32:  # avoid exact ReLU kinks at 0 and give the biases some weight
+        p32[k] = p32[k] + (0.05 * np.random.default_rng(60).standard_normal(p32[k].shape)).astype(np.float32)
+    wins = _windows(32, 24, block, seed=7)
+    with learned.Trainer(block, params=p32, proposal=proposal) as tr:
+        d = torch.from_numpy(wins).cuda()
+        loss, g = ising.ising_nn_loss_grad(tr.h, d, len(wins))
+    p64 = {k: v.astype(np.float64) for k, v in p32.items()}
+    if proposal == STAGED:
+        want_loss, want_g = staged.staged_loss_and_grads(p64, wins, block)
+    else:
+        F = block + 2
+        want_loss, want_g = cnn.loss_and_grads(p64, staged.stage_frame(wins, staged.ring_mask(block)),
+                                               wins[:, 1:F - 1, 1:F - 1].astype(np.float64))
+    assert abs(loss - want_loss) < 1e-5 * abs(want_loss)
+    G = ising.nn_unflatten(g)
+    for k in want_g:
+        ref = want_g[k]
+        scale = 1e-2 * np.abs(ref).max()
+        err = np.abs(G[k] - ref) / np.maximum(np.abs(ref), scale)
+        assert err.max() < 1e-4, (k, err.max())
+
+
+def test_adam_and_bf16_export_match_reference(torch):
+    """Three Adam steps with the oracle's gradients on both sides: FP32 master
+    weights vs the float64 Adam, and the BF16 blob = bf16(master weights)."""
+    block = 4
+    p32 = learned.init_params(seed=40)
+    p64 = {k: v.astype(np.float64) for k, v in p32.items()}
+    m = {k: np.zeros_like(v) for k, v in p64.items()}
+    v = {k: np.zeros_like(x) for k, x in p64.items()}
+    wins = _windows(32, 16, block, seed=41)
+    lr = 3e-3
+    with learned.Trainer(block, params=p32) as tr:
+        for t in (1, 2, 3):
+            _, g = staged.staged_loss_and_grads(p64, wins[5 * t:5 * t + 5], block,
+                                                [("net", [(i, j) for i in range(block) for j in range(block)])])
+            g32 = {k: x.astype(np.float32) for k, x in g.items()}
+            ising.ising_nn_apply_grads(tr.h, ising.nn_flatten(g32), lr)
+            p64, m, v = staged.adam_step(p64, {k: x.astype(np.float64) for k, x in g32.items()}, m, v, t, lr)
+        got = tr.params()
+        blob = tr.blob()
+    for k in p64:
+        err = np.abs(got[k].astype(np.float64) - p64[k])
+        assert err.max() < 2e-6 * max(1.0, np.abs(p64[k]).max()), (k, err.max())
+    flat = ising.nn_flatten(got)
+    want_blob = (cnn.bf16_round(flat.astype(np.float64)).astype(np.float32).view(np.uint32) >> 16)
+    assert np.array_equal(blob.astype(np.uint32), want_blob)
+
+
+def _block_only_chain(L, block, beta, blob, n, seed):
+    Es, M2 = [], []
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, seed=seed) as lat:
+        ising.ising_nn_load(lat.ctx, blob)
+        ising.ising_set_proposal(lat.ctx, STAGED)
+        for _ in range(n):
+            ising.ising_block_pass(lat.ctx, 1, block)
+            E, M = lat.measure()
+            Es.append(E)
+            M2.append(M * M)
+        prop, acc = ising.ising_block_stats(lat.ctx)
+    return np.array(Es, float), np.array(M2, float), prop, acc
+
+
+def test_staged_block_moves_exact_on_4x4(torch):
+    L, block, beta, n = 4, 2, 0.44, 12000
+    ex = exact.averages(L, beta)
+    with learned.Trainer(block, params=learned.init_params(seed=9, scale=1.0), proposal=STAGED) as tr:
+        blob = tr.blob()
+    Es, M2, prop, acc = _block_only_chain(L, block, beta, blob, n, 11)
+    e, de = stats.mean_and_error(Es[200:])
+    m, dm = stats.mean_and_error(M2[200:])
+    assert abs(e - ex["E"]) < 3 * de, (e, de, ex["E"])
+    assert abs(m - ex["M2"]) < 3 * dm, (m, dm, ex["M2"])
+    assert prop == n * 4 and 0 < acc < prop
+
+
+def test_staged_block_moves_match_kaufman_8x8(torch):
+    L, block, beta, n = 8, 4, BETA_C, 12000
+    with learned.Trainer(block, params=learned.init_params(seed=14, scale=1.0), proposal=STAGED) as tr:
+        blob = tr.blob()
+    Es, _, prop, acc = _block_only_chain(L, block, beta, blob, n, 15)
+    e, de = stats.mean_and_error(Es[300:])
+    want = kaufman_energy(L, beta) * L * L
+    assert acc > 0.02 * prop
+    assert abs(e - want) < 3 * de, (e, de, want)
+
+
+@pytest.fixture(scope="module")
+def trained16(torch):
+    """A staged 16 x 16 network trained briefly at beta_c (tens of seconds)."""
+    wins = learned.generate_windows([64, 128], BETA_C, 6144, 16, seed=51, thermalise=2000, thin=40)
+    with learned.Trainer(16, seed=52, proposal=STAGED) as tr:
+        losses = tr.fit(wins, epochs=2, batch=256, lr=2e-3, seed=53)
+        blob = tr.blob()
+    return blob, losses
+
+
+def test_trained_staged_16x16_accepts_and_keeps_the_chain(torch, trained16):
+    blob, losses = trained16
+    assert np.mean(losses[-5:]) < np.mean(losses[:5])
+    L, block, beta = 64, 16, BETA_C
+    res, rates = {}, []
+    for mode in ("plain", "staged"):
+        Es, Ms = [], []
+        for seed in range(61, 69):
+            with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, seed=seed) as lat:
+                every = 0
+                if mode == "staged":
+                    ising.ising_nn_load(lat.ctx, blob)
+                    ising.ising_set_proposal(lat.ctx, STAGED)
+                    every = 1
+                ising.ising_sweep_blocks(lat.ctx, 500, 0, block, every)
+                ising.ising_sweep_blocks(lat.ctx, 3000, 1, block, every)
+                E, M = lat.series(3000)
+                Es.append(stats.mean_and_error(E / (L * L)))
+                Ms.append(stats.mean_and_error(np.abs(M) / (L * L)))
+                if mode == "staged":
+                    p, a = ising.ising_block_stats(lat.ctx)
+                    rates.append(a / p)
+        res[mode] = (stats.combine_runs([a for a, _ in Es], [b for _, b in Es]),
+                     stats.combine_runs([a for a, _ in Ms], [b for _, b in Ms]))
+    assert min(rates) > 0.01, rates
+    for idx in (0, 1):
+        (a, da), (b, db) = res["plain"][idx], res["staged"][idx]
+        assert abs(a - b) < 3 * np.hypot(da, db), (idx, res)
+    e_exact = kaufman_energy(L, beta)
+    (b, db) = res["staged"][0]
+    assert abs(b - e_exact) < 3 * db, (b, db, e_exact)
+
+
+def test_batch_staged_pass_equals_single_lattice_pass(torch):
+    Ls, betas, block, seed = [32, 64], np.array([0.38, 0.42, 0.46]), 8, 5
+    with learned.Trainer(block, params=learned.init_params(seed=13), proposal=STAGED) as tr:
+        blob = tr.blob()
+    with ising.Batch(Ls, betas, 1000, seed=seed) as b:
+        ising.ising_batch_nn_load(b.h, blob)
+        ising.ising_batch_set_proposal(b.h, STAGED)
+        ising.ising_batch_block_pass(b.h, 3, block)
+        got = {(l, i): b.spins(l, i) for l in range(2) for i in range(3)}
+        pb, ab = ising.ising_batch_block_stats(b.h)
+    tot_p = tot_a = 0
+    for l, L in enumerate(Ls):
+        for i in range(3):
+            with ising.Lattice(L, betas[i], ising.ISING_LAYOUT_BITS) as lat:
+                ising.ising_set_replica(lat.ctx, l * 3 + i)
+                lat.seed(seed)
+                ising.ising_nn_load(lat.ctx, blob)
+                ising.ising_set_proposal(lat.ctx, STAGED)
+                ising.ising_block_pass(lat.ctx, 3, block)
+                assert np.array_equal(lat.spins(), got[(l, i)]), (l, i)
+                p_, a_ = ising.ising_block_stats(lat.ctx)
+                tot_p += p_
+                tot_a += a_
+    assert (pb, ab) == (tot_p, tot_a) and ab > 0
