@@ -388,6 +388,8 @@ def run_ours(args):
         "roofline": roofline,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_indep:
+        line["indep_samples"] = measure_indep_samples(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt = oracle_sample(L, BETAS[1], 2)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -407,6 +409,138 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_indep_samples(args, stream):
+    """Independent samples per second at beta_c on L = 256 for the plain
+    Metropolis chain, the learned chain (1 sweep + 1 staged 16x16 block pass per
+    step) and Swendsen-Wang steps.
+
+    tau_int (|M| and E) comes from many chains run together (one batch per
+    method: `indep_chains` plain chains, `indep_learned_chains` learned chains,
+    all started from plain-sweep equilibrium), pooled autocorrelation with
+    Sokal's window and jackknife errors over groups of chains
+    (stats.tau_int_chains); Swendsen-Wang from single chains (its tau is a few
+    steps).  Speed in two regimes: one chain alone on the GPU (launch- and
+    latency-bound: steps/s of one lattice) and the batch (throughput: steps/s
+    of every chain of the batch together).  Independent samples/s = chains x
+    steps/s / (2 tau_int)."""
+    import numpy as np
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import learned, stats
+
+    beta, L, block = 0.4406868, 256, 16
+    t_all = time.perf_counter()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    t0 = time.perf_counter()
+    wins = learned.generate_windows([64, 128, 256], beta, args.indep_train_windows // 3, block, seed=7,
+                                    thermalise=2000, thin=20, per_config=64, stream=stream)
+    with learned.Trainer(block, seed=8, proposal=PROPOSALS["staged"]) as tr:
+        losses = tr.fit(wins, epochs=args.indep_train_epochs, batch=512, lr=2e-3, seed=9)
+        blob = tr.blob()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    def batch_chains(mode, n_ch, n_steps, seed):
+        with ising.Batch([L] * n_ch, [beta], 1, stream=stream, seed=seed) as b:
+            ising.ising_batch_set_series(b.h, n_steps)
+            b.run(args.indep_thermalise)  # plain-sweep equilibrium for every method
+            if mode == "learned":
+                ising.ising_batch_nn_load(b.h, blob)
+                ising.ising_batch_set_proposal(b.h, PROPOSALS["staged"])
+
+                def go():
+                    for _ in range(n_steps):
+                        b.run(1)
+                        ising.ising_batch_block_pass(b.h, 1, block)
+            else:
+                def go():
+                    b.run(n_steps)
+            secs = timed(go)
+            st, _ = ising.ising_batch_status(b.h)
+            E, M, _ = ising.ising_batch_series(b.h, n_steps, n_ch)
+            acc = ising.ising_batch_block_stats(b.h) if mode == "learned" else (0, 0)
+        assert st == 0, "batch status %d" % st
+        return E.astype(np.float64), np.abs(M).astype(np.float64), secs, acc
+
+    out = {"L": L, "beta": beta, "block": block}
+    for mode, n_ch, n_steps in (("plain", args.indep_chains, args.indep_plain_sweeps),
+                                ("learned", args.indep_learned_chains, args.indep_learned_steps)):
+        E, M, secs, acc = batch_chains(mode, n_ch, n_steps, 11)
+        tm, dtm = stats.tau_int_chains(M)
+        te, dte = stats.tau_int_chains(E)
+        out[mode] = {"chains": n_ch, "steps_per_chain": n_steps,
+                     "tau_int_absM": tm, "tau_int_absM_err": dtm, "tau_int_E": te, "tau_int_E_err": dte,
+                     "run_over_tau_absM": n_steps / tm, "run_over_tau_E": n_steps / te,
+                     "batch_steps_per_s_per_chain": n_steps / secs,
+                     "batch_indep_absM_per_s": n_ch * n_steps / secs / (2 * tm),
+                     "batch_indep_E_per_s": n_ch * n_steps / secs / (2 * te),
+                     "mean_absm": float(M.mean() / (L * L)), "mean_e": float(E.mean() / (L * L))}
+        if mode == "learned":
+            out[mode]["block_acceptance"] = acc[1] / max(acc[0], 1)
+    # one chain alone on the GPU
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=21) as lat:
+        lat.sweep(2000, 0)
+        n = args.indep_single_steps
+        secs = timed(lambda: ising.ising_sweep(lat.ctx, 10 * n, 1))
+        out["plain"]["single_steps_per_s"] = 10 * n / secs
+        ising.ising_nn_load(lat.ctx, blob)
+        ising.ising_set_proposal(lat.ctx, PROPOSALS["staged"])
+        secs = timed(lambda: ising.ising_sweep_blocks(lat.ctx, n, 1, block, 1))
+        out["learned"]["single_steps_per_s"] = n / secs
+        secs = timed(lambda: ising.ising_sw_step(lat.ctx, 5 * n, 1))
+        out["sw"] = {"single_steps_per_s": 5 * n / secs}
+    Ms, Es = [], []
+    for c in range(8):
+        with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=40 + c) as lat:
+            ising.ising_sw_step(lat.ctx, 200, 0)
+            ising.ising_sw_step(lat.ctx, 4000, 1)
+            E, M = lat.series(4000)
+            Ms.append(np.abs(M).astype(np.float64))
+            Es.append(E.astype(np.float64))
+    tm, dtm = stats.tau_int_chains(np.stack(Ms, 1))
+    te, dte = stats.tau_int_chains(np.stack(Es, 1))
+    out["sw"].update({"chains": 8, "steps_per_chain": 4000, "tau_int_absM": tm, "tau_int_absM_err": dtm,
+                      "tau_int_E": te, "tau_int_E_err": dte})
+    for m in ("plain", "learned", "sw"):
+        o = out[m]
+        o["single_indep_absM_per_s"] = o["single_steps_per_s"] / (2 * o["tau_int_absM"])
+        o["single_indep_E_per_s"] = o["single_steps_per_s"] / (2 * o["tau_int_E"])
+
+    def ratio(a, b, key, err_a, err_b):
+        r = a[key] / b[key]
+        return r, r * float(np.hypot(err_a, err_b))
+
+    pl, le = out["plain"], out["learned"]
+    gains = {}
+    for obs in ("absM", "E"):
+        rel_l = le["tau_int_%s_err" % obs] / le["tau_int_%s" % obs]
+        rel_p = pl["tau_int_%s_err" % obs] / pl["tau_int_%s" % obs]
+        for reg in ("single", "batch"):
+            r, dr = ratio(le, pl, "%s_indep_%s_per_s" % (reg, obs), rel_l, rel_p)
+            gains["learned_over_plain_%s_%s" % (reg, obs)] = [r, dr]
+    out["gain"] = gains
+    out["train"] = {"windows": int(len(wins)), "epochs": args.indep_train_epochs,
+                    "loss_first": float(np.mean(losses[:5])), "loss_last": float(np.mean(losses[-5:])),
+                    "seconds": t_train}
+    out["seconds"] = time.perf_counter() - t_all
+    out["note"] = ("tau_int in steps (plain: sweeps; learned: sweep + staged block pass; sw: "
+                   "Swendsen-Wang steps); gains are independent samples/s of the learned chain over "
+                   "the plain chain, [value, 1-sigma] from the tau errors; 'single' = one chain alone on "
+                   "the GPU, 'batch' = the chains of one batch together")
+    return out
 
 
 def run_batch(args):
@@ -964,6 +1098,16 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the fixed kernel shape instead of the autotuner's choice")
+    ap.add_argument("--no-indep", action="store_true",
+                    help="skip the independent-samples comparison at beta_c (plain / learned / SW)")
+    ap.add_argument("--indep-chains", type=int, default=64)
+    ap.add_argument("--indep-plain-sweeps", type=int, default=200000)
+    ap.add_argument("--indep-learned-chains", type=int, default=32)
+    ap.add_argument("--indep-learned-steps", type=int, default=12000)
+    ap.add_argument("--indep-single-steps", type=int, default=2000)
+    ap.add_argument("--indep-thermalise", type=int, default=20000)
+    ap.add_argument("--indep-train-windows", type=int, default=60000)
+    ap.add_argument("--indep-train-epochs", type=int, default=3)
     ap.add_argument("--train-windows", type=int, default=100000)
     ap.add_argument("--proposal", choices=sorted(PROPOSALS), default="staged",
                     help="learned block proposal family (learned workloads)")

@@ -51,6 +51,9 @@ struct alignas(16) StagedPlan {
   // [off3[k], off3[k+1])
   int16_t off1[kMaxStages + 1], off2[kMaxStages + 1], off3[kMaxStages + 1];
   int16_t l1[kMaxList], l2[kMaxList], l3[kMaxB * kMaxB];
+  // for each l1 entry: bit t (t = 3 (dy + 1) + dx + 1) set iff the input tap at
+  // offset (dy, dx) is a known site before the entry's stage
+  uint16_t m1[kMaxList];
 };
 static_assert(sizeof(StagedPlan) % 16 == 0, "the plan is copied to shared memory as uint4");
 
@@ -73,19 +76,20 @@ __host__ __device__ __forceinline__ bool ring_edge(int fy, int fx, int F) {
   return ey || ex;
 }
 
-// P_i = clamp(rint(sigmoid(l) 2^32), 1, 2^32 - 1)
+// P_i = clamp(rint(sigmoid(l) 2^32), 1, 2^32 - 1).  p 2^32 is exact in FP32
+// (a power-of-two scaling); rounding it to an integer (ties to even) and the
+// saturating conversion give the same integer as the same steps in FP64.
 __device__ __forceinline__ uint32_t quantise_p(float logit) {
   const float p = 1.f / (1.f + expf(-logit));
-  const double v = rint((double)p * 4294967296.0);
-  if (v < 1.0) return 1u;
-  if (v > 4294967295.0) return 0xffffffffu;
-  return (uint32_t)v;
+  const uint32_t v = __float2uint_rn(p * 4294967296.f);  // saturates at 2^32 - 1
+  return v < 1u ? 1u : v;
 }
 
-// log2 of (P or 2^32 - P) / 2^32
+// log2 of (P or 2^32 - P) / 2^32, the count rounded to FP32 first (P in
+// [1, 2^32 - 1], so 2^32 - P = -P in 32-bit unsigned arithmetic)
 __device__ __forceinline__ float log2_q_term(uint32_t P, int s) {
-  const double num = s > 0 ? (double)P : 4294967296.0 - (double)P;
-  return log2f((float)num) - 32.f;
+  const uint32_t num = s > 0 ? P : 0u - P;
+  return log2f(__uint2float_rn(num)) - 32.f;
 }
 
 __device__ __forceinline__ int get_spin(const uint32_t* planes, int L, int Wc, int y, int x) {

@@ -29,6 +29,7 @@
 // logits read it, and logits only at the stage's sites (position lists from
 // the plan).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,6 +68,12 @@ struct Builder {
       for (int fx = 0; fx < F; ++fx) known[(size_t)fy * F + fx] = ring_edge(fy, fx, F) ? 1 : 0;
   }
   bool kn(int fy, int fx) const { return known[(size_t)fy * F + fx] != 0; }
+  int stage_index_of(int iy, int ix) const {
+    for (size_t k = 0; k < stages.size(); ++k)
+      for (int i : stages[k])
+        if (i == iy * B + ix) return (int)k;
+    return 1 << 30;
+  }
   void add(bool is_exact, const std::vector<int>& sites) {
     stages.push_back(sites);
     exact.push_back(is_exact ? 1 : 0);
@@ -184,6 +191,16 @@ bool build_plan(int B, int kind, StagedPlan* out) {
         }
         if (need1[p]) {
           if (n1 >= kMaxList) return false;
+          const int py = p / F, px = p % F;
+          uint16_t m = 0;
+          for (int t = 0; t < 9; ++t) {
+            const int qy = py + t / 3 - 1, qx = px + t % 3 - 1;
+            if (qy < 0 || qy >= F || qx < 0 || qx >= F) continue;
+            const bool inner = qy >= 1 && qy <= B && qx >= 1 && qx <= B;
+            const bool kn = inner ? (b.stage_index_of(qy - 1, qx - 1) < k) : ring_edge(qy, qx, F);
+            if (kn) m |= (uint16_t)(1u << t);
+          }
+          out->m1[n1] = m;
           out->l1[n1++] = (int16_t)p;
         }
       }
@@ -203,20 +220,24 @@ namespace {
 
 constexpr int kFP = kMaxB + 4;  // padded grid side (frame + zero border)
 
+// Two windows are evaluated side by side in every layer phase: window 0 =
+// the square's ring plus the sites drawn so far (the proposal being drawn),
+// window 1 = ring plus the current interior (teacher forcing for q(old)).
+// Layer 2 runs in FP16 (both MMA operands): the activations are rounded to
+// FP16 (11-bit significand; BF16's 8 bits would leave ~1 % logit errors), and
+// the weights are the BF16 weight values held in FP16, which represents every
+// BF16 value of magnitude 2^-14 .. 65504 exactly.
 struct StagedSmem {
-  // layer-1 activations as a BF16 pair hi + lo (the tensor-core A operand with
-  // ~16 mantissa bits), layer-2 activations in FP32; zero border of one
-  __nv_bfloat16 h1[kFP * kFP * kCP];
-  __nv_bfloat16 h1lo[kFP * kFP * kCP];
-  float h2[kFP * kFP * kC];
-  __nv_bfloat16 w2t[kC * kK2P];
+  __half h1[2][kFP * kFP * kCP];  // layer-1 activations (tensor-core A operand), zero border
+  float h2[2][kFP * kFP * kC];    // layer-2 activations (FP32), zero border
+  __half w2t[kC * kK2P];
   float w1[kOffB1 + kC];  // W1 then b1
   float w3[kC * 9 + 1];   // W3 then b3
   float b2[kC];
-  float logit[kMaxB * kMaxB];
+  float logit[2][kMaxB * kMaxB];
+  float csum[4];              // exact-stage term of a summed neighbour, h = -3, -1, 1, 3
   uint32_t u[kMaxB * kMaxB];  // per-site draw uniforms
-  int8_t win[kMaxFrame];      // ring + the sites drawn so far (new interior)
-  int8_t wold[kMaxFrame];     // ring + current interior
+  int8_t win[2][kMaxFrame];
   float red_lq[kInferThreads / 32];
   int red_de[kInferThreads / 32];
   int accept;
@@ -224,125 +245,200 @@ struct StagedSmem {
 };
 static_assert(offsetof(StagedSmem, w2t) % 16 == 0 && offsetof(StagedSmem, plan) % 16 == 0,
               "uint4 copies into shared memory");
+static_assert(sizeof(StagedSmem) <= 227 * 1024, "one CTA per SM must fit");
 
 __device__ void load_all(StagedSmem& S, const __nv_bfloat16* __restrict__ w,
                          const __nv_bfloat16* __restrict__ w2t, const StagedPlan* __restrict__ plan) {
   for (int i = threadIdx.x; i < kOffB1 + kC; i += blockDim.x) S.w1[i] = bf(w[kOffW1 + i]);
   for (int i = threadIdx.x; i < kC * 9 + 1; i += blockDim.x) S.w3[i] = bf(w[kOffW3 + i]);
   for (int i = threadIdx.x; i < kC; i += blockDim.x) S.b2[i] = bf(w[kOffB2 + i]);
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(w2t);
-    uint4* dst = reinterpret_cast<uint4*>(S.w2t);
-    for (int i = threadIdx.x; i < kC * kK2P * 2 / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-  }
+  for (int i = threadIdx.x; i < kC * kK2P; i += blockDim.x) S.w2t[i] = __float2half_rn(bf(w2t[i]));
   {
     const uint4* src = reinterpret_cast<const uint4*>(plan);
     uint4* dst = reinterpret_cast<uint4*>(&S.plan);
     for (int i = threadIdx.x; i < (int)(sizeof(StagedPlan) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
   }
-  const __nv_bfloat16 z = __float2bfloat16(0.f);
-  for (int i = threadIdx.x; i < kFP * kFP * kCP; i += blockDim.x) {
-    S.h1[i] = z;
-    S.h1lo[i] = z;
+  // Only the one-position border of the padded grids is read without being
+  // written first (every other position a layer reads was computed in the same
+  // stage), so only the border is zeroed.
+  const int FB = __ldg(&plan->B) + 4;  // frame + border extent in the kFP-stride grids
+  const __half z = __float2half_rn(0.f);
+  for (int t = threadIdx.x; t < 2 * 4 * FB; t += blockDim.x) {
+    const int wi = t / (4 * FB), e = t - wi * 4 * FB, side = e / FB, o = e - side * FB;
+    const int gy = side == 0 ? 0 : (side == 1 ? FB - 1 : o);
+    const int gx = side < 2 ? o : (side == 2 ? 0 : FB - 1);
+    const int g = gy * kFP + gx;
+    for (int c = 0; c < kCP; ++c) S.h1[wi][g * kCP + c] = z;
+    for (int c = 0; c < kC; ++c) S.h2[wi][g * kC + c] = 0.f;
   }
-  for (int i = threadIdx.x; i < kFP * kFP * kC; i += blockDim.x) S.h2[i] = 0.f;
 }
 
-// Layer 1 (CUDA cores) at the listed frame positions: input channel 0 = spin
-// of w where known before stage k, channel 1 = known mask; only known taps
-// contribute (ascending tap order).
-__device__ void layer1s(StagedSmem& S, const int8_t* w, int k, const int16_t* list, int n) {
-  const int B = S.plan.B, F = B + 2, FP = F + 2;
-  for (int task = threadIdx.x; task < n * (kC / 4); task += blockDim.x) {
-    const int cg = task & (kC / 4 - 1), idx = task / (kC / 4);
-    const int p = list[idx];
-    const int fy = p / F, fx = p - (p / F) * F;
-    unsigned mask = 0;
+// Layer-1 weights as per-lane mma.sync B fragments (FP16 pairs), built once
+// per CTA.  Layer 1 is a GEMM with K = 9 taps x 2 input channels, ordered
+// k = 2 t + ch and padded to 32: k-step 0 holds taps 0..7, k-step 1 tap 8.
+// For lane (g = lane / 4, q = lane % 4) and n-tile nt (channel n = 8 nt + g):
+// kb0 = (W1[n][0][q], W1[n][1][q]), kb1 = taps q + 4, kb2 = tap 8 (q = 0 only).
+struct L1Frag {
+  uint32_t kb0[4], kb1[4], kb2[4];
+};
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ L1Frag layer1_frags(const StagedSmem& S) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  L1Frag f;
 #pragma unroll
-    for (int t = 0; t < 9; ++t)
-      if (known_at(S.plan, fy + t / 3 - 1, fx + t % 3 - 1, k)) mask |= 1u << t;
-    float z[4];
+  for (int nt = 0; nt < 4; ++nt) {
+    const int n = nt * 8 + g;
+    f.kb0[nt] = pack_h2(S.w1[(n * 2 + 0) * 9 + q], S.w1[(n * 2 + 1) * 9 + q]);
+    f.kb1[nt] = pack_h2(S.w1[(n * 2 + 0) * 9 + q + 4], S.w1[(n * 2 + 1) * 9 + q + 4]);
+    f.kb2[nt] = q == 0 ? pack_h2(S.w1[(n * 2 + 0) * 9 + 8], S.w1[(n * 2 + 1) * 9 + 8]) : 0u;
+  }
+  return f;
+}
+
+// A-fragment half pair (spin x known, known) of the input tap at window index
+// p + off (tap t of the 3 x 3 stencil); taps outside the frame or not yet
+// known (bit t of mask clear) give (0, 0).
+__device__ __forceinline__ uint32_t l1_tap(const int8_t* w, int p, int off, unsigned mask, int t) {
+  if (!((mask >> t) & 1u)) return 0u;
+  return pack_h2((float)w[p + off], 1.f);
+}
+
+// Layer 1 on the tensor cores for windows 0 .. nw-1 at the listed frame
+// positions (known-tap masks from the plan): mma.sync m16n8k16 FP16 -> FP32,
+// A fragments built in registers from the spin grid; epilogue bias + ReLU,
+// FP16 into the activation grid.
+__device__ void layer1t(StagedSmem& S, const L1Frag& f, int nw, const int16_t* list,
+                        const uint16_t* masks, int n) {
+  const int F = S.plan.B + 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int rows = nw * n;
+  const int n_mt = (rows + 15) / 16;
+  // window-index offsets of this lane's taps q, q + 4 and 8
+  const int off0 = (q / 3 - 1) * F + q % 3 - 1;
+  const int off1 = ((q + 4) / 3 - 1) * F + (q + 4) % 3 - 1;
+  const int off2 = F + 1;
+  for (int mt = warp; mt < n_mt; mt += nwarps) {
+    uint32_t a[2][3];  // [row g / g + 8][tap q, tap q + 4, tap 8]
+    int pos[2], wsel[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) z[j] = S.w1[kOffB1 + 4 * cg + j];
-    while (mask) {
-      const int t = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const float sv = (float)w[(fy + t / 3 - 1) * F + fx + t % 3 - 1];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = 4 * cg + j;
-        z[j] += S.w1[(c * 2 + 0) * 9 + t] * sv + S.w1[(c * 2 + 1) * 9 + t];
+    for (int h = 0; h < 2; ++h) {
+      const int r = mt * 16 + g + 8 * h;
+      a[h][0] = a[h][1] = a[h][2] = 0u;
+      pos[h] = -1;
+      wsel[h] = 0;
+      if (r < rows) {
+        const int wi = r >= n ? 1 : 0;
+        const int idx = r - wi * n;
+        const int p = list[idx];
+        const unsigned m = masks[idx];
+        const int fy = p / F, fx = p - (p / F) * F;
+        const int8_t* w = S.win[wi];
+        a[h][0] = l1_tap(w, p, off0, m, q);
+        a[h][1] = l1_tap(w, p, off1, m, q + 4);
+        a[h][2] = q == 0 ? l1_tap(w, p, off2, m, 8) : 0u;
+        pos[h] = (fy + 1) * kFP + fx + 1;
+        wsel[h] = wi;
       }
     }
+    float acc[4][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = 4 * cg + j;
-      const float h = fmaxf(z[j], 0.f);
-      const __nv_bfloat16 hi = __float2bfloat16(h);
-      S.h1[((fy + 1) * FP + fx + 1) * kCP + c] = hi;
-      S.h1lo[((fy + 1) * FP + fx + 1) * kCP + c] = __float2bfloat16(h - __bfloat162float(hi));
+    for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[nt][j] = 0.f;
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
+          "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+          : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+          : "r"(a[0][0]), "r"(a[1][0]), "r"(a[0][1]), "r"(a[1][1]), "r"(f.kb0[nt]), "r"(f.kb1[nt]));
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
+          "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+          : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+          : "r"(a[0][2]), "r"(a[1][2]), "r"(0u), "r"(0u), "r"(f.kb2[nt]), "r"(0u));
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (pos[h] < 0) continue;
+      __half* dst = &S.h1[wsel[h]][pos[h] * kCP];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int c = nt * 8 + 2 * q;
+        const __half2 v = __floats2half2_rn(fmaxf(acc[nt][2 * h] + S.w1[kOffB1 + c], 0.f),
+                                            fmaxf(acc[nt][2 * h + 1] + S.w1[kOffB1 + c + 1], 0.f));
+        *reinterpret_cast<__half2*>(dst + c) = v;
+      }
     }
   }
 }
 
-// Layer 2 on the tensor cores at the listed frame positions: implicit GEMM,
-// M = positions, N = 32 channels, K = 288 (tap-major, 16 channels per step),
-// mma.sync m16n8k16 BF16 -> FP32, A rows gathered by ldmatrix straight from
-// the zero-padded activation grid (hi and lo parts into one accumulator).
-__device__ void layer2s(StagedSmem& S, const int16_t* list, int M) {
-  const int F = S.plan.B + 2, FP = F + 2;
+// Layer 2 on the tensor cores for windows 0 .. nw-1 at the listed frame
+// positions: implicit GEMM, M = nw x positions, N = 32 channels, K = 288
+// (tap-major, 16 channels per step), mma.sync m16n8k16 FP16 -> FP32, A rows
+// gathered by ldmatrix (one row address per lane) straight from the
+// zero-padded activation grid of the row's window.
+__device__ void layer2s(StagedSmem& S, int nw, const int16_t* list, int M) {
+  const int F = S.plan.B + 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int n_mt = (M + 15) / 16;
+  const int rows = nw * M;
+  const int n_mt = (rows + 15) / 16;
   for (int mt = warp; mt < n_mt; mt += nwarps) {
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    const int row = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-    const int p = row >= M ? list[0] : list[row];  // padding rows: any valid row, results dropped
+    int row = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+    if (row >= rows) row = 0;  // padding rows: any valid row, results dropped
+    const int wi = row >= M ? 1 : 0;
+    const int p = list[row - wi * M];
     const int py = p / F, px = p - (p / F) * F;
-    const int acol = (lane >> 4) * 8;
-#pragma unroll 1
+    // this lane's A row address (tap (0, 0), first 8 channels of its half)
+    const uint32_t abase = smem_addr(S.h1[wi] + (py * kFP + px) * kCP + (lane >> 4) * 8);
+    // this lane's B row address for ldmatrix.x4: n-tiles nt, nt + 1 of W2
+    // (lanes 16..31 give the second one), k half (lane / 8) % 2
+    const uint32_t bbase = smem_addr(S.w2t + ((lane >> 4) * 8 + (lane & 7)) * kK2P + ((lane >> 3) & 1) * 8);
+#pragma unroll
     for (int kc = 0; kc < 18; ++kc) {
       const int tap = kc >> 1, ci0 = (kc & 1) * 16;
       const int dy = tap / 3, dx = tap - (tap / 3) * 3;
-      const int aoff = ((py + dy) * FP + px + dx) * kCP + ci0 + acol;
-      uint32_t a0, a1, a2, a3, l0, l1, l2, l3;
+      uint32_t a0, a1, a2, a3;
       asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                    : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
-                   : "r"(smem_addr(&S.h1[aoff])));
-      asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                   : "=r"(l0), "=r"(l1), "=r"(l2), "=r"(l3)
-                   : "r"(smem_addr(&S.h1lo[aoff])));
+                   : "r"(abase + (uint32_t)(((dy * kFP + dx) * kCP + ci0) * 2)));
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const __nv_bfloat16* brow =
-            &S.w2t[(nt * 8 + (lane & 7)) * kK2P + kc * 16 + ((lane >> 3) & 1) * 8];
-        uint32_t b0, b1;
-        asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-                     : "=r"(b0), "=r"(b1)
-                     : "r"(smem_addr(brow)));
+      for (int np = 0; np < 2; ++np) {
+        uint32_t b0, b1, b2, b3;
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(b0), "=r"(b1), "=r"(b2), "=r"(b3)
+                     : "r"(bbase + (uint32_t)((np * 16 * kK2P + kc * 16) * 2)));
         asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
             "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-            : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+            : "+f"(acc[2 * np][0]), "+f"(acc[2 * np][1]), "+f"(acc[2 * np][2]), "+f"(acc[2 * np][3])
             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
         asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
             "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-            : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
-            : "r"(l0), "r"(l1), "r"(l2), "r"(l3), "r"(b0), "r"(b1));
+            : "+f"(acc[2 * np + 1][0]), "+f"(acc[2 * np + 1][1]), "+f"(acc[2 * np + 1][2]),
+              "+f"(acc[2 * np + 1][3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b2), "r"(b3));
       }
     }
     const int g = lane >> 2, t2 = (lane & 3) * 2;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const int rr = mt * 16 + g + half * 8;
-      if (rr >= M) continue;
-      const int pp = list[rr];
+      if (rr >= rows) continue;
+      const int ow = rr >= M ? 1 : 0;
+      const int pp = list[rr - ow * M];
       const int fy = pp / F, fx = pp - (pp / F) * F;
-      float* dst = &S.h2[((fy + 1) * FP + fx + 1) * kC];
+      float* dst = &S.h2[ow][((fy + 1) * kFP + fx + 1) * kC];
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         const int c = nt * 8 + t2;
@@ -353,26 +449,30 @@ __device__ void layer2s(StagedSmem& S, const int16_t* list, int M) {
   }
 }
 
-// Layer 3 (CUDA cores): logits at the listed interior indices; eight lanes
-// per logit, four channels each over the nine taps, shuffle sum.
-__device__ void layer3s(StagedSmem& S, const int16_t* list, int n) {
-  const int B = S.plan.B, F = B + 2, FP = F + 2;
+// Layer 3 (CUDA cores) for windows 0 .. nw-1: logits at the listed interior
+// indices; eight lanes per logit, four channels each over the nine taps,
+// shuffle sum.
+__device__ void layer3s(StagedSmem& S, int nw, const int16_t* list, int n) {
+  const int B = S.plan.B;
   const int sub = threadIdx.x & 7, c0 = 4 * sub;
   const int per = (int)(blockDim.x >> 3);
-  const int rounds = (n + per - 1) / per;
+  const int total = nw * n;
+  const int rounds = (total + per - 1) / per;
   for (int r = 0; r < rounds; ++r) {
     const int k = r * per + (int)(threadIdx.x >> 3);
     float z = 0.f;
-    int i = 0;
-    if (k < n) {
-      i = list[k];
+    int i = 0, wi = 0;
+    if (k < total) {
+      wi = k >= n ? 1 : 0;
+      i = list[k - wi * n];
       const int iy = i / B, ix = i - (i / B) * B;
       const int fy = iy + 1, fx = ix + 1;
+      const float* h2 = S.h2[wi];
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
-          const float4 h = *reinterpret_cast<const float4*>(&S.h2[((fy + dy) * FP + fx + dx) * kC + c0]);
+          const float4 h = *reinterpret_cast<const float4*>(&h2[((fy + dy) * kFP + fx + dx) * kC + c0]);
           const int t = dy * 3 + dx;
           z += S.w3[(c0 + 0) * 9 + t] * h.x + S.w3[(c0 + 1) * 9 + t] * h.y +
                S.w3[(c0 + 2) * 9 + t] * h.z + S.w3[(c0 + 3) * 9 + t] * h.w;
@@ -381,7 +481,7 @@ __device__ void layer3s(StagedSmem& S, const int16_t* list, int n) {
     z += __shfl_xor_sync(0xffffffffu, z, 4);
     z += __shfl_xor_sync(0xffffffffu, z, 2);
     z += __shfl_xor_sync(0xffffffffu, z, 1);
-    if (k < n && sub == 0) S.logit[i] = z + S.w3[kC * 9];
+    if (k < total && sub == 0) S.logit[wi][i] = z + S.w3[kC * 9];
   }
 }
 
@@ -391,71 +491,56 @@ __device__ __forceinline__ float lcosh2(float x) {
   return a + log1pf(expf(-2.f * a));
 }
 
+// The exact-stage contribution lcosh(beta (h + 1)) - lcosh(beta (h - 1)) of a
+// summed neighbour whose other three neighbours sum to h (odd, |h| <= 3), for
+// the four values of h (threads 0..3; the caller synchronises).
+__device__ __forceinline__ void exact_table(StagedSmem& S, float beta) {
+  if (threadIdx.x < 4) {
+    const float h = (float)(2 * (int)threadIdx.x - 3);
+    S.csum[threadIdx.x] = lcosh2(beta * (h + 1.f)) - lcosh2(beta * (h - 1.f));
+  }
+}
+
 // Exact log-odds of s_i = +1 at stage k for window w (interior index i).
 __device__ float exact_logodds(const StagedSmem& S, const int8_t* w, int k, int i, float beta) {
   const int B = S.plan.B, F = B + 2;
   const int fy = i / B + 1, fx = i - (i / B) * B + 1;
-  const int dy[4] = {-1, 1, 0, 0}, dx[4] = {0, 0, -1, 1};
   float l = 0.f;
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
-    const int ny = fy + dy[d], nx = fx + dx[d];
+    const int ny = fy + (d == 0 ? -1 : (d == 1 ? 1 : 0));
+    const int nx = fx + (d == 2 ? -1 : (d == 3 ? 1 : 0));
     if (known_at(S.plan, ny, nx, k)) {
       l += 2.f * beta * (float)w[ny * F + nx];
     } else {
-      int h = 0;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int my = ny + dy[e], mx = nx + dx[e];
-        if (my == fy && mx == fx) continue;
-        h += w[my * F + mx];
-      }
-      l += lcosh2(beta * (float)(h + 1)) - lcosh2(beta * (float)(h - 1));
+      // h = the summed neighbour's other three neighbours: its four minus this
+      // site's entry (0 in window 0, where the site is not drawn yet; its
+      // current spin in window 1)
+      int h = -w[fy * F + fx];
+      h += w[(ny - 1) * F + nx] + w[(ny + 1) * F + nx] + w[ny * F + nx - 1] + w[ny * F + nx + 1];
+      l += S.csum[(h + 3) >> 1];
     }
   }
   return l;
 }
 
-// Logits of stage k for window w at the stage's sites (S.logit); the caller
-// synchronises before and after.
-__device__ void stage_eval(StagedSmem& S, const int8_t* w, int k, float beta) {
+// Network logits of stage k for windows 0 .. nw-1 at the stage's sites
+// (S.logit[w]); the caller synchronises before, this returns after the last
+// phase without a final barrier.
+__device__ void net_eval(StagedSmem& S, const L1Frag& f, int nw, int k) {
   const StagedPlan& P = S.plan;
-  const int a = P.off3[k], b = P.off3[k + 1];
-  if (P.exact[k]) {
-    for (int t = a + (int)threadIdx.x; t < b; t += blockDim.x) {
-      const int i = P.l3[t];
-      S.logit[i] = exact_logodds(S, w, k, i, beta);
-    }
-    return;
-  }
-  layer1s(S, w, k, P.l1 + P.off1[k], P.off1[k + 1] - P.off1[k]);
+  layer1t(S, f, nw, P.l1 + P.off1[k], P.m1 + P.off1[k], P.off1[k + 1] - P.off1[k]);
   __syncthreads();
-  layer2s(S, P.l2 + P.off2[k], P.off2[k + 1] - P.off2[k]);
+  layer2s(S, nw, P.l2 + P.off2[k], P.off2[k + 1] - P.off2[k]);
   __syncthreads();
-  layer3s(S, P.l3 + a, b - a);
-}
-
-// Teacher-forced log2 q of the interior of S.wold (every thread returns its
-// own sites' share; sum over the CTA for the total).
-__device__ float log2_q_old(StagedSmem& S, float beta) {
-  const StagedPlan& P = S.plan;
-  const int B = P.B, F = B + 2;
-  const int i = threadIdx.x;
-  const int my_stage = i < B * B ? P.stage_of[i] : -1;
-  float lq = 0.f;
-  for (int k = 0; k < P.n_stages; ++k) {
-    stage_eval(S, S.wold, k, beta);
-    __syncthreads();
-    if (my_stage == k) lq += log2_q_term(quantise_p(S.logit[i]), S.wold[(i / B + 1) * F + i % B + 1]);
-    __syncthreads();
-  }
-  return lq;
+  layer3s(S, nw, P.l3 + P.off3[k], P.off3[k + 1] - P.off3[k]);
 }
 
 // One staged MH update of square (bx, by) of a lattice (whole CTA).
-__device__ void process_square(StagedSmem& S, uint32_t* planes, int L, int Wc, int colour, int ox,
-                               int oy, int bx, int by, uint32_t pass, uint32_t replica,
-                               const RngParams& rng, float beta, unsigned long long* stats) {
+__device__ void process_square(StagedSmem& S, const L1Frag& f1, uint32_t* planes, int L, int Wc,
+                               int colour, int ox, int oy, int bx, int by, uint32_t pass,
+                               uint32_t replica, const RngParams& rng, float beta,
+                               unsigned long long* stats) {
   const StagedPlan& P = S.plan;
   const int B = P.B, F = B + 2, BB = B * B;
   const int nbx = L / B;
@@ -471,8 +556,8 @@ __device__ void process_square(StagedSmem& S, uint32_t* planes, int L, int Wc, i
       x = (x % L + L) % L;
       v = (int8_t)get_spin(planes, L, Wc, y, x);
     }
-    S.wold[i] = v;
-    S.win[i] = inner ? 0 : v;
+    S.win[1][i] = v;
+    S.win[0][i] = inner ? 0 : v;
   }
   for (int q = threadIdx.x; q < BB / 4; q += blockDim.x) {
     const uint4 r = philox10_rk(make_uint4(gid, pass, replica, ctr_w(kTagBlkSample, colour, q)),
@@ -482,42 +567,58 @@ __device__ void process_square(StagedSmem& S, uint32_t* planes, int L, int Wc, i
     S.u[4 * q + 2] = r.z;
     S.u[4 * q + 3] = r.w;
   }
+  exact_table(S, beta);
   __syncthreads();
-  const int i = threadIdx.x;
-  const int my_stage = i < BB ? P.stage_of[i] : -1;
-  const int fi = i < BB ? (i / B + 1) * F + i % B + 1 : 0;
-  float lq = 0.f;  // log2 q(old) - log2 q(new), this thread's sites
+  float lq = 0.f;  // log2 q(old) - log2 q(new) over this thread's draws
   for (int k = 0; k < P.n_stages; ++k) {
-    stage_eval(S, S.win, k, beta);
-    __syncthreads();
-    if (my_stage == k) {
-      const uint32_t Pq = quantise_p(S.logit[i]);
-      const int s = S.u[i] < Pq ? 1 : -1;
-      lq -= log2_q_term(Pq, s);
-      S.win[fi] = (int8_t)s;  // read by later stages only
+    // thread t draws the t-th site of the stage (consecutive threads, so only
+    // the first few warps do this phase's work)
+    const int t = threadIdx.x;
+    const bool mine = t < P.off3[k + 1] - P.off3[k];
+    const int si = mine ? P.l3[P.off3[k] + t] : 0;
+    const int sf = (si / B + 1) * F + si % B + 1;
+    if (P.exact[k]) {
+      // a site's exact conditional reads only sites known before stage k, so
+      // it is drawn at once (no other site of the stage reads it)
+      if (mine) {
+        const uint32_t Pn = quantise_p(exact_logodds(S, S.win[0], k, si, beta));
+        const int s = S.u[si] < Pn ? 1 : -1;
+        lq += log2_q_term(quantise_p(exact_logodds(S, S.win[1], k, si, beta)), S.win[1][sf]) -
+              log2_q_term(Pn, s);
+        S.win[0][sf] = (int8_t)s;
+      }
+    } else {
+      net_eval(S, f1, 2, k);
+      __syncthreads();
+      if (mine) {
+        const uint32_t Pn = quantise_p(S.logit[0][si]);
+        const int s = S.u[si] < Pn ? 1 : -1;
+        lq += log2_q_term(quantise_p(S.logit[1][si]), S.win[1][sf]) - log2_q_term(Pn, s);
+        S.win[0][sf] = (int8_t)s;
+      }
     }
-    __syncthreads();
-    stage_eval(S, S.wold, k, beta);
-    __syncthreads();
-    if (my_stage == k) lq += log2_q_term(quantise_p(S.logit[i]), S.wold[fi]);
     __syncthreads();
   }
   // bond energy change over the bonds touching the interior
+  const int i = threadIdx.x;
+  const int fi = i < BB ? (i / B + 1) * F + i % B + 1 : 0;
   int de = 0;
   if (i < BB) {
     const int fy = i / B + 1, fx = i % B + 1;
-    const int os = S.wold[fi], ns = S.win[fi];
+    const int8_t* wn = S.win[0];
+    const int8_t* wo = S.win[1];
+    const int os = wo[fi], ns = wn[fi];
     // bonds to the right and down (interior or ring), plus left / up bonds to
     // the ring: every bond touching the interior once
-    int e_old = -os * (S.wold[fy * F + fx + 1] + S.wold[(fy + 1) * F + fx]);
-    int e_new = -ns * (S.win[fy * F + fx + 1] + S.win[(fy + 1) * F + fx]);
+    int e_old = -os * (wo[fy * F + fx + 1] + wo[(fy + 1) * F + fx]);
+    int e_new = -ns * (wn[fy * F + fx + 1] + wn[(fy + 1) * F + fx]);
     if (fx == 1) {
-      e_old -= os * S.wold[fy * F];
-      e_new -= ns * S.win[fy * F];
+      e_old -= os * wo[fy * F];
+      e_new -= ns * wn[fy * F];
     }
     if (fy == 1) {
-      e_old -= os * S.wold[fx];
-      e_new -= ns * S.win[fx];
+      e_old -= os * wo[fx];
+      e_new -= ns * wn[fx];
     }
     de = e_new - e_old;
   }
@@ -549,7 +650,7 @@ __device__ void process_square(StagedSmem& S, uint32_t* planes, int L, int Wc, i
     if (S.accept) atomicAdd(&stats[1], 1ull);
   }
   __syncthreads();
-  if (S.accept && i < BB && S.win[fi] != S.wold[fi]) {
+  if (S.accept && i < BB && S.win[0][fi] != S.win[1][fi]) {
     const int y = (y0 + i / B) % L, x = (x0 + i % B) % L;
     const int c = (x + y) & 1, j = x >> 1;
     atomicXor(&planes[(size_t)c * L * Wc + (size_t)y * Wc + (j >> 5)], 1u << (j & 31));
@@ -566,7 +667,7 @@ struct StagedPassParams {
   unsigned long long* stats;  // [0] proposed, [1] accepted
 };
 
-__global__ void __launch_bounds__(kInferThreads) k_nn_staged_pass(StagedPassParams Q,
+__global__ void __launch_bounds__(kInferThreads, 1) k_nn_staged_pass(StagedPassParams Q,
                                                              const StagedPlan* __restrict__ plan,
                                                              const __nv_bfloat16* __restrict__ w,
                                                              const __nv_bfloat16* __restrict__ w2t) {
@@ -574,6 +675,7 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_staged_pass(StagedPassPara
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
+  const L1Frag f1 = layer1_frags(S);
   const int B = S.plan.B, L = Q.L;
   const int nbx = L / B, half = nbx / 2;
   const int n_sq = nbx * half;
@@ -581,7 +683,7 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_staged_pass(StagedPassPara
   block_offset(Q.pass, Q.rng.replica, Q.rng, B, ox, oy);
   for (int blk = blockIdx.x; blk < n_sq; blk += gridDim.x) {
     const int by = blk / half, bx = 2 * (blk - by * half) + ((by + Q.colour) & 1);
-    process_square(S, Q.planes, L, Q.Wc, Q.colour, ox, oy, bx, by, Q.pass, Q.rng.replica, Q.rng,
+    process_square(S, f1, Q.planes, L, Q.Wc, Q.colour, ox, oy, bx, by, Q.pass, Q.rng.replica, Q.rng,
                    Q.beta, Q.stats);
   }
 }
@@ -599,7 +701,7 @@ struct StagedBatchParams {
   unsigned long long* stats;
 };
 
-__global__ void __launch_bounds__(kInferThreads) k_nn_staged_batch_pass(StagedBatchParams Q,
+__global__ void __launch_bounds__(kInferThreads, 1) k_nn_staged_batch_pass(StagedBatchParams Q,
                                                                    const StagedPlan* __restrict__ plan,
                                                                    const __nv_bfloat16* __restrict__ w,
                                                                    const __nv_bfloat16* __restrict__ w2t) {
@@ -607,6 +709,7 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_staged_batch_pass(StagedBa
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
+  const L1Frag f1 = layer1_frags(S);
   const int B = S.plan.B;
   const long long total = Q.unit0[Q.n_rep];
   for (long long u = blockIdx.x; u < total; u += gridDim.x) {
@@ -624,13 +727,13 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_staged_batch_pass(StagedBa
     int ox, oy;
     block_offset(Q.pass, (uint32_t)r, Q.rng, B, ox, oy);
     const float beta = Q.beta_of_slot[Q.slot_of[r]];
-    process_square(S, Q.spins + Q.off[r], L, Wc, Q.colour, ox, oy, bx, by, Q.pass, (uint32_t)r, Q.rng,
-                   beta, Q.stats);
+    process_square(S, f1, Q.spins + Q.off[r], L, Wc, Q.colour, ox, oy, bx, by, Q.pass, (uint32_t)r,
+                   Q.rng, beta, Q.stats);
   }
 }
 
-// Stage logits of windows (tests and diagnostics).
-__global__ void __launch_bounds__(kInferThreads) k_nn_stage_logits(const int8_t* __restrict__ windows,
+// Stage logits of windows (tests and diagnostics): window k in S.win[0].
+__global__ void __launch_bounds__(kInferThreads, 1) k_nn_stage_logits(const int8_t* __restrict__ windows,
                                                               int n, int stage, float beta,
                                                               const StagedPlan* __restrict__ plan,
                                                               const __nv_bfloat16* __restrict__ w,
@@ -640,21 +743,29 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_stage_logits(const int8_t*
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
+  const L1Frag f1 = layer1_frags(S);
   const int B = S.plan.B, F = B + 2, BB = B * B;
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
-    for (int i = threadIdx.x; i < F * F; i += blockDim.x) S.win[i] = windows[(size_t)k * F * F + i];
-    for (int i = threadIdx.x; i < BB; i += blockDim.x) S.logit[i] = 0.f;
+    for (int i = threadIdx.x; i < F * F; i += blockDim.x) S.win[0][i] = windows[(size_t)k * F * F + i];
+    for (int i = threadIdx.x; i < BB; i += blockDim.x) S.logit[0][i] = 0.f;
+    exact_table(S, beta);
     __syncthreads();
-    stage_eval(S, S.win, stage, beta);
+    if (S.plan.exact[stage]) {
+      for (int i = threadIdx.x; i < BB; i += blockDim.x)
+        if (S.plan.stage_of[i] == stage) S.logit[0][i] = exact_logodds(S, S.win[0], stage, i, beta);
+    } else {
+      net_eval(S, f1, 1, stage);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < BB; i += blockDim.x)
-      out[(size_t)k * BB + i] = S.plan.stage_of[i] == stage ? S.logit[i] : 0.f;
+      out[(size_t)k * BB + i] = S.plan.stage_of[i] == stage ? S.logit[0][i] : 0.f;
     __syncthreads();
   }
 }
 
-// Teacher-forced ln q of windows (tests and diagnostics).
-__global__ void __launch_bounds__(kInferThreads) k_nn_log_q(const int8_t* __restrict__ windows, int n,
+// Teacher-forced ln q of windows (tests and diagnostics): window k in S.win[1],
+// the same per-stage evaluation as q(old) in process_square.
+__global__ void __launch_bounds__(kInferThreads, 1) k_nn_log_q(const int8_t* __restrict__ windows, int n,
                                                        float beta, const StagedPlan* __restrict__ plan,
                                                        const __nv_bfloat16* __restrict__ w,
                                                        const __nv_bfloat16* __restrict__ w2t,
@@ -663,11 +774,32 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_log_q(const int8_t* __rest
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
-  const int F = S.plan.B + 2;
+  const L1Frag f1 = layer1_frags(S);
+  const StagedPlan& P = S.plan;
+  const int B = P.B, F = B + 2;
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
-    for (int i = threadIdx.x; i < F * F; i += blockDim.x) S.wold[i] = windows[(size_t)k * F * F + i];
+    for (int t = threadIdx.x; t < F * F; t += blockDim.x) {
+      const int8_t v = windows[(size_t)k * F * F + t];
+      S.win[1][t] = v;
+      S.win[0][t] = v;  // layer phases run on windows 0 and 1; both hold the window here
+    }
+    exact_table(S, beta);
     __syncthreads();
-    float lq = log2_q_old(S, beta);
+    float lq = 0.f;
+    for (int st = 0; st < P.n_stages; ++st) {
+      const int t = threadIdx.x;
+      const bool mine = t < P.off3[st + 1] - P.off3[st];
+      const int si = mine ? P.l3[P.off3[st] + t] : 0;
+      const int sf = (si / B + 1) * F + si % B + 1;
+      if (P.exact[st]) {
+        if (mine) lq += log2_q_term(quantise_p(exact_logodds(S, S.win[1], st, si, beta)), S.win[1][sf]);
+      } else {
+        net_eval(S, f1, 2, st);
+        __syncthreads();
+        if (mine) lq += log2_q_term(quantise_p(S.logit[1][si]), S.win[1][sf]);
+      }
+      __syncthreads();
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lq += __shfl_xor_sync(0xffffffffu, lq, o);
     if ((threadIdx.x & 31) == 0) S.red_lq[threadIdx.x >> 5] = lq;

@@ -61,6 +61,53 @@ def tau_int(x, c: float = 5.0) -> float:
     return float(max(tau, 0.5))
 
 
+def _pooled_acf(X, mean):
+    """Autocovariance averaged over the columns of X (steps x chains), about
+    a common mean, normalised to rho(0) = 1."""
+    n = X.shape[0]
+    Y = X - mean
+    f = np.fft.rfft(Y, 2 * n, axis=0)
+    acov = np.fft.irfft(f * np.conj(f), axis=0)[:n].sum(axis=1)
+    if acov[0] == 0.0:
+        out = np.zeros(n)
+        out[0] = 1.0
+        return out
+    return acov / acov[0]
+
+
+def _sokal(rho, c):
+    tau = 0.5
+    for W in range(1, rho.size):
+        tau += rho[W]
+        if W >= c * tau:
+            return float(max(tau, 0.5))
+    return float(max(tau, 0.5))
+
+
+def tau_int_chains(X, c: float = 5.0, groups: int = 8):
+    """tau_int of an observable recorded by many independent chains of the
+    same process: X (steps x chains).  The autocorrelation is pooled over the
+    chains (deviations from the grand mean) before Sokal's automatic window;
+    the error is a jackknife over `groups` groups of chains.  Returns
+    (tau, error)."""
+    X = np.asarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    tau = _sokal(_pooled_acf(X, X.mean()), c)
+    g = min(groups, X.shape[1])
+    if g < 2:
+        return tau, float("nan")
+    parts = np.array_split(np.arange(X.shape[1]), g)
+    jk = []
+    for p in parts:
+        keep = np.setdiff1d(np.arange(X.shape[1]), p)
+        Xk = X[:, keep]
+        jk.append(_sokal(_pooled_acf(Xk, Xk.mean()), c))
+    jk = np.asarray(jk)
+    err = float(np.sqrt((g - 1) / g * ((jk - jk.mean()) ** 2).sum()))
+    return tau, err
+
+
 def mean_and_error(x, discard: int = 0):
     x = np.asarray(x, dtype=np.float64)[discard:]
     return float(x.mean()), blocking_error(x)

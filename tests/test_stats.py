@@ -35,3 +35,14 @@ def test_independent_samples_per_second():
     x = _ar1(0.0, 100000, 1)
     v = stats.independent_samples_per_second(x, seconds=10.0, chains=2)
     assert abs(v - 100000 / 10 / 1.0 * 2) < 0.1 * v
+
+
+def test_tau_int_chains_ar1():
+    """Pooled over 32 short AR(1) chains (each 40 tau long) the estimate agrees
+    with the closed form within its jackknife error (and 10 %)."""
+    rho = 0.95
+    want = ar1_tau_int(rho)  # 19.5
+    X = np.stack([_ar1(rho, 800, 100 + s) for s in range(32)], axis=1)
+    tau, err = stats.tau_int_chains(X)
+    assert err > 0
+    assert abs(tau - want) < max(3 * err, 0.1 * want), (tau, err, want)
