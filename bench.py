@@ -141,18 +141,25 @@ def measured_peaks() -> dict:
 # 33.70 MB read + 0.66 MB written per launch (2 sweeps) after ncu's cache flush.
 # Reported only for that shape; any other shape reports null.
 NCU_TRAFFIC = {"shape": (2, 228, 64), "bytes_per_launch": 33.70e6 + 0.66e6}
-# Algorithmic integer lane-operations per site update of the bit-sliced,
-# lazily evaluated acceptance test (per 32-site word: neighbour classes and
-# update 24 ops, E[Philox blocks] = 1.95 x 40 ops, 4 x 1.95 planes x 5 ops),
-# i.e. (24 + 78 + 39) / 32.
-ALU_OPS_PER_SITE = 141.0 / 32.0
-INT32_LANES_PER_SM = 128
+# Algorithmic work of the bit-sliced, lazily evaluated acceptance test per
+# 32-site word, by the pipe it issues to.  ALU pipe (three-input logic, shifts):
+# neighbour classes + funnel shift + update 13; per Philox4x32-10 block
+# 10 rounds x 2 three-input XORs = 20, plus 4 planes x 3 logic ops (threshold
+# bit, accept, still undecided) = 12; E[blocks] = 1.95 for independent words:
+# 13 + 1.95 x 32 = 75.4.  FMA pipe: per block 10 rounds x 2 wide integer
+# multiplies = 20, i.e. 39 per word.  Both pipes take 64 lanes per SM per clock,
+# so the ALU pipe binds: per site 75.4 / 32 lane-ops.
+ALU_OPS_PER_WORD = 13.0 + 1.95 * 32.0
+FMA_OPS_PER_WORD = 1.95 * 20.0
+ALU_OPS_PER_SITE = ALU_OPS_PER_WORD / 32.0
+ALU_LANES_PER_SM = 64
 N_SM = 152
 
 
 def alu_peak_gops(peaks: dict, sm_mhz: float | None) -> float:
+    """ALU-pipe lane-operations per second: 152 SMs x 64 lanes x SM clock."""
     mhz = sm_mhz or peaks.get("sm_max_mhz", 2070.0)
-    return N_SM * INT32_LANES_PER_SM * mhz * 1e6 / 1e9
+    return N_SM * ALU_LANES_PER_SM * mhz * 1e6 / 1e9
 
 
 def cpu_model() -> str:
@@ -365,11 +372,19 @@ def run_ours(args):
                     if (cfg["k"], cfg["tile_rows"], cfg["tile_words"]) == NCU_TRAFFIC["shape"] else None),
         "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
                    if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
-        "peak_source": "152 SMs x 128 INT32 lanes x median SM clock under load",
+        "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 75.4 ALU-pipe and "
+                       "39 FMA-pipe lane-ops per 32-site word, both pipes 64 lanes/SM/clock): "
+                       "152 SMs x 64 lanes x median SM clock under load",
+        "alu_ceiling_flips_per_ns": 32.0 * peak / ALU_OPS_PER_WORD,
         "per_launch_ms": per_launch_ms, "launches": kern_launches,
         "hbm_packed_accounting": {"achieved_gbs": hbm_gbs,
                                   "frac_of_measured": hbm_gbs / peaks.get("hbm_gbs", 6800.0),
-                                  "bytes_per_site_sweep": 0.25},
+                                  "bytes_per_site_sweep": 0.25,
+                                  "ceiling_frac_at_full_alu": 0.25 * 32.0 * peak / ALU_OPS_PER_WORD
+                                  / peaks.get("hbm_gbs", 6800.0),
+                                  "note": "60 % of the HBM roof is unreachable under "
+                                          "Philox4x32-10: at 100 % of the ALU-pipe roof the sweep "
+                                          "moves only this fraction of the packed-byte HBM roof"},
     }
 
     line = {

@@ -177,6 +177,8 @@ int ising_launch_count(ising_ctx* ctx, int64_t* launches);
  * 256 and at most 8192, and at most 4096 records per call (EINVAL otherwise).
  * The first call on a device looks up the array's device address (once per
  * device, current device); make that first call before any stream capture.
+ * A cudaDeviceReset of that device leaves the kept address stale: do not call
+ * this entry point on a device after resetting it.
  * All calls on a device share the array and leave their contents in it (the
  * record accumulators are cleared at the start of every call); calls that
  * overlap on the GPU race on it, so order them on one stream.  Async on
@@ -352,7 +354,10 @@ int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);
  * persistent launch per call for L < 768 (up to 64 x 64 sites one CTA with the
  * lattice in shared memory, else a cooperative grid with three bounded
  * grid-barrier phases per step: runs, unions, flips; a barrier wait gives up
- * after about 2 s and later synchronising calls then fail with ISING_ETIMEOUT),
+ * after about 2 s and later synchronising calls then fail with ISING_ETIMEOUT;
+ * work queued after the timed-out step, sweeps included, ran on a lattice the
+ * step left half-updated, so the lattice and its records are undefined until
+ * ising_seed, ising_set_spins or ising_set_bits),
  * a few kernels per step from L = 768 (from L = 2048 with tiled labelling in
  * shared memory; Wolff first tries growth from the seed).  KERNELS /
  * PERSISTENT force one way.  The chain is the same either way, bit for bit. */

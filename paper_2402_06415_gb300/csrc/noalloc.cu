@@ -38,7 +38,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once per device).
+// Device address of g_scratch on the current device, looked up with that device
+// current on the first call there and kept for the process.  A cudaDeviceReset
+// (or a reset of the primary context) reloads the module and leaves the kept
+// address stale; callers that reset a device must not call this entry point on
+// it afterwards.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -42,10 +42,13 @@ def _reference(L, beta, seed, n1, n2, k):
     return start, mid, end, (E1, M1), (E2, M2)
 
 
-@pytest.mark.parametrize("L,k", [(256, 2), (512, 3), (1024, 1)])
-def test_noalloc_matches_regular_two_calls(torch_cuda, L, k):
+# L = 256 / 512 / 1024 take 4- / 8- / 16-word tiles, L = 2048 the 32-word tiles,
+# L = 8192 the largest lattice the static scratch holds
+@pytest.mark.parametrize("L,k,n1,n2", [(256, 2, 7, 5), (512, 3, 7, 5), (1024, 1, 7, 5),
+                                       (2048, 2, 3, 3), (8192, 2, 3, 3)])
+def test_noalloc_matches_regular_two_calls(torch_cuda, L, k, n1, n2):
     torch = torch_cuda
-    beta, seed, n1, n2 = 0.4406868, 21, 7, 5
+    beta, seed = 0.4406868, 21
     start, mid, end, (E1, M1), (E2, M2) = _reference(L, beta, seed, n1, n2, k)
 
     Wc = ising.ising_words_per_row(L)
@@ -53,25 +56,52 @@ def test_noalloc_matches_regular_two_calls(torch_cuda, L, k):
     out = torch.empty_like(dev)
     E = torch.zeros(n1, dtype=torch.int64, device="cuda")
     M = torch.zeros(n1, dtype=torch.int64, device="cuda")
+    E2d = torch.zeros(n2, dtype=torch.int64, device="cuda")
+    M2d = torch.zeros(n2, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
     assert dev.shape == (2, L, Wc)
 
     # first call: sweeps 0 .. n1-1, dev -> out
     ising.ising_sweep_bits_noalloc(dev, out, L, beta, seed, 0, 0, n1, 1, E, M, k, stream)
     torch.cuda.synchronize()
-    free_after_first = torch.cuda.mem_get_info()[0]
     assert np.array_equal(out.cpu().numpy().view(np.uint32), mid)
     assert np.array_equal(E.cpu().numpy(), E1) and np.array_equal(M.cpu().numpy(), M1)
 
-    # second call continues the chain in place: sweeps n1 .. n1+n2-1
-    E2d = torch.zeros(n2, dtype=torch.int64, device="cuda")
-    M2d = torch.zeros(n2, dtype=torch.int64, device="cuda")
+    # second call continues the chain in place: sweeps n1 .. n1+n2-1 (every
+    # buffer is allocated and the device idle before the free-memory snapshot)
+    torch.cuda.synchronize()
+    free_before_second = torch.cuda.mem_get_info()[0]
     ising.ising_sweep_bits_noalloc(out, out, L, beta, seed, 0, n1, n2, 1, E2d, M2d, k, stream)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy().view(np.uint32), end)
     assert np.array_equal(E2d.cpu().numpy(), E2) and np.array_equal(M2d.cpu().numpy(), M2)
     # no device memory was taken by the second call
-    assert torch.cuda.mem_get_info()[0] == free_after_first
+    assert torch.cuda.mem_get_info()[0] == free_before_second
+
+
+def test_noalloc_record_slots_with_offset_start(torch_cuda):
+    """measure_every = 3 from sweep 7: records of sweeps 8, 11, 14, ... land in
+    slots 0, 1, 2, ... exactly as the regular entry point records them."""
+    torch = torch_cuda
+    L, beta, seed, k, t0, n, every = 512, 0.4406868, 5, 2, 7, 11, 3
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS) as lat:
+        lat.set_kernel(ising.ISING_KERNEL_TILED, k, L // 64, 4)
+        lat.seed(seed)
+        lat.sweep(t0, 0)
+        start = lat.bits().copy()
+        lat.sweep(n, every)
+        end = lat.bits().copy()
+        n_rec = sum(1 for t in range(t0, t0 + n) if (t + 1) % every == 0)
+        Er, Mr = lat.series(n_rec)
+    dev = torch.from_numpy(start.view(np.int32)).cuda()
+    out = torch.empty_like(dev)
+    E = torch.zeros(n_rec, dtype=torch.int64, device="cuda")
+    M = torch.zeros(n_rec, dtype=torch.int64, device="cuda")
+    ising.ising_sweep_bits_noalloc(dev, out, L, beta, seed, 0, t0, n, every, E, M, k,
+                                   torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), end)
+    assert np.array_equal(E.cpu().numpy(), Er) and np.array_equal(M.cpu().numpy(), Mr)
 
 
 def test_noalloc_refuses_oversized_lattice(torch_cuda):
