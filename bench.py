@@ -144,12 +144,13 @@ NCU_TRAFFIC = {"shape": (2, 228, 64), "bytes_per_launch": 33.70e6 + 0.66e6}
 # Algorithmic work of the bit-sliced, lazily evaluated acceptance test per
 # 32-site word, by the pipe it issues to.  ALU pipe (three-input logic, shifts):
 # neighbour classes + funnel shift + update 13; per Philox4x32-10 block
-# 10 rounds x 2 three-input XORs = 20, plus 4 planes x 3 logic ops (threshold
-# bit, accept, still undecided) = 12; E[blocks] = 1.95 for independent words:
-# 13 + 1.95 x 32 = 75.4.  FMA pipe: per block 10 rounds x 2 wide integer
-# multiplies = 20, i.e. 39 per word.  Both pipes take 64 lanes per SM per clock,
-# so the ALU pipe binds: per site 75.4 / 32 lane-ops.
-ALU_OPS_PER_WORD = 13.0 + 1.95 * 32.0
+# 10 rounds x 2 three-input XORs = 20, plus 4 planes x 4 logic ops (threshold
+# bit 1, accept 2 -- four inputs: acc | (D & t & ~p) --, still undecided 1) = 16;
+# E[blocks] = 1.95 for independent words: 13 + 1.95 x 36 = 83.2.  FMA pipe: per
+# block 10 rounds x 2 wide integer multiplies = 20, i.e. 39 per word.  Both pipes
+# take 64 lanes per SM per clock, so the ALU pipe binds: per site 83.2 / 32
+# lane-ops.
+ALU_OPS_PER_WORD = 13.0 + 1.95 * 36.0
 FMA_OPS_PER_WORD = 1.95 * 20.0
 ALU_OPS_PER_SITE = ALU_OPS_PER_WORD / 32.0
 ALU_LANES_PER_SM = 64
@@ -372,7 +373,7 @@ def run_ours(args):
                     if (cfg["k"], cfg["tile_rows"], cfg["tile_words"]) == NCU_TRAFFIC["shape"] else None),
         "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
                    if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
-        "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 75.4 ALU-pipe and "
+        "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 83.2 ALU-pipe and "
                        "39 FMA-pipe lane-ops per 32-site word, both pipes 64 lanes/SM/clock): "
                        "152 SMs x 64 lanes x median SM clock under load",
         "alu_ceiling_flips_per_ns": 32.0 * peak / ALU_OPS_PER_WORD,
