@@ -95,10 +95,43 @@ __device__ bool grid_barrier(const BatchDev& d) {
   return *((volatile int*)&d.ctr->status) == 0;
 }
 
+constexpr int kQueueCap = 512;  // undecided words per half sweep finished by whole warps
+
+// Bit-plane compare of Philox blocks B0 .. B1-1 for the undecided lanes D of one
+// word, with the replica's per-plane threshold masks tm[k] = (all ones iff bit
+// 31 - k of t4, the same for t8) read from shared memory; cls marks the lanes
+// that test against t4.  VOTE: stop once no lane of the warp is undecided
+// (every lane of the warp must call it); without it every block is drawn.
+template <int B0, int B1, bool VOTE>
+__device__ __forceinline__ void planes_tab(uint32_t g, uint32_t t, uint32_t rep, uint32_t colour,
+                                           const uint32_t (&rk0)[10], const uint32_t (&rk1)[10],
+                                           const uint2* __restrict__ tm, uint32_t& D, uint32_t cls,
+                                           uint32_t& acc) {
+#pragma unroll
+  for (int b = B0; b < B1; ++b) {
+    if (VOTE && !__any_sync(0xffffffffu, D != 0u)) break;
+    const uint4 r = philox10_rk(make_uint4(g, t, rep, ctr_w(kTagMet, colour, b)), rk0, rk1);
+    const uint32_t p[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint2 m = tm[4 * b + q];
+      const uint32_t tk = (cls & m.x) | (~cls & m.y);  // lane's threshold bit
+      acc |= D & tk & ~p[q];
+      D &= ~(tk ^ p[q]);
+    }
+  }
+}
+
 // One round (ns sweeps from global sweep t0) of one item, in shared memory.
+struct ItemSmem {
+  uint2 tm[kMaxRepPerItem][32];  // per replica and plane: threshold masks (t4, t8)
+  uint32_t q_idx[kQueueCap], q_d[kQueueCap], q_cls[kQueueCap];
+  int q_n[2];
+};
+
 __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool record,
                          uint32_t step, uint32_t* sm, uint32_t* s_t4, uint32_t* s_t8,
-                         unsigned int* s_anti, unsigned int* s_ones) {
+                         unsigned int* s_anti, unsigned int* s_ones, ItemSmem& X) {
   const int l = d.item_ladder[item], i0 = d.item_i0[item], nr = d.item_nr[item];
   const int L = d.lad_L[l];
   const int Wc = (L / 2 + 31) / 32, n = L / 2;
@@ -115,16 +148,27 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
     s_anti[qq] = 0u;
     s_ones[qq] = 0u;
   }
+  if (threadIdx.x < 2) X.q_n[threadIdx.x] = 0;
   __syncthreads();
-  // Sweeps: the CTA's threads cover the item's words of one colour, then a CTA
-  // barrier.  (Warp-owned replicas with only __syncwarp() between half sweeps
-  // measured slower: too few resident warps per SM for this many replicas.)
+  for (int e = threadIdx.x; e < nr * 32; e += blockDim.x) {
+    const int qq = e >> 5, k = e & 31;
+    X.tm[qq][k] = make_uint2(0u - ((s_t4[qq] >> (31 - k)) & 1u), 0u - ((s_t8[qq] >> (31 - k)) & 1u));
+  }
+  __syncthreads();
+  // Half sweeps in two phases, as in the single-lattice tiled kernel: phase 1
+  // draws the first two Philox blocks (8 planes) of every word and queues the
+  // words with lanes still undecided (~7 %); phase 2 finishes the queued words
+  // with every lane of a warp on one of them, instead of each warp waiting for
+  // its slowest word.  (Warp-owned replicas with only __syncwarp() between half
+  // sweeps measured slower: too few resident warps per SM for this many
+  // replicas.)
   const int lane = threadIdx.x & 31;
   const int words = nr * plane;
   const FastDiv fplane = make_fastdiv((uint32_t)plane), fwc = make_fastdiv((uint32_t)Wc);
   for (int s = 0; s < ns; ++s) {
     const uint32_t t = t0 + (uint32_t)s;
     for (int c = 0; c < 2; ++c) {
+      const int cur = c;  // queue counter of this half sweep (the other is reset meanwhile)
       for (int b0 = threadIdx.x & ~31; b0 < words; b0 += blockDim.x) {
         const int idx = b0 + lane;
         const bool active = idx < words;
@@ -141,9 +185,42 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
         const uint32_t side = side_word([rm](int ww) { return rm[ww]; }, w, Wc, n, (y + c) & 1);
         const uint32_t valid = active ? valid_mask(w, Wc, n) : 0u;
         const Classes k = classify(sv, up, dn, mid, side);
-        const uint32_t f = flip_mask_rk(k, valid, (uint32_t)(y * Wc + w), t, (uint32_t)(r0 + qq),
-                                        (uint32_t)c, d.rk0, d.rk1, s_t4[qq], s_t8[qq]);
-        if (active) So[y * Wc + w] = sv ^ f;
+        uint32_t D = (k.one | k.zero) & valid, acc = 0;
+        const uint32_t g = (uint32_t)(y * Wc + w), rep = (uint32_t)(r0 + qq);
+        planes_tab<0, 2, false>(g, t, rep, (uint32_t)c, d.rk0, d.rk1, X.tm[qq], D, k.one, acc);
+        if (active) So[y * Wc + w] = sv ^ ((k.ge2 & valid) | acc);
+        bool ovf = false;
+        if (D != 0u) {  // D != 0 only for active words
+          const int slot = atomicAdd(&X.q_n[cur], 1);
+          if (slot < kQueueCap) {
+            X.q_idx[slot] = (uint32_t)idx;
+            X.q_d[slot] = D;
+            X.q_cls[slot] = k.one;
+          } else {
+            ovf = true;
+          }
+        }
+        if (__any_sync(0xffffffffu, ovf)) {  // queue full: finish in place
+          uint32_t e = ovf ? D : 0u, acc2 = 0;
+          planes_tab<2, 8, true>(g, t, rep, (uint32_t)c, d.rk0, d.rk1, X.tm[qq], e, k.one, acc2);
+          if (ovf) So[y * Wc + w] ^= acc2;
+        }
+      }
+      __syncthreads();
+      const int nq = min(X.q_n[cur], kQueueCap);
+      if (threadIdx.x == 0) X.q_n[cur ^ 1] = 0;
+      for (int b0 = threadIdx.x & ~31; b0 < nq; b0 += blockDim.x) {
+        const int e = b0 + lane;
+        const bool act = e < nq;
+        const int idx = act ? (int)X.q_idx[e] : 0;
+        uint32_t D = act ? X.q_d[e] : 0u, acc = 0;
+        const uint32_t cls = act ? X.q_cls[e] : 0u;
+        const int qq = (int)fdiv((uint32_t)idx, fplane);
+        const int rem = idx - qq * plane;
+        const int y = (int)fdiv((uint32_t)rem, fwc), w = rem - y * Wc;
+        planes_tab<2, 8, true>((uint32_t)(y * Wc + w), t, (uint32_t)(r0 + qq), (uint32_t)c, d.rk0, d.rk1,
+                               X.tm[qq], D, cls, acc);
+        if (act && acc) sm[qq * per_rep + c * plane + y * Wc + w] ^= acc;
       }
       __syncthreads();
     }
@@ -237,6 +314,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev d, int n_sweeps) {
   extern __shared__ uint32_t sm[];
   __shared__ uint32_t s_t4[kMaxRepPerItem], s_t8[kMaxRepPerItem];
   __shared__ unsigned int s_anti[kMaxRepPerItem], s_ones[kMaxRepPerItem];
+  __shared__ ItemSmem X;
   if (*((volatile int*)&d.ctr->status) != 0) return;
   const uint32_t sweep0 = *((volatile unsigned int*)&d.ctr->sweep);
   const int j0 = d.cta_first[blockIdx.x], j1 = d.cta_first[blockIdx.x + 1];
@@ -248,7 +326,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev d, int n_sweeps) {
     const bool at_pt = ns == to_pt;
     const uint32_t step = (tg + (uint32_t)ns) / (uint32_t)d.pt_every - 1u;
     for (int j = j0; j < j1; ++j)
-      run_item(d, d.cta_items[j], tg, ns, at_pt, step, sm, s_t4, s_t8, s_anti, s_ones);
+      run_item(d, d.cta_items[j], tg, ns, at_pt, step, sm, s_t4, s_t8, s_anti, s_ones, X);
     done += ns;
     if (!grid_barrier(d)) return;
     if (at_pt) {
