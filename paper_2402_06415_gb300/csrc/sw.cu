@@ -281,49 +281,63 @@ __global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __res
   }
 }
 
-// After the edge unions: every local root (mark 2) finds its final root and
-// stores it (its own entry only); a final root draws its cluster's coin into
-// mark[] (0 / 1).  Then parent[parent[i]] is every site's final root.
+// After the edge unions: every local root (mark 2) finds its final root; a
+// non-final one stores it (its own entry only), a final root draws its
+// cluster's coin into mark[] (0 / 1) and leaves its entry alone.
 __global__ void k_sw_resolve(uint32_t* __restrict__ parent, uint8_t* __restrict__ mark, long long N,
                              uint32_t step, RngParams rng) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     if (mark[i] != 2) continue;
     const uint32_t m = find_root_ro(parent, (uint32_t)i);
-    parent[i] = m;
     if (m == (uint32_t)i) {
       const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
       const uint32_t w = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
       mark[i] = (uint8_t)(w >> 31);
+    } else {
+      parent[i] = m;
     }
   }
 }
 
-// One warp per packed word, one lane per site: each lane gathers its site's
-// final root (parent[parent[site]] after k_sw_resolve) and that root's coin;
-// a ballot assembles the flip mask (independent gathers in flight per lane).
+// Every non-final local root (still mark 2) takes the coin of its final root
+// (its parent entry after k_sw_resolve, whose mark is 0 / 1).  Afterwards
+// mark[parent[site]] is every site's coin: a site's entry points at a local
+// root (the tile pass sets it; unions link only roots, and path halving moves
+// it to another local root), and every local root now holds its cluster's coin.
+__global__ void k_sw_coin_copy(const uint32_t* __restrict__ parent, uint8_t* __restrict__ mark,
+                               long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (mark[i] == 2) mark[i] = mark[parent[i]];
+  }
+}
+
+// One warp per 64 consecutive sites of a row (both colours): lane l reads the
+// parent entries of sites 64 w + 2 l and 64 w + 2 l + 1 with one 8-byte load
+// (each entry a local root), gathers their coins, and two ballots assemble the
+// flip masks of packed word w of the two colour planes (site x of row y is bit
+// (x >> 1) & 31 of word x >> 6 of colour (x + y) & 1).  The parent array is read
+// once, contiguously.  Needs L % 64 == 0 (the tiled path's lattices).
 __global__ void __launch_bounds__(256) k_sw_apply2(uint32_t* __restrict__ planes, int L, int Wc,
                                                    const uint32_t* __restrict__ parent,
-                                                   const uint8_t* __restrict__ coin, FastDiv fplane,
-                                                   FastDiv fwc) {
-  const int n = L / 2;
-  const uint32_t words = 2u * (uint32_t)L * (uint32_t)Wc;
+                                                   const uint8_t* __restrict__ coin) {
   const int lane = threadIdx.x & 31;
+  const uint32_t segs = (uint32_t)L * (uint32_t)Wc;  // 64-site row segments
   const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t i = warp0; i < words; i += nwarps) {
-    const int c = (int)fdiv(i, fplane);
-    const uint32_t rem = i - (uint32_t)c * fplane.d;
-    const int y = (int)fdiv(rem, fwc), w = (int)(rem - (uint32_t)y * (uint32_t)Wc);
-    const int j = 32 * w + lane;
-    bool f = false;
-    if (j < n) {
-      const int x = 2 * j + ((y + c) & 1);
-      const uint32_t m = __ldg(&parent[__ldg(&parent[(size_t)y * L + x])]);
-      f = __ldg(&coin[m]) != 0;
+  for (uint32_t i = warp0; i < segs; i += nwarps) {
+    const uint32_t y = i / (uint32_t)Wc, w = i - y * (uint32_t)Wc;
+    const uint2 pr = __ldg(reinterpret_cast<const uint2*>(parent + (size_t)y * L + 64 * w + 2 * lane));
+    const bool f0 = __ldg(&coin[pr.x]) != 0;  // x even: colour y & 1
+    const bool f1 = __ldg(&coin[pr.y]) != 0;  // x odd: the other colour
+    const uint32_t m0 = __ballot_sync(0xffffffffu, f0);
+    const uint32_t m1 = __ballot_sync(0xffffffffu, f1);
+    if (lane == 0) {
+      const uint32_t c0 = y & 1u;
+      if (m0) planes[(size_t)c0 * L * Wc + (size_t)y * Wc + w] ^= m0;
+      if (m1) planes[(size_t)(c0 ^ 1u) * L * Wc + (size_t)y * Wc + w] ^= m1;
     }
-    const uint32_t mask = __ballot_sync(0xffffffffu, f);
-    if (lane == 0 && mask) planes[i] ^= mask;
   }
 }
 
@@ -410,9 +424,11 @@ cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
     k_sw_resolve<<<grid_of(N), 256, 0, s>>>(parent, flip, N, step, rng);
     e = cudaGetLastError();
     if (e) return e;
-    k_sw_apply2<<<grid_of(2LL * lat.L * lat.Wc * 32), 256, 0, s>>>(
-        lat.planes, lat.L, lat.Wc, parent, flip, make_fastdiv((uint32_t)lat.L * (uint32_t)lat.Wc),
-        make_fastdiv((uint32_t)lat.Wc));
+    k_sw_coin_copy<<<grid_of(N), 256, 0, s>>>(parent, flip, N);
+    e = cudaGetLastError();
+    if (e) return e;
+    k_sw_apply2<<<grid_of((long long)lat.L * lat.Wc * 32), 256, 0, s>>>(lat.planes, lat.L, lat.Wc,
+                                                                        parent, flip);
     return cudaGetLastError();
   }
   k_sw_roots<<<grid_of(N), 256, 0, s>>>(parent, N, step, rng, flip);
