@@ -262,6 +262,8 @@ int ising_batch_block_pass(ising_batch* b, int n_passes, int block);
 int ising_batch_block_stats(ising_batch* b, int64_t* proposed, int64_t* accepted);
 /* Proposal family of the batch's block passes (as ising_set_proposal). */
 int ising_batch_set_proposal(ising_batch* b, int kind);
+/* Layer-2 engine of the batch's staged block passes (as ising_set_nn_engine). */
+int ising_batch_set_nn_engine(ising_batch* b, int engine);
 
 /* Failure-path self test (no counterpart in the paper): launches one kernel
  * that waits, with the same bounded spin as the batch grid barrier, on a device
@@ -319,6 +321,21 @@ int ising_nn_load(ising_ctx* ctx, const void* bf16_weights, size_t bytes);
  * Applies to later ising_block_pass / ising_sweep_blocks calls. */
 enum { ISING_PROPOSAL_ONESHOT = 0, ISING_PROPOSAL_STAGED = 1 };
 int ising_set_proposal(ising_ctx* ctx, int kind);
+
+/* Engine of the STAGED proposal's second convolution (32 -> 32 channels, the
+ * contraction that dominates its cost); results agree to FP32 rounding order.
+ * MMA_SYNC (default): warp-level mma.sync m16n8k16, FP16 operands, FP32
+ * accumulators in registers, on exactly the frame positions the stage needs.
+ * TCGEN05: tcgen05.mma with M = 128 frame positions x N = 32 channels, FP16
+ * operands staged in shared memory, FP32 accumulators in tensor memory (64 of
+ * its columns per tile, at most 3 tiles), issued by one thread and completed
+ * through an mbarrier whose wait is bounded (about 1 s of SM clock): on a time
+ * out the square is rejected and ising_block_stats returns ISING_ETIMEOUT.
+ * On the 18 x 18 frames of 16 x 16 squares the tile granularity costs more
+ * than the tensor pipe saves (the default is the faster engine there).
+ * ISING_EINVAL for other values.  Applies to later block passes. */
+enum { ISING_NN_ENGINE_MMA_SYNC = 0, ISING_NN_ENGINE_TCGEN05 = 1 };
+int ising_set_nn_engine(ising_ctx* ctx, int engine);
 
 /* The stage schedule of a proposal for squares of side block (2..16, even):
  * stage_of_site[block * block] (row-major interior index -> stage) and
@@ -421,6 +438,9 @@ int ising_nn_apply_grads(ising_nn* nn, const float* host_grads, int count, float
  * loss terms at the stage's sites; loss = their sum / number of windows
  * (minus the mean log-likelihood of the network stages). */
 int ising_nn_set_proposal(ising_nn* nn, int kind);
+/* Layer-2 engine of ising_nn_stage_logits / ising_nn_log_q (as
+ * ising_set_nn_engine; training keeps its own FP32 path). */
+int ising_nn_set_engine(ising_nn* nn, int engine);
 /* Logits of stage `stage` of the trainer's proposal for count windows on the
  * device (BF16 inference path): network stages give the CNN logits, exact
  * stages the exact log-odds at beta, at the stage's sites; other sites 0.

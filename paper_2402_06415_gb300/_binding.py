@@ -30,6 +30,8 @@ ISING_CLUSTER_PERSISTENT = 2
 
 ISING_PROPOSAL_ONESHOT = 0
 ISING_PROPOSAL_STAGED = 1
+ISING_NN_ENGINE_MMA_SYNC = 0
+ISING_NN_ENGINE_TCGEN05 = 1
 
 ISING_KERNEL_AUTO = 0
 ISING_KERNEL_HALF = 1
@@ -121,6 +123,9 @@ _PROTOS = [
     ("ising_set_proposal", _i, [_p, _i]),
     ("ising_batch_set_proposal", _i, [_p, _i]),
     ("ising_nn_set_proposal", _i, [_p, _i]),
+    ("ising_set_nn_engine", _i, [_p, _i]),
+    ("ising_batch_set_nn_engine", _i, [_p, _i]),
+    ("ising_nn_set_engine", _i, [_p, _i]),
     ("ising_proposal_schedule", _i, [_i, _i, _p, _p, _i, ctypes.POINTER(_i)]),
     ("ising_nn_stage_logits", _i, [_p, _p, _i, _i, ctypes.c_double, _p]),
     ("ising_nn_log_q", _i, [_p, _p, _i, ctypes.c_double, _p]),
@@ -721,6 +726,18 @@ def ising_batch_set_proposal(b: int, kind: int) -> None:
 
 def ising_nn_set_proposal(nn: int, kind: int) -> None:
     _check(lib().ising_nn_set_proposal(nn, int(kind)))
+
+
+def ising_set_nn_engine(ctx: int, engine: int) -> None:
+    _check(lib().ising_set_nn_engine(ctx, int(engine)))
+
+
+def ising_batch_set_nn_engine(b: int, engine: int) -> None:
+    _check(lib().ising_batch_set_nn_engine(b, int(engine)))
+
+
+def ising_nn_set_engine(nn: int, engine: int) -> None:
+    _check(lib().ising_nn_set_engine(nn, int(engine)))
 
 
 def ising_proposal_schedule(block: int, kind: int = ISING_PROPOSAL_STAGED):

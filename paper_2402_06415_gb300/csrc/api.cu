@@ -87,9 +87,10 @@ struct ising_ctx {
   int kernel = ISING_KERNEL_HALF, k = 1, tile_rows = 1, tile_words = 4, grid = 0, block = 0;
   __nv_bfloat16* nn_w = nullptr;    // BF16 weights of the block proposal
   __nv_bfloat16* nn_w2t = nullptr;
-  unsigned long long* blk_stats = nullptr;  // [2] proposed, accepted
+  unsigned long long* blk_stats = nullptr;  // [3] proposed, accepted, device wait time-outs
   int64_t block_passes = 0;
   int proposal = 0;                  // ISING_PROPOSAL_ONESHOT / _STAGED
+  int nn_engine = 0;                 // ISING_NN_ENGINE_MMA_SYNC / _TCGEN05 (staged proposal)
   nnc::StagedPlan* plan = nullptr;   // device plan of the staged proposal
   int plan_B = 0;                    // block size the plan was built for
   uint32_t* sw_parent = nullptr;  // Swendsen-Wang scratch
@@ -790,8 +791,8 @@ int ising_nn_load(ising_ctx* c, const void* bf16_weights, size_t bytes) {
     return fail(ISING_EINVAL, "weights blob must be %zu bytes of bf16", nn_blob_bytes());
   if (!c->nn_w) {
     cudaError_t e = nn_alloc_weights(&c->nn_w, &c->nn_w2t);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->blk_stats, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(c->blk_stats, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->blk_stats, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->blk_stats, 0, 3 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(ISING_ENOMEM, "block-proposal weights: %s", cudaGetErrorString(e));
@@ -821,8 +822,8 @@ int ising_block_pass(ising_ctx* c, int n_passes, int block) {
       cudaError_t e =
           c->proposal == ISING_PROPOSAL_STAGED
               ? nn_staged_block_pass(c->bits[c->cur], c->L, c->Wc, c->plan, block,
-                                     (uint32_t)c->block_passes, col, rng, c->beta, c->nn_w, c->nn_w2t,
-                                     c->blk_stats, c->stream)
+                                     (uint32_t)c->block_passes, col, rng, c->beta, c->nn_engine, c->nn_w,
+                                     c->nn_w2t, c->blk_stats, c->stream)
               : nn_block_pass(c->bits[c->cur], c->L, c->Wc, block, (uint32_t)c->block_passes, col, rng,
                               c->beta, c->nn_w, c->nn_w2t, c->blk_stats, c->stream);
       if (int st = launch_result(c, e, "block pass")) return st;
@@ -837,6 +838,14 @@ int ising_set_proposal(ising_ctx* c, int kind) {
   if (kind != ISING_PROPOSAL_ONESHOT && kind != ISING_PROPOSAL_STAGED)
     return fail(ISING_EINVAL, "proposal kind must be ISING_PROPOSAL_ONESHOT or ISING_PROPOSAL_STAGED");
   c->proposal = kind;
+  return ok();
+}
+
+int ising_set_nn_engine(ising_ctx* c, int engine) {
+  if (int st = check_ctx(c)) return st;
+  if (engine != ISING_NN_ENGINE_MMA_SYNC && engine != ISING_NN_ENGINE_TCGEN05)
+    return fail(ISING_EINVAL, "engine must be ISING_NN_ENGINE_MMA_SYNC or ISING_NN_ENGINE_TCGEN05");
+  c->nn_engine = engine;
   return ok();
 }
 
@@ -1015,11 +1024,12 @@ int ising_sw_step(ising_ctx* c, int n_steps, int measure_every) {
 
 int ising_block_stats(ising_ctx* c, int64_t* proposed, int64_t* accepted) {
   if (int st = check_ctx(c)) return st;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   if (c->blk_stats)
     if (int st = to_host_sync(c, h, c->blk_stats, sizeof(h))) return st;
   if (proposed) *proposed = (int64_t)h[0];
   if (accepted) *accepted = (int64_t)h[1];
+  if (h[2]) return fail(ISING_ETIMEOUT, "a block pass gave up waiting for its tensor-core work");
   return ok();
 }
 

@@ -405,6 +405,7 @@ struct ising_batch {
   unsigned long long* d_blk_stats = nullptr;
   int64_t block_passes = 0;
   int proposal = 0;                  // ISING_PROPOSAL_ONESHOT / _STAGED
+  int nn_engine = 0;                 // ISING_NN_ENGINE_MMA_SYNC / _TCGEN05 (staged proposal)
   nnc::StagedPlan* plan = nullptr;   // device plan of the staged proposal
   int plan_B = 0;
   // captured graph
@@ -874,8 +875,8 @@ int ising_batch_nn_load(ising_batch* b, const void* bf16_weights, size_t bytes) 
   if (!b->nn_w) {
     cudaError_t e = nn_alloc_weights(&b->nn_w, &b->nn_w2t);
     if (!e) e = cudaMalloc((void**)&b->d_beta_slot, (size_t)b->n_beta * sizeof(float));
-    if (!e) e = cudaMalloc((void**)&b->d_blk_stats, 2 * sizeof(unsigned long long));
-    if (!e) e = cudaMemset(b->d_blk_stats, 0, 2 * sizeof(unsigned long long));
+    if (!e) e = cudaMalloc((void**)&b->d_blk_stats, 3 * sizeof(unsigned long long));
+    if (!e) e = cudaMemset(b->d_blk_stats, 0, 3 * sizeof(unsigned long long));
     if (!e) {
       std::vector<float> bf(b->betas.begin(), b->betas.end());
       e = cudaMemcpy(b->d_beta_slot, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice);
@@ -923,8 +924,8 @@ int ising_batch_block_pass(ising_batch* b, int n_passes, int block) {
       if (b->proposal == ISING_PROPOSAL_STAGED)
         BTRY(nn_batch_staged_block_pass(b->spins, b->d_off, b->d_L, b->d_slot, b->d_beta_slot,
                                         b->d_unit0, b->unit_total, b->n_rep, b->n_beta, b->plan, col,
-                                        (uint32_t)b->block_passes, rng, b->nn_w, b->nn_w2t,
-                                        b->d_blk_stats, b->stream));
+                                        (uint32_t)b->block_passes, rng, b->nn_engine, b->nn_w,
+                                        b->nn_w2t, b->d_blk_stats, b->stream));
       else
         BTRY(nn_batch_block_pass(b->spins, b->d_off, b->d_L, b->d_slot, b->d_beta_slot, b->d_unit0,
                                  b->unit_total, b->n_rep, b->n_beta, block, col,
@@ -946,15 +947,25 @@ int ising_batch_set_proposal(ising_batch* b, int kind) {
   return ISING_OK;
 }
 
+int ising_batch_set_nn_engine(ising_batch* b, int engine) {
+  if (int st = check_b(b)) return st;
+  if (engine != ISING_NN_ENGINE_MMA_SYNC && engine != ISING_NN_ENGINE_TCGEN05)
+    return bfail(ISING_EINVAL, "engine must be ISING_NN_ENGINE_MMA_SYNC or ISING_NN_ENGINE_TCGEN05");
+  b->nn_engine = engine;
+  set_last_error("");
+  return ISING_OK;
+}
+
 int ising_batch_block_stats(ising_batch* b, int64_t* proposed, int64_t* accepted) {
   if (int st = check_b(b)) return st;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   if (b->d_blk_stats) {
     BTRY(cudaMemcpyAsync(h, b->d_blk_stats, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
     BTRY(cudaStreamSynchronize(b->stream));
   }
   if (proposed) *proposed = (int64_t)h[0];
   if (accepted) *accepted = (int64_t)h[1];
+  if (h[2]) return bfail(ISING_ETIMEOUT, "a block pass gave up waiting for its tensor-core work");
   set_last_error("");
   return ISING_OK;
 }

@@ -153,16 +153,16 @@ cudaError_t nn_block_pass(uint32_t* planes, int L, int Wc, int B, uint32_t pass,
 // plan built by nnc::nn_upload_plan (nn_common.cuh).
 namespace nnc { struct StagedPlan; }
 cudaError_t nn_staged_block_pass(uint32_t* planes, int L, int Wc, const nnc::StagedPlan* d_plan, int B,
-                                 uint32_t pass, int colour, const RngParams& rng, double beta,
+                                 uint32_t pass, int colour, const RngParams& rng, double beta, int engine,
                                  const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
                                  unsigned long long* stats, cudaStream_t s);
 cudaError_t nn_batch_staged_block_pass(uint32_t* spins, const long long* off, const int* lad_L,
                                        const int* slot_of, const float* beta_of_slot,
                                        const long long* unit0, long long total_units, int n_rep,
                                        int n_beta, const nnc::StagedPlan* d_plan, int colour,
-                                       uint32_t pass, const RngParams& rng, const __nv_bfloat16* wbf,
-                                       const __nv_bfloat16* w2t, unsigned long long* stats,
-                                       cudaStream_t s);
+                                       uint32_t pass, const RngParams& rng, int engine,
+                                       const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
+                                       unsigned long long* stats, cudaStream_t s);
 namespace nnc {
 cudaError_t nn_upload_plan(int B, int kind, StagedPlan** d_plan, int* n_net, cudaStream_t s);
 }

@@ -866,6 +866,7 @@ using namespace ising;
 struct ising_nn {
   int B = 16;
   int kind = kProposalOneShot;
+  int engine = kEngineMmaSync;  // layer-2 engine of the staged inference entry points
   StagedPlan* plan = nullptr;  // device copy of the proposal plan
   int n_net = 1;
   cudaStream_t stream = nullptr;
@@ -1019,6 +1020,15 @@ int ising_nn_set_proposal(ising_nn* n, int kind) {
   return ISING_OK;
 }
 
+int ising_nn_set_engine(ising_nn* n, int engine) {
+  if (!n) return nfail(ISING_EINVAL, "null trainer");
+  if (engine != kEngineMmaSync && engine != kEngineTcgen05)
+    return nfail(ISING_EINVAL, "engine must be ISING_NN_ENGINE_MMA_SYNC or ISING_NN_ENGINE_TCGEN05");
+  n->engine = engine;
+  set_last_error("");
+  return ISING_OK;
+}
+
 int ising_nn_stage_logits(ising_nn* n, const int8_t* dev_windows, int count, int stage, double beta,
                           float* dev_logits) {
   if (!n || (count > 0 && (!dev_windows || !dev_logits)) || count < 0)
@@ -1028,8 +1038,8 @@ int ising_nn_stage_logits(ising_nn* n, const int8_t* dev_windows, int count, int
   if (stage < 0 || stage >= n_stages) return nfail(ISING_EINVAL, "stage %d out of range [0, %d)", stage, n_stages);
   if (!(beta >= 0.0) || !std::isfinite(beta)) return nfail(ISING_EINVAL, "beta must be finite and >= 0");
   if (count == 0) return ISING_OK;
-  NTRY(nn_stage_logits(dev_windows, count, n->plan, stage, (float)beta, n->wbf, n->w2t, dev_logits,
-                       n->stream));
+  NTRY(nn_stage_logits(dev_windows, count, n->plan, stage, (float)beta, n->engine, n->wbf, n->w2t,
+                       dev_logits, n->stream));
   set_last_error("");
   return ISING_OK;
 }
@@ -1039,7 +1049,8 @@ int ising_nn_log_q(ising_nn* n, const int8_t* dev_windows, int count, double bet
     return nfail(ISING_EINVAL, "bad arguments");
   if (!(beta >= 0.0) || !std::isfinite(beta)) return nfail(ISING_EINVAL, "beta must be finite and >= 0");
   if (count == 0) return ISING_OK;
-  NTRY(nn_log_q(dev_windows, count, n->plan, (float)beta, n->wbf, n->w2t, dev_log_q, n->stream));
+  NTRY(nn_log_q(dev_windows, count, n->plan, (float)beta, n->engine, n->wbf, n->w2t, dev_log_q,
+                n->stream));
   set_last_error("");
   return ISING_OK;
 }

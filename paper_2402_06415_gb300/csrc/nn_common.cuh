@@ -35,6 +35,10 @@ constexpr int kInferThreads = 512;  // inference / block-pass kernels
 // the schedule is built on the host by build_plan (nn_staged.cu).
 constexpr int kProposalOneShot = 0;
 constexpr int kProposalStaged = 1;
+// layer-2 engine of the staged proposal: warp-level mma.sync on the listed
+// positions (default) or tcgen05 tiles with TMEM accumulators
+constexpr int kEngineMmaSync = 0;
+constexpr int kEngineTcgen05 = 1;
 constexpr int kMaxStages = 32;
 constexpr int kMaxFrame = (kMaxB + 2) * (kMaxB + 2);
 constexpr int kMaxNetStages = 12;
@@ -132,11 +136,11 @@ cudaError_t nn_plan_stages(int B, int kind, int* n_stages);
 // -> CNN logits at the stage's sites, exact stages -> exact log-odds there;
 // other sites 0.  out [count][B*B].
 cudaError_t nn_stage_logits(const int8_t* windows, int count, const StagedPlan* d_plan, int stage,
-                            float beta, const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
+                            float beta, int engine, const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
                             float* out, cudaStream_t s);
 // Teacher-forced natural log of the quantised proposal density of each
 // window's interior given its ring.  out [count].
-cudaError_t nn_log_q(const int8_t* windows, int count, const StagedPlan* d_plan, float beta,
+cudaError_t nn_log_q(const int8_t* windows, int count, const StagedPlan* d_plan, float beta, int engine,
                      const __nv_bfloat16* wbf, const __nv_bfloat16* w2t, float* out,
                      cudaStream_t s);
 

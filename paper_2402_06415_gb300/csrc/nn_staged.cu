@@ -220,17 +220,82 @@ namespace {
 
 constexpr int kFP = kMaxB + 4;  // padded grid side (frame + zero border)
 
+// tcgen05 operand layouts (K-major, no swizzle: core matrices of 8 rows x 16
+// bytes, rows 16 bytes apart, 8-row groups 128 bytes apart).  h1 holds, per
+// window and per 8-channel chunk, every grid position (kFP-stride grid of the
+// frame and its zero border) as one 16-byte row, so the A operand of tap
+// (dy, dx) for 128 consecutive positions is the same layout shifted by
+// (dy kFP + dx) rows: no im2col copy.
+constexpr int kTcPos = 528;  // positions per chunk: tiles start at the first frame position (>= 21),
+                             // end <= 378 + 127, plus the largest tap shift 21
+constexpr int kTcChunkBytes = kTcPos * 16;
+constexpr int kTcWinBytes = (kC / 8) * kTcChunkBytes;  // 4 chunks
+constexpr int kTcTiles = 3;                            // 128-position tiles per window (B <= 16)
+constexpr int kTmemCols = 256;                         // 2 windows x 3 tiles x 32 columns, rounded up
+constexpr int kW2Bytes = (kK2 / 8) * kC * 16;          // W2 as the B operand: [k chunk][n][8]
+constexpr long long kTcWaitLimit = 2000000000LL;       // clock64 cycles an MMA wait may take (~1 s)
+// instruction descriptor of tcgen05.mma kind::f16: D F32 (bits 4-5 = 1), A and
+// B F16 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N / 8 at bit 17,
+// M / 16 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kC >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+// shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (M/N-direction) byte offsets, all >> 4; descriptor version 1 (bit 46);
+// no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      :
+      : "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// waits for phase `parity` of the mbarrier, at most kTcWaitLimit cycles
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kTcWaitLimit) return false;
+  }
+}
+
+// 32 consecutive 32-bit columns of the warp's 32 TMEM lanes (lane = row)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Two windows are evaluated side by side in every layer phase: window 0 =
 // the square's ring plus the sites drawn so far (the proposal being drawn),
 // window 1 = ring plus the current interior (teacher forcing for q(old)).
-// Layer 2 runs in FP16 (both MMA operands): the activations are rounded to
-// FP16 (11-bit significand; BF16's 8 bits would leave ~1 % logit errors), and
-// the weights are the BF16 weight values held in FP16, which represents every
-// BF16 value of magnitude 2^-14 .. 65504 exactly.
+// Layer 2 runs in FP16 on the tensor cores (both operands): the activations
+// are rounded to FP16 (11-bit significand; BF16's 8 bits left ~1 % logit
+// errors), and the weights are the BF16 weight values held in FP16, which
+// represents every BF16 value of magnitude 2^-14 .. 65504 exactly.
 struct StagedSmem {
-  __half h1[2][kFP * kFP * kCP];  // layer-1 activations (tensor-core A operand), zero border
-  float h2[2][kFP * kFP * kC];    // layer-2 activations (FP32), zero border
-  __half w2t[kC * kK2P];
+  alignas(128) unsigned char h1[2 * kTcWinBytes];  // layer-1 activations, FP16 [window][chunk][position][8]
+  alignas(128) unsigned char w2[kW2Bytes];         // W2, FP16 [k chunk][output channel][8]
+  float h2[2][kFP * kFP * kC];  // layer-2 activations (FP32) [window][position][channel chunk ^ (position & 7)][4]
   float w1[kOffB1 + kC];  // W1 then b1
   float w3[kC * 9 + 1];   // W3 then b3
   float b2[kC];
@@ -241,36 +306,77 @@ struct StagedSmem {
   float red_lq[kInferThreads / 32];
   int red_de[kInferThreads / 32];
   int accept;
+  int tc_fail;          // an MMA wait ran out of time (results of this CTA are void)
+  uint32_t tmem_base;   // TMEM address of the accumulators (written by tcgen05.alloc)
+  alignas(8) unsigned long long mbar;  // completion barrier of the MMAs
   StagedPlan plan;
 };
-static_assert(offsetof(StagedSmem, w2t) % 16 == 0 && offsetof(StagedSmem, plan) % 16 == 0,
-              "uint4 copies into shared memory");
+static_assert(offsetof(StagedSmem, plan) % 16 == 0, "uint4 copies into shared memory");
 static_assert(sizeof(StagedSmem) <= 227 * 1024, "one CTA per SM must fit");
+
+__device__ __forceinline__ __half* h1_at(StagedSmem& S, int w, int g, int c) {
+  return reinterpret_cast<__half*>(S.h1 + w * kTcWinBytes + (c >> 3) * kTcChunkBytes + g * 16 + (c & 7) * 2);
+}
 
 __device__ void load_all(StagedSmem& S, const __nv_bfloat16* __restrict__ w,
                          const __nv_bfloat16* __restrict__ w2t, const StagedPlan* __restrict__ plan) {
   for (int i = threadIdx.x; i < kOffB1 + kC; i += blockDim.x) S.w1[i] = bf(w[kOffW1 + i]);
   for (int i = threadIdx.x; i < kC * 9 + 1; i += blockDim.x) S.w3[i] = bf(w[kOffW3 + i]);
   for (int i = threadIdx.x; i < kC; i += blockDim.x) S.b2[i] = bf(w[kOffB2 + i]);
-  for (int i = threadIdx.x; i < kC * kK2P; i += blockDim.x) S.w2t[i] = __float2half_rn(bf(w2t[i]));
+  // W2 as the K-major B operand: element (k chunk, output channel n, e) holds
+  // W2[n][ci][tap] with k = 8 chunk + e = 32 tap + ci (the A operand's order)
+  __half* w2h = reinterpret_cast<__half*>(S.w2);
+  for (int i = threadIdx.x; i < kK2 * kC; i += blockDim.x) {
+    const int kch = i >> 8, n = (i >> 3) & 31, k = 8 * kch + (i & 7);
+    w2h[i] = __float2half_rn(bf(w2t[n * kK2P + (k >> 5) * kC + (k & 31)]));
+  }
   {
     const uint4* src = reinterpret_cast<const uint4*>(plan);
     uint4* dst = reinterpret_cast<uint4*>(&S.plan);
     for (int i = threadIdx.x; i < (int)(sizeof(StagedPlan) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
   }
-  // Only the one-position border of the padded grids is read without being
-  // written first (every other position a layer reads was computed in the same
-  // stage), so only the border is zeroed.
-  const int FB = __ldg(&plan->B) + 4;  // frame + border extent in the kFP-stride grids
-  const __half z = __float2half_rn(0.f);
+  // Only the one-position border of the padded grid is read without being
+  // written first (every frame position a tap of a needed output reads was
+  // computed in the same stage), so only the border is zeroed.
+  const int FB = __ldg(&plan->B) + 4;  // frame + border extent in the kFP-stride grid
   for (int t = threadIdx.x; t < 2 * 4 * FB; t += blockDim.x) {
     const int wi = t / (4 * FB), e = t - wi * 4 * FB, side = e / FB, o = e - side * FB;
     const int gy = side == 0 ? 0 : (side == 1 ? FB - 1 : o);
     const int gx = side < 2 ? o : (side == 2 ? 0 : FB - 1);
     const int g = gy * kFP + gx;
-    for (int c = 0; c < kCP; ++c) S.h1[wi][g * kCP + c] = z;
-    for (int c = 0; c < kC; ++c) S.h2[wi][g * kC + c] = 0.f;
+    for (int ch = 0; ch < kC / 8; ++ch)
+      *reinterpret_cast<uint4*>(S.h1 + wi * kTcWinBytes + ch * kTcChunkBytes + g * 16) = make_uint4(0, 0, 0, 0);
   }
+  if (threadIdx.x == 0) {
+    S.tc_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+// Tensor memory for the layer-2 accumulators: allocated by warp 0 after
+// load_all, before any MMA; every thread reads the address after the barrier.
+__device__ void tmem_setup(StagedSmem& S) {
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Frees the tensor memory (every MMA has completed and every tcgen05.ld has
+// been waited for by then).
+__device__ void tmem_teardown(StagedSmem& S) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(kTmemCols)
+                 : "memory");
 }
 
 // Layer-1 weights as per-lane mma.sync B fragments (FP16 pairs), built once
@@ -309,9 +415,10 @@ __device__ __forceinline__ uint32_t l1_tap(const int8_t* w, int p, int off, unsi
 }
 
 // Layer 1 on the tensor cores for windows 0 .. nw-1 at the listed frame
-// positions (known-tap masks from the plan): mma.sync m16n8k16 FP16 -> FP32,
-// A fragments built in registers from the spin grid; epilogue bias + ReLU,
-// FP16 into the activation grid.
+// positions (known-tap masks from the plan): mma.sync m16n8k16 FP16 -> FP32
+// (K = 18 is too small for a tcgen05 tile to pay), A fragments built in
+// registers from the spin grid; epilogue bias + ReLU, FP16 into the layer-2
+// operand layout.
 __device__ void layer1t(StagedSmem& S, const L1Frag& f, int nw, const int16_t* list,
                         const uint16_t* masks, int n) {
   const int F = S.plan.B + 2;
@@ -325,7 +432,7 @@ __device__ void layer1t(StagedSmem& S, const L1Frag& f, int nw, const int16_t* l
   const int off2 = F + 1;
   for (int mt = warp; mt < n_mt; mt += nwarps) {
     uint32_t a[2][3];  // [row g / g + 8][tap q, tap q + 4, tap 8]
-    int pos[2], wsel[2];
+    int pos[2], wsel[2];  // grid position and window of rows g and g + 8
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int r = mt * 16 + g + 8 * h;
@@ -365,28 +472,33 @@ __device__ void layer1t(StagedSmem& S, const L1Frag& f, int nw, const int16_t* l
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (pos[h] < 0) continue;
-      __half* dst = &S.h1[wsel[h]][pos[h] * kCP];
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         const int c = nt * 8 + 2 * q;
         const __half2 v = __floats2half2_rn(fmaxf(acc[nt][2 * h] + S.w1[kOffB1 + c], 0.f),
                                             fmaxf(acc[nt][2 * h + 1] + S.w1[kOffB1 + c + 1], 0.f));
-        *reinterpret_cast<__half2*>(dst + c) = v;
+        *reinterpret_cast<__half2*>(h1_at(S, wsel[h], pos[h], c)) = v;
       }
     }
   }
 }
 
-// Layer 2 on the tensor cores for windows 0 .. nw-1 at the listed frame
-// positions: implicit GEMM, M = nw x positions, N = 32 channels, K = 288
-// (tap-major, 16 channels per step), mma.sync m16n8k16 FP16 -> FP32, A rows
-// gathered by ldmatrix (one row address per lane) straight from the
-// zero-padded activation grid of the row's window.
-__device__ void layer2s(StagedSmem& S, int nw, const int16_t* list, int M) {
+// frame-row offset of 3 x 3 tap t (t = 3 dy + dx, dy, dx in 0..2)
+__device__ __forceinline__ constexpr int tap_row(int t) { return (t / 3 - 1) * kFP + (t % 3 - 1); }
+
+// Layer 2 with warp-level MMA for windows 0 .. nw-1 at the listed frame
+// positions only: implicit GEMM, M = nw x positions, N = 32 channels,
+// K = 288 (tap-major, 16 channels per step), mma.sync m16n8k16 FP16 -> FP32.
+// ldmatrix gathers the A rows (one row address per lane) and the W2 rows from
+// the same shared-memory layouts the tcgen05 path reads (every (position,
+// 8-channel chunk) and (k chunk, output channel) is one 16-byte row).
+__device__ void layer2_mma(StagedSmem& S, int nw, const int16_t* list, int M) {
   const int F = S.plan.B + 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int rows = nw * M;
   const int n_mt = (rows + 15) / 16;
+  // B rows for ldmatrix.x4: matrix m = lane / 8 is (n-tile 2 np + m / 2, k chunk + m % 2)
+  const uint32_t bbase = smem_addr(S.w2) + (uint32_t)((((lane >> 3) & 1) * kC + (lane >> 4) * 8 + (lane & 7)) * 16);
   for (int mt = warp; mt < n_mt; mt += nwarps) {
     float acc[4][4];
 #pragma unroll
@@ -397,26 +509,22 @@ __device__ void layer2s(StagedSmem& S, int nw, const int16_t* list, int M) {
     if (row >= rows) row = 0;  // padding rows: any valid row, results dropped
     const int wi = row >= M ? 1 : 0;
     const int p = list[row - wi * M];
-    const int py = p / F, px = p - (p / F) * F;
-    // this lane's A row address (tap (0, 0), first 8 channels of its half)
-    const uint32_t abase = smem_addr(S.h1[wi] + (py * kFP + px) * kCP + (lane >> 4) * 8);
-    // this lane's B row address for ldmatrix.x4: n-tiles nt, nt + 1 of W2
-    // (lanes 16..31 give the second one), k half (lane / 8) % 2
-    const uint32_t bbase = smem_addr(S.w2t + ((lane >> 4) * 8 + (lane & 7)) * kK2P + ((lane >> 3) & 1) * 8);
+    const int g = (p / F + 1) * kFP + p % F + 1;
+    // A rows: window wi, grid position g, channel chunk lane / 16 of the k step
+    const uint32_t abase = smem_addr(S.h1) + (uint32_t)(wi * kTcWinBytes + (lane >> 4) * kTcChunkBytes + g * 16);
 #pragma unroll
     for (int kc = 0; kc < 18; ++kc) {
-      const int tap = kc >> 1, ci0 = (kc & 1) * 16;
-      const int dy = tap / 3, dx = tap - (tap / 3) * 3;
+      const int tap = kc >> 1, half = kc & 1;
       uint32_t a0, a1, a2, a3;
       asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                    : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3)
-                   : "r"(abase + (uint32_t)(((dy * kFP + dx) * kCP + ci0) * 2)));
+                   : "r"(abase + (uint32_t)(2 * half * kTcChunkBytes + tap_row(tap) * 16)));
 #pragma unroll
       for (int np = 0; np < 2; ++np) {
         uint32_t b0, b1, b2, b3;
         asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                      : "=r"(b0), "=r"(b1), "=r"(b2), "=r"(b3)
-                     : "r"(bbase + (uint32_t)((np * 16 * kK2P + kc * 16) * 2)));
+                     : "r"(bbase + (uint32_t)(((4 * tap + 2 * half) * kC + 16 * np) * 16)));
         asm volatile(
             "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
             "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
@@ -430,23 +538,94 @@ __device__ void layer2s(StagedSmem& S, int nw, const int16_t* list, int M) {
             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b2), "r"(b3));
       }
     }
-    const int g = lane >> 2, t2 = (lane & 3) * 2;
+    const int gq = lane >> 2, t2 = (lane & 3) * 2;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int rr = mt * 16 + g + half * 8;
+    for (int hf = 0; hf < 2; ++hf) {
+      const int rr = mt * 16 + gq + hf * 8;
       if (rr >= rows) continue;
       const int ow = rr >= M ? 1 : 0;
       const int pp = list[rr - ow * M];
-      const int fy = pp / F, fx = pp - (pp / F) * F;
-      float* dst = &S.h2[ow][((fy + 1) * kFP + fx + 1) * kC];
+      const int pg = (pp / F + 1) * kFP + pp % F + 1;
+      float* dst = &S.h2[ow][pg * kC];
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
-        const int c = nt * 8 + t2;
-        dst[c] = fmaxf(acc[nt][half * 2 + 0] + S.b2[c], 0.f);
-        dst[c + 1] = fmaxf(acc[nt][half * 2 + 1] + S.b2[c + 1], 0.f);
+        const int c = nt * 8 + t2;  // channels c, c + 1: one 4-channel chunk (swizzled)
+        *reinterpret_cast<float2*>(dst + 4 * ((c >> 2) ^ (pg & 7)) + (c & 3)) =
+            make_float2(fmaxf(acc[nt][hf * 2 + 0] + S.b2[c], 0.f), fmaxf(acc[nt][hf * 2 + 1] + S.b2[c + 1], 0.f));
       }
     }
   }
+}
+
+// Layer 2 on the 5th-generation tensor cores for windows 0 .. nw-1: implicit
+// GEMM over the grid positions from the first to the last listed one (the
+// listed positions are the ones the stage's logits read), in tiles of
+// M = 128 positions, N = 32 channels, K = 288 in 18 steps of 16 (tap-major,
+// two 8-channel chunks per step).  One thread issues tcgen05.mma with both
+// operands in shared memory (A = the activation grid shifted by the tap, B =
+// W2) and accumulators in tensor memory, then commits to an mbarrier; after
+// the (bounded) wait every warp reads its 32 TMEM lanes of a tile with
+// tcgen05.ld and writes bias + ReLU in FP32 to h2.  Rows of the range that no
+// listed position needs are computed from stale inputs and never read.
+__device__ void layer2_tc(StagedSmem& S, int nw, const int16_t* list, int M, uint32_t& parity) {
+  const int F = S.plan.B + 2;
+  const int pf0 = list[0], pf1 = list[M - 1];
+  const int g0 = (pf0 / F + 1) * kFP + pf0 % F + 1;
+  const int g1 = (pf1 / F + 1) * kFP + pf1 % F + 1;
+  const int ntiles = (g1 - g0) / 128 + 1;
+  // the layer-1 stores of every thread become visible to the async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the start-address field is the descriptor's low 14 bits (address / 16,
+    // all shared-memory addresses < 2^18), so a descriptor for address + off
+    // is the descriptor plus off / 16: one base descriptor per operand, and
+    // compile-time offsets per tap and channel half
+    const uint64_t bdesc0 = umma_desc(smem_addr(S.w2), kC * 16, 128);
+    for (int w = 0; w < nw; ++w)
+      for (int j = 0; j < ntiles; ++j) {
+        const uint32_t d = S.tmem_base + (uint32_t)((w * kTcTiles + j) * kC);
+        const uint64_t adesc0 = umma_desc(smem_addr(S.h1) + (uint32_t)(w * kTcWinBytes) +
+                                              (uint32_t)(g0 + 128 * j) * 16u,
+                                          kTcChunkBytes, 128);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+#pragma unroll
+          for (int kc = 0; kc < 2; ++kc) {
+            const int64_t aoff = (2 * kc * kTcChunkBytes + tap_row(t) * 16) / 16;
+            const int64_t boff = ((4 * t + 2 * kc) * kC * 16) / 16;
+            umma_f16(d, adesc0 + (uint64_t)aoff, bdesc0 + (uint64_t)boff, (t | kc) != 0);
+          }
+        }
+      }
+    umma_commit(smem_addr(&S.mbar));
+  }
+  const bool ok = mbar_wait(smem_addr(&S.mbar), parity);
+  parity ^= 1u;
+  if (!ok) S.tc_fail = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3;
+  // warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of its quadrant)
+  for (int job = warp >> 2; job < nw * ntiles; job += (int)(blockDim.x >> 7)) {
+    const int w = job / ntiles, j = job - (job / ntiles) * ntiles;
+    uint32_t r[32];
+    tmem_ld32(S.tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)((w * kTcTiles + j) * kC), r);
+    const int g = g0 + 128 * j + 32 * q + lane;
+    const int gy = g / kFP, gx = g - (g / kFP) * kFP;
+    if (g <= g1 && gx >= 1 && gx <= F && gy >= 1 && gy <= F) {
+      float* dst = &S.h2[w][g * kC];
+      // 16-byte chunk c4 of the row goes to chunk c4 ^ (g & 7): the eight
+      // lanes of a store phase (consecutive rows) hit eight different chunks
+#pragma unroll
+      for (int c = 0; c < kC; c += 4)
+        *reinterpret_cast<float4*>(dst + 4 * ((c >> 2) ^ (g & 7))) =
+            make_float4(fmaxf(__uint_as_float(r[c]) + S.b2[c], 0.f), fmaxf(__uint_as_float(r[c + 1]) + S.b2[c + 1], 0.f),
+                        fmaxf(__uint_as_float(r[c + 2]) + S.b2[c + 2], 0.f),
+                        fmaxf(__uint_as_float(r[c + 3]) + S.b2[c + 3], 0.f));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
 // Layer 3 (CUDA cores) for windows 0 .. nw-1: logits at the listed interior
@@ -472,7 +651,8 @@ __device__ void layer3s(StagedSmem& S, int nw, const int16_t* list, int n) {
       for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
-          const float4 h = *reinterpret_cast<const float4*>(&h2[((fy + dy) * kFP + fx + dx) * kC + c0]);
+          const int gp = (fy + dy) * kFP + fx + dx;
+          const float4 h = *reinterpret_cast<const float4*>(&h2[gp * kC + 4 * (sub ^ (gp & 7))]);
           const int t = dy * 3 + dx;
           z += S.w3[(c0 + 0) * 9 + t] * h.x + S.w3[(c0 + 1) * 9 + t] * h.y +
                S.w3[(c0 + 2) * 9 + t] * h.z + S.w3[(c0 + 3) * 9 + t] * h.w;
@@ -527,19 +707,23 @@ __device__ float exact_logodds(const StagedSmem& S, const int8_t* w, int k, int 
 // Network logits of stage k for windows 0 .. nw-1 at the stage's sites
 // (S.logit[w]); the caller synchronises before, this returns after the last
 // phase without a final barrier.
-__device__ void net_eval(StagedSmem& S, const L1Frag& f, int nw, int k) {
+__device__ void net_eval(StagedSmem& S, const L1Frag& f, int nw, int k, uint32_t& parity, bool tc) {
   const StagedPlan& P = S.plan;
   layer1t(S, f, nw, P.l1 + P.off1[k], P.m1 + P.off1[k], P.off1[k + 1] - P.off1[k]);
-  __syncthreads();
-  layer2s(S, nw, P.l2 + P.off2[k], P.off2[k + 1] - P.off2[k]);
+  if (tc) {
+    layer2_tc(S, nw, P.l2 + P.off2[k], P.off2[k + 1] - P.off2[k], parity);  // synchronises first
+  } else {
+    __syncthreads();
+    layer2_mma(S, nw, P.l2 + P.off2[k], P.off2[k + 1] - P.off2[k]);
+  }
   __syncthreads();
   layer3s(S, nw, P.l3 + P.off3[k], P.off3[k + 1] - P.off3[k]);
 }
 
 // One staged MH update of square (bx, by) of a lattice (whole CTA).
-__device__ void process_square(StagedSmem& S, const L1Frag& f1, uint32_t* planes, int L, int Wc,
-                               int colour, int ox, int oy, int bx, int by, uint32_t pass,
-                               uint32_t replica, const RngParams& rng, float beta,
+__device__ void process_square(StagedSmem& S, const L1Frag& f1, uint32_t& parity, bool tc, uint32_t* planes,
+                               int L, int Wc, int colour, int ox, int oy, int bx, int by,
+                               uint32_t pass, uint32_t replica, const RngParams& rng, float beta,
                                unsigned long long* stats) {
   const StagedPlan& P = S.plan;
   const int B = P.B, F = B + 2, BB = B * B;
@@ -588,7 +772,7 @@ __device__ void process_square(StagedSmem& S, const L1Frag& f1, uint32_t* planes
         S.win[0][sf] = (int8_t)s;
       }
     } else {
-      net_eval(S, f1, 2, k);
+      net_eval(S, f1, 2, k, parity, tc);
       __syncthreads();
       if (mine) {
         const uint32_t Pn = quantise_p(S.logit[0][si]);
@@ -646,6 +830,10 @@ __device__ void process_square(StagedSmem& S, const L1Frag& f1, uint32_t* planes
                                 rng.rk0, rng.rk1);
     const float ua = (float)(r.x >> 8) * (1.0f / 16777216.0f);
     S.accept = (log_alpha >= 0.f || ua < expf(log_alpha)) ? 1 : 0;
+    if (S.tc_fail) {  // a tensor-core wait ran out: no move, the host is told
+      S.accept = 0;
+      atomicAdd(&stats[2], 1ull);
+    }
     atomicAdd(&stats[0], 1ull);
     if (S.accept) atomicAdd(&stats[1], 1ull);
   }
@@ -661,6 +849,7 @@ __device__ void process_square(StagedSmem& S, const L1Frag& f1, uint32_t* planes
 struct StagedPassParams {
   uint32_t* planes;  // packed lattice [2][L][Wc]
   int L, Wc, colour;
+  int tc;            // layer 2 on tcgen05 (1) or mma.sync (0)
   uint32_t pass;
   RngParams rng;
   float beta;
@@ -675,7 +864,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_staged_pass(StagedPassP
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
+  if (Q.tc) tmem_setup(S);
   const L1Frag f1 = layer1_frags(S);
+  uint32_t parity = 0;  // phase of the MMA completion barrier
   const int B = S.plan.B, L = Q.L;
   const int nbx = L / B, half = nbx / 2;
   const int n_sq = nbx * half;
@@ -683,9 +874,10 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_staged_pass(StagedPassP
   block_offset(Q.pass, Q.rng.replica, Q.rng, B, ox, oy);
   for (int blk = blockIdx.x; blk < n_sq; blk += gridDim.x) {
     const int by = blk / half, bx = 2 * (blk - by * half) + ((by + Q.colour) & 1);
-    process_square(S, f1, Q.planes, L, Q.Wc, Q.colour, ox, oy, bx, by, Q.pass, Q.rng.replica, Q.rng,
-                   Q.beta, Q.stats);
+    process_square(S, f1, parity, Q.tc != 0, Q.planes, L, Q.Wc, Q.colour, ox, oy, bx, by, Q.pass,
+                   Q.rng.replica, Q.rng, Q.beta, Q.stats);
   }
+  if (Q.tc) tmem_teardown(S);
 }
 
 struct StagedBatchParams {
@@ -696,6 +888,7 @@ struct StagedBatchParams {
   const float* beta_of_slot;
   const long long* unit0;  // [n_rep + 1]
   int n_rep, n_beta, colour;
+  int tc;  // layer 2 on tcgen05 (1) or mma.sync (0)
   uint32_t pass;
   RngParams rng;
   unsigned long long* stats;
@@ -709,7 +902,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_staged_batch_pass(Stage
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
+  if (Q.tc) tmem_setup(S);
   const L1Frag f1 = layer1_frags(S);
+  uint32_t parity = 0;  // phase of the MMA completion barrier
   const int B = S.plan.B;
   const long long total = Q.unit0[Q.n_rep];
   for (long long u = blockIdx.x; u < total; u += gridDim.x) {
@@ -727,14 +922,15 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_staged_batch_pass(Stage
     int ox, oy;
     block_offset(Q.pass, (uint32_t)r, Q.rng, B, ox, oy);
     const float beta = Q.beta_of_slot[Q.slot_of[r]];
-    process_square(S, f1, Q.spins + Q.off[r], L, Wc, Q.colour, ox, oy, bx, by, Q.pass, (uint32_t)r,
-                   Q.rng, beta, Q.stats);
+    process_square(S, f1, parity, Q.tc != 0, Q.spins + Q.off[r], L, Wc, Q.colour, ox, oy, bx, by, Q.pass,
+                   (uint32_t)r, Q.rng, beta, Q.stats);
   }
+  if (Q.tc) tmem_teardown(S);
 }
 
 // Stage logits of windows (tests and diagnostics): window k in S.win[0].
 __global__ void __launch_bounds__(kInferThreads, 1) k_nn_stage_logits(const int8_t* __restrict__ windows,
-                                                              int n, int stage, float beta,
+                                                              int n, int stage, float beta, int tc,
                                                               const StagedPlan* __restrict__ plan,
                                                               const __nv_bfloat16* __restrict__ w,
                                                               const __nv_bfloat16* __restrict__ w2t,
@@ -743,7 +939,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_stage_logits(const int8
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
+  if (tc) tmem_setup(S);
   const L1Frag f1 = layer1_frags(S);
+  uint32_t parity = 0;  // phase of the MMA completion barrier
   const int B = S.plan.B, F = B + 2, BB = B * B;
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
     for (int i = threadIdx.x; i < F * F; i += blockDim.x) S.win[0][i] = windows[(size_t)k * F * F + i];
@@ -754,19 +952,21 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_stage_logits(const int8
       for (int i = threadIdx.x; i < BB; i += blockDim.x)
         if (S.plan.stage_of[i] == stage) S.logit[0][i] = exact_logodds(S, S.win[0], stage, i, beta);
     } else {
-      net_eval(S, f1, 1, stage);
+      net_eval(S, f1, 1, stage, parity, tc != 0);
     }
     __syncthreads();
+    const float nan = __int_as_float(0x7fc00000);
     for (int i = threadIdx.x; i < BB; i += blockDim.x)
-      out[(size_t)k * BB + i] = S.plan.stage_of[i] == stage ? S.logit[0][i] : 0.f;
+      out[(size_t)k * BB + i] = S.tc_fail ? nan : (S.plan.stage_of[i] == stage ? S.logit[0][i] : 0.f);
     __syncthreads();
   }
+  if (tc) tmem_teardown(S);
 }
 
 // Teacher-forced ln q of windows (tests and diagnostics): window k in S.win[1],
 // the same per-stage evaluation as q(old) in process_square.
 __global__ void __launch_bounds__(kInferThreads, 1) k_nn_log_q(const int8_t* __restrict__ windows, int n,
-                                                       float beta, const StagedPlan* __restrict__ plan,
+                                                       float beta, int tc, const StagedPlan* __restrict__ plan,
                                                        const __nv_bfloat16* __restrict__ w,
                                                        const __nv_bfloat16* __restrict__ w2t,
                                                        float* __restrict__ out) {
@@ -774,7 +974,9 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_log_q(const int8_t* __r
   StagedSmem& S = *reinterpret_cast<StagedSmem*>(smem_raw);
   load_all(S, w, w2t, plan);
   __syncthreads();
+  if (tc) tmem_setup(S);
   const L1Frag f1 = layer1_frags(S);
+  uint32_t parity = 0;  // phase of the MMA completion barrier
   const StagedPlan& P = S.plan;
   const int B = P.B, F = B + 2;
   for (int k = blockIdx.x; k < n; k += gridDim.x) {
@@ -794,7 +996,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_log_q(const int8_t* __r
       if (P.exact[st]) {
         if (mine) lq += log2_q_term(quantise_p(exact_logodds(S, S.win[1], st, si, beta)), S.win[1][sf]);
       } else {
-        net_eval(S, f1, 2, st);
+        net_eval(S, f1, 2, st, parity, tc != 0);
         __syncthreads();
         if (mine) lq += log2_q_term(quantise_p(S.logit[1][si]), S.win[1][sf]);
       }
@@ -807,10 +1009,11 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_nn_log_q(const int8_t* __r
     if (threadIdx.x == 0) {
       float t = 0.f;
       for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) t += S.red_lq[w8];
-      out[k] = 0.69314718f * t;
+      out[k] = S.tc_fail ? __int_as_float(0x7fc00000) : 0.69314718f * t;
     }
     __syncthreads();
   }
+  if (tc) tmem_teardown(S);
 }
 
 int sm_count() {
@@ -852,32 +1055,33 @@ cudaError_t nn_plan_stages(int B, int kind, int* n_stages) {
 }
 
 cudaError_t nn_stage_logits(const int8_t* windows, int count, const StagedPlan* d_plan, int stage,
-                            float beta, const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
+                            float beta, int engine, const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
                             float* out, cudaStream_t s) {
   static DeviceCache attr;
   cudaError_t e = allow_smem(k_nn_stage_logits, attr);
   if (e) return e;
   const int grid = std::max(1, std::min(count, 2 * sm_count()));
-  k_nn_stage_logits<<<grid, kInferThreads, sizeof(StagedSmem), s>>>(windows, count, stage, beta, d_plan,
-                                                                   wbf, w2t, out);
+  k_nn_stage_logits<<<grid, kInferThreads, sizeof(StagedSmem), s>>>(windows, count, stage, beta, engine,
+                                                                   d_plan, wbf, w2t, out);
   return cudaGetLastError();
 }
 
-cudaError_t nn_log_q(const int8_t* windows, int count, const StagedPlan* d_plan, float beta,
+cudaError_t nn_log_q(const int8_t* windows, int count, const StagedPlan* d_plan, float beta, int engine,
                      const __nv_bfloat16* wbf, const __nv_bfloat16* w2t, float* out,
                      cudaStream_t s) {
   static DeviceCache attr;
   cudaError_t e = allow_smem(k_nn_log_q, attr);
   if (e) return e;
   const int grid = std::max(1, std::min(count, 2 * sm_count()));
-  k_nn_log_q<<<grid, kInferThreads, sizeof(StagedSmem), s>>>(windows, count, beta, d_plan, wbf, w2t, out);
+  k_nn_log_q<<<grid, kInferThreads, sizeof(StagedSmem), s>>>(windows, count, beta, engine, d_plan, wbf, w2t,
+                                                             out);
   return cudaGetLastError();
 }
 
 }  // namespace nnc
 
 cudaError_t nn_staged_block_pass(uint32_t* planes, int L, int Wc, const nnc::StagedPlan* d_plan, int B,
-                                 uint32_t pass, int colour, const RngParams& rng, double beta,
+                                 uint32_t pass, int colour, const RngParams& rng, double beta, int engine,
                                  const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
                                  unsigned long long* stats, cudaStream_t s) {
   using namespace nnc;
@@ -889,6 +1093,7 @@ cudaError_t nn_staged_block_pass(uint32_t* planes, int L, int Wc, const nnc::Sta
   Q.L = L;
   Q.Wc = Wc;
   Q.colour = colour;
+  Q.tc = engine;
   Q.pass = pass;
   Q.rng = rng;
   Q.beta = (float)beta;
@@ -903,9 +1108,9 @@ cudaError_t nn_batch_staged_block_pass(uint32_t* spins, const long long* off, co
                                        const int* slot_of, const float* beta_of_slot,
                                        const long long* unit0, long long total_units, int n_rep,
                                        int n_beta, const nnc::StagedPlan* d_plan, int colour,
-                                       uint32_t pass, const RngParams& rng, const __nv_bfloat16* wbf,
-                                       const __nv_bfloat16* w2t, unsigned long long* stats,
-                                       cudaStream_t s) {
+                                       uint32_t pass, const RngParams& rng, int engine,
+                                       const __nv_bfloat16* wbf, const __nv_bfloat16* w2t,
+                                       unsigned long long* stats, cudaStream_t s) {
   using namespace nnc;
   static DeviceCache attr;
   cudaError_t e = allow_smem(k_nn_staged_batch_pass, attr);
@@ -920,6 +1125,7 @@ cudaError_t nn_batch_staged_block_pass(uint32_t* spins, const long long* off, co
   Q.n_rep = n_rep;
   Q.n_beta = n_beta;
   Q.colour = colour;
+  Q.tc = engine;
   Q.pass = pass;
   Q.rng = rng;
   Q.stats = stats;

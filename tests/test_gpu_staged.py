@@ -16,6 +16,8 @@
   proposals (acceptance asserted > 0), and sweeps + passes keep the plain
   chain's <E> and <|M|> within 3 sigma on L = 64.
 * The batched staged pass equals the single-lattice staged pass bit for bit.
+* Both engines of the second convolution (mma.sync, tcgen05) pass the logit,
+  ln q and chain tests; their logits agree to FP32 accumulation order.
 """
 import numpy as np
 import pytest
@@ -29,6 +31,7 @@ pytestmark = pytest.mark.gpu
 
 STAGED = ising.ISING_PROPOSAL_STAGED
 BETA_C = 0.4406868
+ENGINES = [ising.ISING_NN_ENGINE_MMA_SYNC, ising.ISING_NN_ENGINE_TCGEN05]
 
 
 @pytest.fixture(scope="module")
@@ -69,14 +72,16 @@ def test_schedule_matches_oracle():
                 assert so[i, j] == k
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("block", [16, 8, 4])
-def test_stage_logits_match_reference(torch, block):
+def test_stage_logits_match_reference(torch, block, engine):
     p32, pref = _params(3)
     wins = _windows(64, 24, block, seed=5)
     st = staged.schedule(block)
     d = torch.from_numpy(wins).cuda()
     out = torch.zeros((len(wins), block, block), dtype=torch.float32, device="cuda")
     with learned.Trainer(block, params=p32, proposal=STAGED) as tr:
+        ising.ising_nn_set_engine(tr.h, engine)
         for k, (kind, sites) in enumerate(st):
             ising.ising_nn_stage_logits(tr.h, d, len(wins), k, BETA_C, out)
             torch.cuda.synchronize()
@@ -91,12 +96,14 @@ def test_stage_logits_match_reference(torch, block):
             assert np.all(got[:, ~m] == 0.0)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("block", [16, 4])
-def test_log_q_matches_reference(torch, block):
+def test_log_q_matches_reference(torch, block, engine):
     p32, pref = _params(7)
     wins = _windows(64, 16, block, seed=8)
     st = staged.schedule(block)
     with learned.Trainer(block, params=p32, proposal=STAGED) as tr:
+        ising.ising_nn_set_engine(tr.h, engine)
         d = torch.from_numpy(wins).cuda()
         out = torch.zeros(len(wins), dtype=torch.float32, device="cuda")
         ising.ising_nn_log_q(tr.h, d, len(wins), BETA_C, out)
@@ -170,11 +177,39 @@ def test_adam_and_bf16_export_match_reference(torch):
     assert np.array_equal(blob.astype(np.uint32), want_blob)
 
 
-def _block_only_chain(L, block, beta, blob, n, seed):
+def test_engines_agree_on_stage_logits(torch):
+    """Same windows, same weights: the two layer-2 engines differ only in the
+    order of the FP32 accumulation of the same FP16 products."""
+    block = 16
+    p32, _ = _params(17)
+    wins = _windows(128, 64, block, seed=18)
+    st = staged.schedule(block)
+    d = torch.from_numpy(wins).cuda()
+    got = {}
+    with learned.Trainer(block, params=p32, proposal=STAGED) as tr:
+        for engine in ENGINES:
+            ising.ising_nn_set_engine(tr.h, engine)
+            outs = []
+            for k, (kind, _) in enumerate(st):
+                if kind != "net":
+                    continue
+                out = torch.zeros((len(wins), block, block), dtype=torch.float32, device="cuda")
+                ising.ising_nn_stage_logits(tr.h, d, len(wins), k, BETA_C, out)
+                outs.append(out.cpu().numpy())
+            got[engine] = np.stack(outs)
+        with pytest.raises(ising.IsingError):
+            ising.ising_nn_set_engine(tr.h, 2)
+    a, b = got[ENGINES[0]], got[ENGINES[1]]
+    assert np.abs(a).max() > 1.0
+    assert np.abs(a - b).max() <= 1e-4 * max(1.0, np.abs(a).max())
+
+
+def _block_only_chain(L, block, beta, blob, n, seed, engine=ising.ISING_NN_ENGINE_MMA_SYNC):
     Es, M2 = [], []
     with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, seed=seed) as lat:
         ising.ising_nn_load(lat.ctx, blob)
         ising.ising_set_proposal(lat.ctx, STAGED)
+        ising.ising_set_nn_engine(lat.ctx, engine)
         for _ in range(n):
             ising.ising_block_pass(lat.ctx, 1, block)
             E, M = lat.measure()
@@ -197,11 +232,12 @@ def test_staged_block_moves_exact_on_4x4(torch):
     assert prop == n * 4 and 0 < acc < prop
 
 
-def test_staged_block_moves_match_kaufman_8x8(torch):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_staged_block_moves_match_kaufman_8x8(torch, engine):
     L, block, beta, n = 8, 4, BETA_C, 12000
     with learned.Trainer(block, params=learned.init_params(seed=14, scale=1.0), proposal=STAGED) as tr:
         blob = tr.blob()
-    Es, _, prop, acc = _block_only_chain(L, block, beta, blob, n, 15)
+    Es, _, prop, acc = _block_only_chain(L, block, beta, blob, n, 15, engine)
     e, de = stats.mean_and_error(Es[300:])
     want = kaufman_energy(L, beta) * L * L
     assert acc > 0.02 * prop
@@ -251,13 +287,15 @@ def test_trained_staged_16x16_accepts_and_keeps_the_chain(torch, trained16):
     assert abs(b - e_exact) < 3 * db, (b, db, e_exact)
 
 
-def test_batch_staged_pass_equals_single_lattice_pass(torch):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_staged_pass_equals_single_lattice_pass(torch, engine):
     Ls, betas, block, seed = [32, 64], np.array([0.38, 0.42, 0.46]), 8, 5
     with learned.Trainer(block, params=learned.init_params(seed=13), proposal=STAGED) as tr:
         blob = tr.blob()
     with ising.Batch(Ls, betas, 1000, seed=seed) as b:
         ising.ising_batch_nn_load(b.h, blob)
         ising.ising_batch_set_proposal(b.h, STAGED)
+        ising.ising_batch_set_nn_engine(b.h, engine)
         ising.ising_batch_block_pass(b.h, 3, block)
         got = {(l, i): b.spins(l, i) for l in range(2) for i in range(3)}
         pb, ab = ising.ising_batch_block_stats(b.h)
@@ -269,6 +307,7 @@ def test_batch_staged_pass_equals_single_lattice_pass(torch):
                 lat.seed(seed)
                 ising.ising_nn_load(lat.ctx, blob)
                 ising.ising_set_proposal(lat.ctx, STAGED)
+                ising.ising_set_nn_engine(lat.ctx, engine)
                 ising.ising_block_pass(lat.ctx, 3, block)
                 assert np.array_equal(lat.spins(), got[(l, i)]), (l, i)
                 p_, a_ = ising.ising_block_stats(lat.ctx)
