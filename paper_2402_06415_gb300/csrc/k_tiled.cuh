@@ -220,7 +220,10 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
   constexpr int H = 2 * K;
   constexpr int TW = 32 * TWW;
   constexpr int SP = TW + 8;
-  constexpr int QCAP = 512;
+  // queue capacity: about 1 word in 10 is still undecided after 8 planes, ~500
+  // words per half sweep of a 72 x 64-word tile (at 512 a quarter of those
+  // half sweeps overflowed into the in-place path)
+  constexpr int QCAP = 768;
   extern __shared__ uint4 smem4[];
   __shared__ uint32_t q_pos[QCAP], q_d[QCAP], q_cls[QCAP];
   __shared__ int q_n[2];
@@ -373,17 +376,24 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
           if (ovfb) So[(r + 1) * SP + col] ^= xb;
         }
       };
+      // three kinds of work item (row pairs, the odd last row, the halo
+      // columns) dealt round-robin to the warps as one sequence, so the warps
+      // that took one item more of a kind start the next kind later
       const int npairs = nrows >> 1;
       for (int item = warp; item < npairs * TWW; item += nwarps) {
         const int r = r_lo + 2 * (item / TWW);
         const int col = 4 + 32 * (item % TWW) + lane;
         phase1_pair(r, col);
       }
+      int w1 = warp - (npairs * TWW) % nwarps;
+      w1 += w1 < 0 ? nwarps : 0;
       if (nrows & 1) {  // odd row count: the last row alone
-        for (int item = warp; item < TWW; item += nwarps)
+        for (int item = w1; item < TWW; item += nwarps)
           phase1(r_lo + nrows - 1, 4 + 32 * item + lane, true);
+        w1 -= TWW % nwarps;
+        w1 += w1 < 0 ? nwarps : 0;
       }
-      for (int base = warp * 32; base < 2 * nrows; base += blockDim.x) {
+      for (int base = w1 * 32; base < 2 * nrows; base += blockDim.x) {
         const int idx = base + lane;
         const bool active = idx < 2 * nrows;
         const int r = r_lo + (active ? (idx >> 1) : 0);

@@ -100,9 +100,11 @@ def test_sweeps_bit_exact(layout, kernel, kargs, L, beta):
     assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
 
 
-@pytest.mark.parametrize("kargs", [(2, 37, 64), (1, 152, 32), (4, 64, 32)])
+@pytest.mark.parametrize("kargs", [(2, 37, 64), (1, 152, 32), (4, 64, 32), (2, 16, 64)])
 def test_tiled32_L4096(kargs):
-    """Warp-per-row tiled kernel with its compaction queue, 64- and 32-word tiles."""
+    """Warp-per-row tiled kernel with its compaction queue, 64- and 32-word tiles;
+    (2, 37, 64) and (2, 16, 64) (256-row strips, ~1700 undecided words per half
+    sweep) overflow the queue, so the in-place path runs too."""
     L, beta, seed, n = 4096, BETA_C, 31, 7
     ref, E_ref, M_ref = _oracle_run(L, beta, seed, n)
     got, E, M = _gpu_run(L, beta, seed, n, BITS, TILED, kargs)
