@@ -37,6 +37,7 @@ MEASURE_EVERY = 10
 BETAS = [0.40, 0.4406868, 0.50]
 SEED = 1
 PROPOSALS = {"oneshot": 0, "staged": 1}  # ISING_PROPOSAL_ONESHOT / _STAGED
+NN_ENGINES = {"mma_sync": 0, "tcgen05": 1}  # ISING_NN_ENGINE_MMA_SYNC / _TCGEN05
 
 # Tiled-kernel launch shape for L = 16384 (sweeps per launch, row strips,
 # words per tile row): the best shape of an autotuning sweep on GB300, used when
@@ -954,6 +955,81 @@ def run_sw(args):
     return 0
 
 
+def run_sw_step(args):
+    """Time of one Swendsen-Wang step on one lattice at beta_c (default L = 16384):
+    30 untimed steps bring the clusters to equilibrium size, then W warm-up and K
+    timed steps, one CUDA-event pair around the K steps."""
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    L, beta = args.sw_L, 0.4406868
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=3) as lat:
+        lat.sw_step(30 + args.warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.sw_step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "Swendsen-Wang step time", "value": ms, "unit": "ms/step", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "data": "synthetic", "dtype": "u32",
+            "config": {"workload": "one Swendsen-Wang step of the %d^2 Ising lattice at beta_c" % L},
+            "site_updates_per_ns": L * L / (ms * 1e6)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_staged_pass(args):
+    """Time of one staged 16x16 block pass (both square colours) on one lattice
+    at beta_c (default L = 256) with a randomly initialised network: W warm-up and
+    K timed passes, one CUDA-event pair around the K passes; --nn-engine picks the
+    engine of the second convolution."""
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import learned
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    L, beta, block = args.pass_L, 0.4406868, 16
+    engine = NN_ENGINES[args.nn_engine]
+    with learned.Trainer(block, seed=1, proposal=PROPOSALS["staged"]) as tr:
+        blob = tr.blob()
+    with ising.Lattice(L, beta, ising.ISING_LAYOUT_BITS, stream=stream, seed=3) as lat:
+        ising.ising_nn_load(lat.ctx, blob)
+        ising.ising_set_proposal(lat.ctx, PROPOSALS["staged"])
+        ising.ising_set_nn_engine(lat.ctx, engine)
+        lat.sweep(50, 0)
+        ising.ising_block_pass(lat.ctx, args.warmup, block)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ising.ising_block_pass(lat.ctx, args.steps, block)
+        e1.record(stream)
+        e1.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / args.steps
+        prop, acc = ising.ising_block_stats(lat.ctx)
+    line = {"metric": "staged block pass time", "value": us, "unit": "us/pass", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "data": "synthetic (random-init network)", "dtype": "f16/f32",
+            "config": {"workload": "staged 16x16 block pass, both square colours, %d^2 lattice at "
+                                   "beta_c" % L, "engine": args.nn_engine},
+            "squares_per_pass": (L // block) ** 2, "acceptance": acc / max(prop, 1)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_quad(args):
     """The paper's quadripartition workloads (Fig. 5b/5d) for the Ising model:
     time per sweep on the square-octagon lattice (J1 = J2 = 1) and on the square
@@ -1138,7 +1214,12 @@ def main(argv=None):
     ap.add_argument("--quad-sweeps", type=int, default=2000)
     ap.add_argument("--precision-sweeps", type=int, default=20000)
     ap.add_argument("--precision-L", type=int, default=1024)
-    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw", "quad", "xy_precision"],
+    ap.add_argument("--sw-L", type=int, default=16384, help="lattice size of --workload sw_step")
+    ap.add_argument("--pass-L", type=int, default=256, help="lattice size of --workload staged_pass")
+    ap.add_argument("--nn-engine", choices=sorted(NN_ENGINES), default="mma_sync",
+                    help="engine of the staged proposal's second convolution (staged_pass)")
+    ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw", "quad",
+                                           "xy_precision", "sw_step", "staged_pass"],
                     default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
@@ -1166,6 +1247,10 @@ def main(argv=None):
         return run_quad(args)
     if args.workload == "xy_precision":
         return run_xy_precision(args)
+    if args.workload == "sw_step":
+        return run_sw_step(args)
+    if args.workload == "staged_pass":
+        return run_staged_pass(args)
     return run_ours(args)
 
 
