@@ -376,9 +376,16 @@ int ising_sw_step(ising_ctx* ctx, int n_steps, int measure_every);
  * step left half-updated, so the lattice and its records are undefined until
  * ising_seed, ising_set_spins or ising_set_bits),
  * a few kernels per step from L = 768 (from L = 2048 with tiled labelling in
- * shared memory; Wolff first tries growth from the seed).  KERNELS /
- * PERSISTENT force one way.  The chain is the same either way, bit for bit. */
-enum { ISING_CLUSTER_AUTO = 0, ISING_CLUSTER_KERNELS = 1, ISING_CLUSTER_PERSISTENT = 2 };
+ * shared memory; Wolff first tries growth from the seed, and its step is one
+ * CUDA graph launch (eight steps per launch when nothing is recorded): the
+ * growth kernel sets the condition of an IF node that holds the labelling
+ * kernels, so a step that growth completes runs one kernel; if the graph
+ * cannot be built, AUTO falls back to separate launches
+ * whose labelling kernels return at once when growth has completed the step).
+ * KERNELS (separate launches) / PERSISTENT / GRAPH (the Wolff graph at any L;
+ * Swendsen-Wang steps as KERNELS) force one way.  The chain is the same either
+ * way, bit for bit. */
+enum { ISING_CLUSTER_AUTO = 0, ISING_CLUSTER_KERNELS = 1, ISING_CLUSTER_PERSISTENT = 2, ISING_CLUSTER_GRAPH = 3 };
 int ising_cluster_set_mode(ising_ctx* ctx, int mode);
 
 /* Wolff single-cluster steps (Wolff, PRL 62, 361 (1989)) on the packed layout:

@@ -27,6 +27,7 @@ ISING_LAYOUT_BITS = 1
 ISING_CLUSTER_AUTO = 0
 ISING_CLUSTER_KERNELS = 1
 ISING_CLUSTER_PERSISTENT = 2
+ISING_CLUSTER_GRAPH = 3
 
 ISING_PROPOSAL_ONESHOT = 0
 ISING_PROPOSAL_STAGED = 1
@@ -418,7 +419,7 @@ class Lattice:
         ising_wolff_step(self.ctx, n, measure_every)
 
     def cluster_set_mode(self, mode: int):
-        """ISING_CLUSTER_AUTO / _KERNELS / _PERSISTENT for sw_step and wolff_step."""
+        """ISING_CLUSTER_AUTO / _KERNELS / _PERSISTENT / _GRAPH for sw_step and wolff_step."""
         _check(lib().ising_cluster_set_mode(self.ctx, int(mode)))
 
     def wolff_set_limits(self, max_sites: int, max_levels: int = 0):

@@ -99,6 +99,8 @@ struct ising_ctx {
   WolffCtl* wolff = nullptr;  // Wolff step state (parent / mark scratch shared with Swendsen-Wang)
   int64_t wolff_steps = 0;
   int wolff_max_sites = kWolffMaxGrowSites, wolff_max_levels = 0;
+  WolffGraph wolff_graph;           // one Wolff step as a CUDA graph (growth + IF labelling)
+  bool wolff_graph_broken = false;  // building it failed once: separate launches from then on
   int cluster_mode = ISING_CLUSTER_AUTO;
   GridCtl* cluster_gctl = nullptr;  // barrier of the persistent cluster kernel
   bool timing = false;
@@ -143,6 +145,7 @@ void free_all(ising_ctx* c) {
   c->plan_B = 0;
   cudaFree(c->sw_parent);
   cudaFree(c->sw_flip);
+  wolff_graph_free(&c->wolff_graph);
   cudaFree(c->wolff);
   cudaFree(c->cluster_gctl);
   c->wolff = nullptr;
@@ -894,7 +897,7 @@ constexpr int kClusterPersistMaxL = 768;
 // Whether cluster steps on this context run as one persistent kernel per call.
 bool cluster_persistent(const ising_ctx* c) {
   if (c->cluster_mode == ISING_CLUSTER_PERSISTENT) return true;
-  if (c->cluster_mode == ISING_CLUSTER_KERNELS) return false;
+  if (c->cluster_mode == ISING_CLUSTER_KERNELS || c->cluster_mode == ISING_CLUSTER_GRAPH) return false;
   // measured on GB300 at beta_c: one launch wins up to L = 512 (70 vs 76 us per
   // step), the kernel-per-phase path at L = 1024 (137 vs 189 us)
   return c->L < kClusterPersistMaxL;
@@ -935,7 +938,7 @@ int record_after_step(ising_ctx* c, int64_t t, int measure_every) {
 
 int ising_cluster_set_mode(ising_ctx* c, int mode) {
   if (int st = check_ctx(c)) return st;
-  if (mode < ISING_CLUSTER_AUTO || mode > ISING_CLUSTER_PERSISTENT) return fail(ISING_EINVAL, "unknown cluster mode");
+  if (mode < ISING_CLUSTER_AUTO || mode > ISING_CLUSTER_GRAPH) return fail(ISING_EINVAL, "unknown cluster mode");
   c->cluster_mode = mode;
   return ok();
 }
@@ -972,6 +975,43 @@ int ising_wolff_step(ising_ctx* c, int n_steps, int measure_every) {
   // default level bound: growth may take about as long as labelling the lattice
   const int levels = c->wolff_max_levels > 0 ? c->wolff_max_levels
                                              : (int)std::min<int64_t>(4096, 32 + (c->N() >> 16));
+  if (n_steps > 0 && !c->wolff_graph_broken && c->cluster_mode != ISING_CLUSTER_KERNELS) {
+    // graph launches: a step that growth completes runs one kernel
+    const BitsLattice lat = c->lat(c->cur);
+    WolffGraph& g = c->wolff_graph;
+    cudaError_t e = cudaSuccess;
+    if (!g.exec || g.planes != lat.planes || g.L != c->L || g.thr != thr || g.replica != rng.replica ||
+        g.key0 != rng.key0 || g.key1 != rng.key1 || g.max_sites != c->wolff_max_sites ||
+        g.max_levels != levels || g.parent != c->sw_parent || g.mark != c->sw_flip || g.ctl != c->wolff)
+      e = wolff_graph_build(&g, lat, thr, rng, c->sw_parent, c->sw_flip, c->wolff_max_sites, levels, c->wolff);
+    if (e == cudaSuccess) {
+      e = wolff_graph_set_step(c->wolff, (uint32_t)c->wolff_steps, c->stream);
+      if (int st = launch_result(c, e, "Wolff step counter")) return st;
+      int k = 0;
+      if (measure_every == 0)  // no records: kWolffGraphUnroll steps per launch
+        for (; k + kWolffGraphUnroll <= n_steps; k += kWolffGraphUnroll) {
+          Timed tm(c);
+          e = cudaGraphLaunch(g.exec_unrolled, c->stream);
+          if (int st = launch_result(c, e, "Wolff step graph")) return st;
+          c->launches += kWolffGraphUnroll;  // growth kernels (labelling adds four when it runs)
+          c->wolff_steps += kWolffGraphUnroll;
+        }
+      for (; k < n_steps; ++k) {
+        const int64_t t = c->wolff_steps;
+        Timed tm(c);
+        e = cudaGraphLaunch(g.exec, c->stream);
+        if (int st = launch_result(c, e, "Wolff step graph")) return st;
+        c->launches += 1;
+        if (int st = record_after_step(c, t, measure_every)) return st;
+        ++c->wolff_steps;
+      }
+      return ok();
+    }
+    cudaGetLastError();
+    if (c->cluster_mode == ISING_CLUSTER_GRAPH)
+      return fail(ISING_ECUDA, "Wolff step graph: %s", cudaGetErrorString(e));
+    c->wolff_graph_broken = true;  // AUTO: separate launches from now on
+  }
   for (int k = 0; k < n_steps; ++k) {
     const int64_t t = c->wolff_steps;
     Timed tm(c);

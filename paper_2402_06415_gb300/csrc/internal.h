@@ -184,10 +184,12 @@ cudaError_t launch_sw_step(const BitsLattice& lat, uint32_t step, uint32_t thr,
 // spins agree and word (b & 3) of Philox(b >> 2, step, replica, bond_tag << 16)
 // is below thr.  Leaves a forest in parent (tiled path: every site points at a
 // local root, mark = 2 at local roots); skipped when gate is non-null and *gate == 0.
+// step_ptr non-null: the kernels read the step from that device word instead
+// (graph replays of a step whose index lives on the device).
 bool sw_tiled(int L);
 cudaError_t launch_cluster_labels(const BitsLattice& lat, uint32_t step, uint32_t thr, uint32_t bond_tag,
                                   const RngParams& rng, uint32_t* parent, uint8_t* mark,
-                                  const uint32_t* gate, cudaStream_t s);
+                                  const uint32_t* gate, cudaStream_t s, const uint32_t* step_ptr = nullptr);
 
 // Wolff single-cluster step state on the device (wolff.cu).
 struct WolffCtl {
@@ -198,6 +200,8 @@ struct WolffCtl {
   unsigned long long flipped;   // sites flipped, all steps
   unsigned long long grown;     // steps completed by growth
   unsigned long long labelled;  // steps completed by labelling
+  uint32_t step;                // graph path: index of the next step (the growth kernel advances it)
+  uint32_t step_body;           // graph path: index of the step whose labelling runs
 };
 constexpr int kWolffMaxGrowSites = 16384;
 size_t wolff_grow_smem(int max_sites);
@@ -206,6 +210,29 @@ size_t wolff_grow_smem(int max_sites);
 cudaError_t launch_wolff_step(const BitsLattice& lat, uint32_t step, uint32_t thr, const RngParams& rng,
                               uint32_t* parent, uint8_t* mark, int max_sites, int max_levels, WolffCtl* ctl,
                               cudaStream_t s);
+// The same step as a CUDA graph: the growth kernel sets the condition of an
+// IF node whose body holds the labelling, resolve and apply kernels, so a step
+// that growth completes launches none of them.  The step index is ctl->step
+// (set it with wolff_graph_set_step); the growth kernel advances it.  exec runs
+// one step, exec_unrolled kWolffGraphUnroll steps in a row.  Built for one set
+// of arguments; the caller rebuilds it when they change.
+constexpr int kWolffGraphUnroll = 8;
+struct WolffGraph {
+  cudaGraph_t graph = nullptr, graph_unrolled = nullptr;
+  cudaGraphExec_t exec = nullptr, exec_unrolled = nullptr;
+  // the arguments the graph was built for
+  const uint32_t* planes = nullptr;
+  int L = 0, max_sites = 0, max_levels = 0;
+  uint32_t thr = 0, replica = 0, key0 = 0, key1 = 0;
+  uint32_t* parent = nullptr;
+  uint8_t* mark = nullptr;
+  WolffCtl* ctl = nullptr;
+};
+cudaError_t wolff_graph_build(WolffGraph* g, const BitsLattice& lat, uint32_t thr, const RngParams& rng,
+                              uint32_t* parent, uint8_t* mark, int max_sites, int max_levels,
+                              WolffCtl* ctl);
+void wolff_graph_free(WolffGraph* g);
+cudaError_t wolff_graph_set_step(WolffCtl* ctl, uint32_t step, cudaStream_t s);
 
 // Cluster steps as one persistent cooperative kernel (cluster_persist.cu):
 // n_steps Swendsen-Wang (wolff = false) or Wolff steps from step0, each a

@@ -85,8 +85,10 @@ __global__ void k_sw_init(uint32_t* __restrict__ parent, long long N, const uint
 __global__ void __launch_bounds__(256) k_sw_bonds(const uint32_t* __restrict__ planes, int L,
                                                   int Wc, uint32_t step, uint32_t thr,
                                                   RngParams rng, uint32_t* __restrict__ parent,
-                                                  FastDiv fL, uint32_t bond_tag, const uint32_t* gate) {
+                                                  FastDiv fL, uint32_t bond_tag, const uint32_t* gate,
+                                                  const uint32_t* step_ptr) {
   if (gated_off(gate)) return;
+  if (step_ptr) step = *step_ptr;
   const long long N = (long long)L * L;
   for (long long pr = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * pr < N;
        pr += (long long)gridDim.x * blockDim.x) {
@@ -191,8 +193,9 @@ __global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __res
                                                            uint32_t step, uint32_t thr, RngParams rng,
                                                            uint32_t* __restrict__ parent,
                                                            uint8_t* __restrict__ mark, uint32_t bond_tag,
-                                                           const uint32_t* gate) {
+                                                           const uint32_t* gate, const uint32_t* step_ptr) {
   if (gated_off(gate)) return;
+  if (step_ptr) step = *step_ptr;
   __shared__ uint32_t lab[kTileSites];
   // per site: bit 0 spin, bit 1 bond li -> li + 1 active, bit 2 bond li -> li + TX
   // active (bonds inside the tile only)
@@ -346,8 +349,9 @@ __global__ void __launch_bounds__(256) k_sw_apply2(uint32_t* __restrict__ planes
 __global__ void __launch_bounds__(256) k_sw_edges(const uint32_t* __restrict__ planes, int L, int Wc,
                                                   uint32_t step, uint32_t thr, RngParams rng,
                                                   uint32_t* __restrict__ parent, uint32_t bond_tag,
-                                                  const uint32_t* gate) {
+                                                  const uint32_t* gate, const uint32_t* step_ptr) {
   if (gated_off(gate)) return;
+  if (step_ptr) step = *step_ptr;
   const int tiles_x = L / kTileX;
   const long long n_tiles = (long long)tiles_x * (L / kTileY);
   const long long total = n_tiles * (kTileX + kTileY);
@@ -392,25 +396,25 @@ bool sw_tiled(int L) { return L % kTileX == 0 && L % kTileY == 0 && L >= 2048; }
 
 cudaError_t launch_cluster_labels(const BitsLattice& lat, uint32_t step, uint32_t thr, uint32_t bond_tag,
                                   const RngParams& rng, uint32_t* parent, uint8_t* mark,
-                                  const uint32_t* gate, cudaStream_t s) {
+                                  const uint32_t* gate, cudaStream_t s, const uint32_t* step_ptr) {
   const long long N = (long long)lat.L * lat.L;
   cudaError_t e;
   // tiles only pay when there are enough of them to fill the GPU (>= 512 CTAs)
   if (sw_tiled(lat.L)) {
     const long long tiles = (long long)(lat.L / kTileX) * (lat.L / kTileY);
     k_sw_local<<<(unsigned)tiles, kTileThreads, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
-                                                        mark, bond_tag, gate);
+                                                        mark, bond_tag, gate, step_ptr);
     e = cudaGetLastError();
     if (e) return e;
     k_sw_edges<<<grid_of(tiles * (kTileX + kTileY)), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng,
-                                                                  parent, bond_tag, gate);
+                                                                  parent, bond_tag, gate, step_ptr);
     return cudaGetLastError();
   }
   k_sw_init<<<grid_of(N), 256, 0, s>>>(parent, N, gate);
   e = cudaGetLastError();
   if (e) return e;
   k_sw_bonds<<<grid_of((N + 1) / 2), 256, 0, s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, parent,
-                                                  make_fastdiv((uint32_t)lat.L), bond_tag, gate);
+                                                  make_fastdiv((uint32_t)lat.L), bond_tag, gate, step_ptr);
   return cudaGetLastError();
 }
 

@@ -62,8 +62,13 @@ size_t grow_hash_cap(int max_sites) {
 __global__ void __launch_bounds__(kGrowThreads) k_wolff_grow(uint32_t* __restrict__ planes, int L, int Wc,
                                                              uint32_t step, uint32_t thr, RngParams rng,
                                                              int max_sites, int max_levels, uint32_t hash_bits,
-                                                             WolffCtl* __restrict__ ctl, FastDiv fL) {
+                                                             WolffCtl* __restrict__ ctl, FastDiv fL,
+                                                             const uint32_t* step_ptr,
+                                                             cudaGraphConditionalHandle cond, int set_cond) {
   extern __shared__ uint32_t sm[];
+  // graph path: the step index lives on the device (read before the first
+  // barrier; thread 0 advances it after the last one)
+  if (step_ptr) step = *step_ptr;
   const uint32_t cap = 1u << hash_bits;
   uint32_t* hash = sm;
   uint32_t* list = sm + cap;
@@ -181,8 +186,17 @@ __global__ void __launch_bounds__(kGrowThreads) k_wolff_grow(uint32_t* __restric
       ctl->labelled += 1;
       ctl->gave_up_run += 1;
     }
+    // graph path: the labelling nodes run only when growth gave up, with this
+    // step's index; the next growth node takes the next one
+    if (set_cond) {
+      ctl->step_body = step;
+      ctl->step = step + 1u;
+      cudaGraphSetConditional(cond, s_state == 1 ? 0u : 1u);
+    }
   }
 }
+
+__global__ void k_wolff_set_step(WolffCtl* ctl, uint32_t step) { ctl->step = step; }
 
 __device__ __forceinline__ uint32_t find_root_ro(const uint32_t* parent, uint32_t a) {
   while (true) {
@@ -277,7 +291,8 @@ cudaError_t launch_wolff_step(const BitsLattice& lat, uint32_t step, uint32_t th
   uint32_t bits = 0;
   while (((size_t)1 << bits) < cap) ++bits;
   k_wolff_grow<<<1, kGrowThreads, wolff_grow_smem(ms), s>>>(lat.planes, lat.L, lat.Wc, step, thr, rng, max_sites,
-                                                            max_levels, bits, ctl, make_fastdiv((uint32_t)lat.L));
+                                                            max_levels, bits, ctl, make_fastdiv((uint32_t)lat.L),
+                                                            nullptr, 0, 0);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
   e = launch_cluster_labels(lat, step, thr, kTagWolffBond, rng, parent, mark, &ctl->need_label, s);
@@ -289,6 +304,131 @@ cudaError_t launch_wolff_step(const BitsLattice& lat, uint32_t step, uint32_t th
       lat.planes, lat.L, lat.Wc, parent, ctl, make_fastdiv((uint32_t)lat.L * (uint32_t)lat.Wc),
       make_fastdiv((uint32_t)lat.Wc));
   return cudaGetLastError();
+}
+
+void wolff_graph_free(WolffGraph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->exec_unrolled) cudaGraphExecDestroy(g->exec_unrolled);
+  if (g->graph_unrolled) cudaGraphDestroy(g->graph_unrolled);
+  *g = WolffGraph{};
+}
+
+cudaError_t wolff_graph_set_step(WolffCtl* ctl, uint32_t step, cudaStream_t s) {
+  k_wolff_set_step<<<1, 1, 0, s>>>(ctl, step);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// n_steps x [growth -> IF(need_label) { labelling, resolve, apply }] recorded
+// into a new graph by stream capture on the private stream cs (capture
+// launches nothing), each body straight into its conditional node's graph.
+cudaError_t wolff_graph_record(cudaStream_t cs, int n_steps, const BitsLattice& lat, uint32_t thr,
+                               const RngParams& rng, uint32_t* parent, uint8_t* mark, int max_sites,
+                               int max_levels, WolffCtl* ctl, cudaGraph_t* out) {
+  const long long N = (long long)lat.L * lat.L;
+  const int ms = max_sites < 1 ? 1 : max_sites;
+  const size_t cap = grow_hash_cap(ms);
+  uint32_t bits = 0;
+  while (((size_t)1 << bits) < cap) ++bits;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e) return e;
+  auto fail = [&](cudaError_t err) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(cs, &junk);  // closes a capture left open by the failure, if any
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return err;
+  };
+  cudaGraphNode_t prev = nullptr;  // the previous step's conditional node
+  for (int k = 0; k < n_steps; ++k) {
+    cudaGraphConditionalHandle cond = 0;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault))) return fail(e);
+    if ((e = cudaStreamBeginCaptureToGraph(cs, graph, prev ? &prev : nullptr, nullptr, prev ? 1 : 0,
+                                           cudaStreamCaptureModeThreadLocal)))
+      return fail(e);
+    k_wolff_grow<<<1, kGrowThreads, wolff_grow_smem(ms), cs>>>(
+        lat.planes, lat.L, lat.Wc, 0u, thr, rng, max_sites, max_levels, bits, ctl,
+        make_fastdiv((uint32_t)lat.L), &ctl->step, cond, 1);
+    if ((e = cudaGetLastError())) return fail(e);
+    // the node the capture just added is the stream's last captured node
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t n_deps = 0;
+    if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &n_deps))) return fail(e);
+    if (n_deps != 1) return fail(cudaErrorStreamCaptureInvalidated);
+    cudaGraphNode_t grow = deps[0];
+    if ((e = cudaStreamEndCapture(cs, &graph))) return fail(e);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond_node = nullptr;
+    if ((e = cudaGraphAddNode(&cond_node, graph, &grow, nullptr, 1, &cp))) return fail(e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+      return fail(e);
+    if ((e = launch_cluster_labels(lat, 0u, thr, kTagWolffBond, rng, parent, mark, nullptr, cs,
+                                   &ctl->step_body)))
+      return fail(e);
+    k_wolff_resolve<<<grid_of(N), 256, 0, cs>>>(parent, mark, N, sw_tiled(lat.L), ctl);
+    if ((e = cudaGetLastError())) return fail(e);
+    k_wolff_apply<<<grid_of(2LL * lat.L * lat.Wc * 32), 256, 0, cs>>>(
+        lat.planes, lat.L, lat.Wc, parent, ctl, make_fastdiv((uint32_t)lat.L * (uint32_t)lat.Wc),
+        make_fastdiv((uint32_t)lat.Wc));
+    if ((e = cudaGetLastError())) return fail(e);
+    if ((e = cudaStreamEndCapture(cs, &body))) return fail(e);
+    prev = cond_node;
+  }
+  *out = graph;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t wolff_graph_build(WolffGraph* g, const BitsLattice& lat, uint32_t thr, const RngParams& rng,
+                              uint32_t* parent, uint8_t* mark, int max_sites, int max_levels,
+                              WolffCtl* ctl) {
+  wolff_graph_free(g);
+  static DeviceCache attr;
+  cudaError_t e = cudaSuccess;
+  if (!attr.get()) {
+    e = cudaFuncSetAttribute(k_wolff_grow, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)wolff_grow_smem(kWolffMaxGrowSites));
+    if (e) return e;
+    attr.set(1);
+  }
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e) return e;
+  WolffGraph w;
+  e = wolff_graph_record(cs, 1, lat, thr, rng, parent, mark, max_sites, max_levels, ctl, &w.graph);
+  if (!e)
+    e = wolff_graph_record(cs, kWolffGraphUnroll, lat, thr, rng, parent, mark, max_sites, max_levels, ctl,
+                           &w.graph_unrolled);
+  if (!e) e = cudaGraphInstantiate(&w.exec, w.graph, 0);
+  if (!e) e = cudaGraphInstantiate(&w.exec_unrolled, w.graph_unrolled, 0);
+  cudaStreamDestroy(cs);
+  if (e) {
+    wolff_graph_free(&w);
+    return e;
+  }
+  w.planes = lat.planes;
+  w.L = lat.L;
+  w.max_sites = max_sites;
+  w.max_levels = max_levels;
+  w.thr = thr;
+  w.replica = rng.replica;
+  w.key0 = rng.key0;
+  w.key1 = rng.key1;
+  w.parent = parent;
+  w.mark = mark;
+  w.ctl = ctl;
+  *g = w;
+  return cudaSuccess;
 }
 
 }  // namespace ising

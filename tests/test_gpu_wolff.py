@@ -6,7 +6,8 @@ connected component, so both ways the GPU finds it (bounded growth from the
 seed in one CTA, or connected components of the whole lattice) must give the
 oracle's configuration bit for bit, and the same cluster size.  The limits
 parametrise which way runs: growth only, labelling only, and a mix in which
-growth gives up part way.
+growth gives up part way; each also as one CUDA graph per step (growth sets
+the condition of an IF node that holds the labelling kernels).
 """
 import numpy as np
 import pytest
@@ -19,10 +20,13 @@ pytestmark = pytest.mark.gpu
 BETA_C = 0.5 * np.log(1.0 + np.sqrt(2.0))
 
 KERNELS, PERSISTENT = ising.ISING_CLUSTER_KERNELS, ising.ISING_CLUSTER_PERSISTENT
+GRAPH = ising.ISING_CLUSTER_GRAPH
 # (mode, (max_sites, max_levels)): the persistent kernel; the kernel path with the
-# default bounds, never growing, growing with generous bounds, tiny bounds
+# default bounds, never growing, growing with generous bounds, tiny bounds; the
+# graph path with the default bounds, never growing, tiny bounds
 LIMITS = {"persistent": (PERSISTENT, None), "default": (KERNELS, None), "label": (KERNELS, (0, 0)),
-          "grow": (KERNELS, (16384, 100000)), "tiny": (KERNELS, (64, 3))}
+          "grow": (KERNELS, (16384, 100000)), "tiny": (KERNELS, (64, 3)),
+          "graph": (GRAPH, None), "graph_label": (GRAPH, (0, 0)), "graph_tiny": (GRAPH, (64, 3))}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -63,13 +67,13 @@ def _run(L, beta, seed, n, limits, replica=0):
 @pytest.mark.parametrize("beta", [1e-9, 0.3, BETA_C, 0.7, 50.0])
 def test_wolff_bit_exact(L, beta, limits):
     st = _run(L, beta, 0xF00D0000 + L, 8, limits, replica=1)
-    if limits in ("label", "persistent"):
+    if limits in ("label", "persistent", "graph_label"):
         assert st["grown"] == 0
     if limits == "grow" and L * L <= 16384 // 4:
         assert st["labelled"] == 0
 
 
-@pytest.mark.parametrize("limits", ["default", "label", "tiny", "persistent"])
+@pytest.mark.parametrize("limits", ["default", "label", "tiny", "persistent", "graph", "graph_tiny"])
 @pytest.mark.parametrize("L,beta", [(2048, BETA_C), (2560, 0.3), (2048, 0.7)])
 def test_wolff_tiled_labelling_bit_exact(L, beta, limits):
     """Lattices of >= 2048 sites a side that are multiples of the 128 x 64 tile
@@ -77,11 +81,57 @@ def test_wolff_tiled_labelling_bit_exact(L, beta, limits):
     _run(L, beta, 60 + L, 4, limits)
 
 
-def test_wolff_growth_used_away_from_criticality():
-    """At beta = 0.3 clusters are small: on the kernel path every step
-    finishes by growth."""
-    st = _run(1024, 0.3, 9, 40, "default")
+@pytest.mark.parametrize("limits", ["default", "graph"])
+def test_wolff_growth_used_away_from_criticality(limits):
+    """At beta = 0.3 clusters are small: on the kernel and graph paths every
+    step finishes by growth."""
+    st = _run(1024, 0.3, 9, 40, limits)
     assert st["labelled"] == 0 and st["grown"] == 40
+
+
+@pytest.mark.parametrize("L,beta", [(1024, 0.3), (2048, BETA_C)])
+def test_wolff_graph_unrolled_steps(L, beta):
+    """Without records the graph path runs eight steps per launch (here 2 x 8
+    plus a remainder of 3): the same chain as the oracle's, bit for bit."""
+    seed, n = 41, 19
+    s = oracle.init(L, seed)
+    with ising.Lattice(L, beta, seed=seed) as lat:
+        lat.set_spins(s)
+        lat.cluster_set_mode(GRAPH)
+        lat.wolff_step(n, 0)
+        got = lat.spins()
+        st = lat.wolff_stats()
+    _, _, C_ref = oracle.wolff_steps(s, beta, seed, n)
+    assert np.array_equal(got, s)
+    assert st["grown"] + st["labelled"] == n and st["flipped"] == int(C_ref.sum())
+
+
+def test_wolff_graph_rebuilt_when_arguments_change():
+    """Graph steps, sweeps (which move the lattice to the other buffer), a new
+    beta and new limits in between: the graph follows, and the step counter it
+    keeps on the device continues the host's, bit for bit."""
+    L, seed = 1024, 77
+    s = oracle.init(L, seed)
+    with ising.Lattice(L, 0.3, seed=seed) as lat:
+        lat.set_spins(s)
+        lat.cluster_set_mode(GRAPH)
+        lat.wolff_step(3)
+        lat.sweep(3)
+        lat.wolff_step(2)
+        ising.ising_set_beta(lat.ctx, BETA_C)
+        lat.wolff_step(2)
+        lat.wolff_set_limits(64, 3)
+        lat.wolff_step(2)
+        got = lat.spins()
+        st = lat.wolff_stats()
+    t = s.copy()
+    oracle.wolff_steps(t, 0.3, seed, 3)
+    oracle.sweep(t, 0.3, seed, 3)
+    oracle.wolff_steps(t, 0.3, seed, 2, step0=3)
+    oracle.wolff_steps(t, BETA_C, seed, 2, step0=5)
+    oracle.wolff_steps(t, BETA_C, seed, 2, step0=7)
+    assert np.array_equal(got, t)
+    assert st["grown"] + st["labelled"] == 9
 
 
 def test_wolff_counter_and_seed_reset():
@@ -113,8 +163,8 @@ def test_wolff_paths_interleaved_and_sparse_records(L):
     beta, seed = BETA_C, 31 + L
     s = oracle.init(L, seed)
     with ising.Lattice(L, beta, seed=seed) as lat:
-        for k, (mode, n) in enumerate([(PERSISTENT, 4), (KERNELS, 3), (PERSISTENT, 7), (KERNELS, 1),
-                                       (PERSISTENT, 5)]):
+        for k, (mode, n) in enumerate([(PERSISTENT, 4), (KERNELS, 3), (GRAPH, 2), (PERSISTENT, 5),
+                                       (KERNELS, 1), (GRAPH, 2), (PERSISTENT, 3)]):
             lat.cluster_set_mode(mode)
             lat.wolff_step(n, 3)
         got = lat.spins()
@@ -147,7 +197,7 @@ def test_wolff_rejects_bad_arguments():
         with pytest.raises(ising.IsingError):
             lat.wolff_step(-1)
         with pytest.raises(ising.IsingError):
-            lat.cluster_set_mode(3)
+            lat.cluster_set_mode(4)
     with ising.Lattice(16, 0.4, ising.ISING_LAYOUT_I8) as lat:
         with pytest.raises(ising.IsingError):
             lat.wolff_step(1)
