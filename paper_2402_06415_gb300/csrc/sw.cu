@@ -189,7 +189,7 @@ __device__ __forceinline__ void sunite(uint32_t* lab, uint32_t a, uint32_t b) {
 // labelled with the start of its run by a warp max-scan, no atomics), then the
 // vertical bonds unite runs (skipping a bond whose left neighbour already joined
 // the same two runs), then every label is resolved to its root.
-__global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __restrict__ planes, int L, int Wc,
+__global__ void __launch_bounds__(kTileThreads, 4) k_sw_local(const uint32_t* __restrict__ planes, int L, int Wc,
                                                            uint32_t step, uint32_t thr, RngParams rng,
                                                            uint32_t* __restrict__ parent,
                                                            uint8_t* __restrict__ mark, uint32_t bond_tag,
@@ -197,6 +197,12 @@ __global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __res
   if (gated_off(gate)) return;
   if (step_ptr) step = *step_ptr;
   __shared__ uint32_t lab[kTileSites];
+  // vertical bonds that need a union, compacted so that every lane of a warp
+  // works on one (a full list makes the scan unite in place)
+  constexpr int kUnionCap = 4096;
+  __shared__ uint16_t ulist[kUnionCap];
+  __shared__ int s_nu;
+  if (threadIdx.x == 0) s_nu = 0;
   // per site: bit 0 spin, bit 1 bond li -> li + 1 active, bit 2 bond li -> li + TX
   // active (bonds inside the tile only)
   __shared__ __align__(16) uint8_t st[kTileSites];
@@ -265,17 +271,57 @@ __global__ void __launch_bounds__(kTileThreads) k_sw_local(const uint32_t* __res
     }
   }
   __syncthreads();
-  // vertical bonds unite runs
+  // vertical bonds unite runs: list the bonds that need a union (warp ballot,
+  // one shared-memory atomic per warp), then unite with every lane busy
+  {
+    const int lane = threadIdx.x & 31;
+    for (int li = threadIdx.x; li < kTileSites; li += blockDim.x) {
+      const int lx = li % kTileX;
+      // skipped: no vertical bond, or the left neighbour's vertical bond
+      // already joined the same two runs
+      const bool need = (st[li] & 4u) && !(lx > 0 && (st[li - 1] & 6u) == 6u && (st[li - 1 + kTileX] & 2u));
+      const uint32_t m = __ballot_sync(0xffffffffu, need);
+      int base = 0;
+      if (lane == 0 && m) base = atomicAdd(&s_nu, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (need) {
+        const int slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < kUnionCap)
+          ulist[slot] = (uint16_t)li;
+        else
+          sunite(lab, (uint32_t)(li + kTileX), (uint32_t)li);
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int nu = min(s_nu, kUnionCap);
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+      const uint32_t li = ulist[i];
+      sunite(lab, li + kTileX, li);
+    }
+  }
+  __syncthreads();
+  // Roots.  Every label is a run start (the runs pass sets run starts, unions
+  // link roots, path halving stores grandparents), so once each run start
+  // knows its root, the root of site li is that of run start lab[li].  Run
+  // starts walk read-only (labels < 2^13 in the low half of each word) and
+  // store their root in the high half of their own word, which no walk reads.
   for (int li = threadIdx.x; li < kTileSites; li += blockDim.x) {
-    if (!(st[li] & 4u)) continue;
     const int lx = li % kTileX;
-    // the left neighbour's vertical bond already joined the same two runs
-    if (lx > 0 && (st[li - 1] & 6u) == 6u && (st[li - 1 + kTileX] & 2u)) continue;
-    sunite(lab, (uint32_t)(li + kTileX), (uint32_t)li);
+    if (lx == 0 || !(st[li - 1] & 2u)) {
+      uint32_t a = (uint32_t)li;
+      while (true) {
+        const uint32_t p = lab[a] & 0xffffu;
+        if (p == a) break;
+        a = p;
+      }
+      lab[li] = (lab[li] & 0xffffu) | (a << 16);
+    }
   }
   __syncthreads();
   for (int li = threadIdx.x; li < kTileSites; li += blockDim.x) {
-    const uint32_t r = sfind(lab, (uint32_t)li);
+    const uint32_t r = lab[lab[li] & 0xffffu] >> 16;
     const int ly = li / kTileX, lx = li - ly * kTileX;
     const int ry = (int)r / kTileX, rx = (int)r - ry * kTileX;
     const size_t g = (size_t)(y0 + ly) * L + x0 + lx;
