@@ -95,6 +95,25 @@ __device__ bool grid_barrier(const BatchDev& d) {
   return *((volatile int*)&d.ctr->status) == 0;
 }
 
+
+// Side word (the x-neighbours of the other colour, as side_word) and valid
+// mask without branches: the 32 lanes of a warp hold words of several rows,
+// so they disagree on the row parity and on first / last word, and a branch
+// would run both ways.
+__device__ __forceinline__ uint32_t side_word_bf(const uint32_t* rm, int w, int Wc, int n, int o) {
+  const int nb = n - 32 * (Wc - 1);
+  const uint32_t cur = rm[w];
+  const uint32_t prevw = rm[w > 0 ? w - 1 : Wc - 1];
+  const uint32_t nextw = rm[w < Wc - 1 ? w + 1 : 0];
+  const uint32_t c0 = w > 0 ? (prevw >> 31) : ((prevw >> (nb - 1)) & 1u);
+  const uint32_t c1 = w < Wc - 1 ? (nextw << 31) : ((nextw & 1u) << (nb - 1));
+  return o == 0 ? ((cur << 1) | c0) : ((cur >> 1) | c1);
+}
+__device__ __forceinline__ uint32_t valid_mask_bf(int w, int Wc, int n) {
+  const int nb = n - 32 * (Wc - 1);
+  const uint32_t last = nb >= 32 ? 0xffffffffu : ((1u << (nb & 31)) - 1u);
+  return w < Wc - 1 ? 0xffffffffu : last;
+}
 constexpr int kQueueCap = 512;  // undecided words per half sweep finished by whole warps
 
 // Bit-plane compare of Philox blocks B0 .. B1-1 for the undecided lanes D of one
@@ -182,8 +201,8 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
         const uint32_t up = Sn[(y == 0 ? L - 1 : y - 1) * Wc + w];
         const uint32_t dn = Sn[(y == L - 1 ? 0 : y + 1) * Wc + w];
         const uint32_t mid = rm[w];
-        const uint32_t side = side_word([rm](int ww) { return rm[ww]; }, w, Wc, n, (y + c) & 1);
-        const uint32_t valid = active ? valid_mask(w, Wc, n) : 0u;
+        const uint32_t side = side_word_bf(rm, w, Wc, n, (y + c) & 1);
+        const uint32_t valid = active ? valid_mask_bf(w, Wc, n) : 0u;
         const Classes k = classify(sv, up, dn, mid, side);
         uint32_t D = (k.one | k.zero) & valid, acc = 0;
         const uint32_t g = (uint32_t)(y * Wc + w), rep = (uint32_t)(r0 + qq);
@@ -232,12 +251,12 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
     const uint32_t* P0 = sm + qq * per_rep;
     const uint32_t* P1 = P0 + plane;
     const uint32_t* rm = P1 + y * Wc;
-    const uint32_t valid = valid_mask(w, Wc, n);
+    const uint32_t valid = valid_mask_bf(w, Wc, n);
     const uint32_t sv = P0[y * Wc + w];
     const uint32_t up = P1[(y == 0 ? L - 1 : y - 1) * Wc + w];
     const uint32_t dn = P1[(y == L - 1 ? 0 : y + 1) * Wc + w];
     const uint32_t mid = rm[w];
-    const uint32_t side = side_word([rm](int ww) { return rm[ww]; }, w, Wc, n, y & 1);
+    const uint32_t side = side_word_bf(rm, w, Wc, n, y & 1);
     const unsigned int a = __popc((sv ^ up) & valid) + __popc((sv ^ dn) & valid) +
                            __popc((sv ^ mid) & valid) + __popc((sv ^ side) & valid);
     const unsigned int o = __popc(sv & valid) + __popc(mid & valid);
