@@ -38,6 +38,7 @@ BETAS = [0.40, 0.4406868, 0.50]
 SEED = 1
 PROPOSALS = {"oneshot": 0, "staged": 1}  # ISING_PROPOSAL_ONESHOT / _STAGED
 NN_ENGINES = {"mma_sync": 0, "tcgen05": 1}  # ISING_NN_ENGINE_MMA_SYNC / _TCGEN05
+TRAIN_PRECISIONS = {"fp32": 0, "bf16_tc": 1}  # ISING_NN_TRAIN_FP32 / _BF16_TC
 
 # Tiled-kernel launch shape for L = 16384 (sweeps per launch, row strips,
 # words per tile row): the best shape of an autotuning sweep on GB300, used when
@@ -464,7 +465,8 @@ def measure_indep_samples(args, stream):
     t0 = time.perf_counter()
     wins = learned.generate_windows([64, 128, 256], beta, args.indep_train_windows // 3, block, seed=7,
                                     thermalise=2000, thin=20, per_config=64, stream=stream)
-    with learned.Trainer(block, seed=8, proposal=PROPOSALS["staged"]) as tr:
+    with learned.Trainer(block, seed=8, proposal=PROPOSALS["staged"],
+                         precision=TRAIN_PRECISIONS[args.train_precision]) as tr:
         losses = tr.fit(wins, epochs=args.indep_train_epochs, batch=512, lr=2e-3, seed=9)
         blob = tr.blob()
     torch.cuda.synchronize()
@@ -550,6 +552,7 @@ def measure_indep_samples(args, stream):
             gains["learned_over_plain_%s_%s" % (reg, obs)] = [r, dr]
     out["gain"] = gains
     out["train"] = {"windows": int(len(wins)), "epochs": args.indep_train_epochs,
+                    "kernel": args.train_precision,
                     "loss_first": float(np.mean(losses[:5])), "loss_last": float(np.mean(losses[-5:])),
                     "seconds": t_train}
     out["seconds"] = time.perf_counter() - t_all
@@ -650,7 +653,8 @@ def run_learned(args):
     t_data = time.perf_counter() - t0
     kind = PROPOSALS[args.proposal]
     t0 = time.perf_counter()
-    with learned.Trainer(block, seed=8, proposal=kind) as tr:
+    with learned.Trainer(block, seed=8, proposal=kind,
+                         precision=TRAIN_PRECISIONS[args.train_precision]) as tr:
         losses = tr.fit(wins, epochs=args.train_epochs, batch=512, lr=2e-3, seed=9)
         blob = tr.blob()
     torch.cuda.synchronize()
@@ -727,7 +731,8 @@ def run_learned(args):
         "plain": res["plain"], "learned": res["learned"], "acceptance_by_block": scan,
         "gain_indep_samples_absM": gain_m, "gain_indep_samples_E": gain_e,
         "train": {"loss_first": float(np.mean(losses[:5])), "loss_last": float(np.mean(losses[-5:])),
-                  "data_s": t_data, "train_s": t_train, "steps": len(losses)},
+                  "data_s": t_data, "train_s": t_train, "steps": len(losses),
+                  "kernel": args.train_precision},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -752,7 +757,8 @@ def run_batch_learned(args):
     wins = learned.generate_windows([64, 128, 256], 0.4406868, 30000, block, seed=7,
                                     thermalise=2000, thin=20, per_config=64)
     kind = PROPOSALS[args.proposal]
-    with learned.Trainer(block, seed=8, proposal=kind) as tr:
+    with learned.Trainer(block, seed=8, proposal=kind,
+                         precision=TRAIN_PRECISIONS[args.train_precision]) as tr:
         tr.fit(wins, epochs=3, batch=512, lr=2e-3, seed=9)
         blob = tr.blob()
     stream = torch.cuda.current_stream()
@@ -1030,6 +1036,58 @@ def run_staged_pass(args):
     return 0
 
 
+def run_train(args):
+    """Training throughput of the staged 16 x 16 proposal's network: K timed
+    train steps (minibatch of 512 windows x 8 network stages, then Adam) after W
+    warm-up steps, with each training kernel (FP32 CUDA cores / BF16 tensor
+    cores).  Algorithmic FLOPs per sample: the three 32 -> 32 contractions
+    (forward, input gradient, weight gradient) 3 x 2 x 324 x 288 x 32, plus
+    layers 1 and 3 (forward and gradients) 2 x 324 x 32 x 18 x 2 + 3 x 2 x 324 x 32 x 9."""
+    import numpy as np
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+    from paper_2402_06415_gb300 import learned
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    block, batch = 16, 512
+    wins = learned.generate_windows([64, 128], 0.4406868, 2048, block, seed=7, thermalise=500, thin=20,
+                                    per_config=64, stream=stream)
+    flop = 3 * 2 * 324 * 288 * 32 + 2 * 324 * 32 * 18 * 2 + 3 * 2 * 324 * 32 * 9
+    res = {}
+    for name in args.train_kernels:
+        with learned.Trainer(block, seed=8, proposal=PROPOSALS["staged"],
+                             precision=TRAIN_PRECISIONS[name]) as tr:
+            d = torch.from_numpy(np.ascontiguousarray(wins[:batch])).cuda()
+            n_net = 8
+            for _ in range(args.warmup):
+                ising.ising_nn_train_step(tr.h, d, batch, 1e-4)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                ising.ising_nn_train_step(tr.h, d, batch, 1e-4)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+        samples = batch * n_net
+        res[name] = {"ms_per_step": ms, "samples_per_s": samples / (ms / 1e3),
+                     "tflops": samples * flop / (ms / 1e3) / 1e12}
+    line = {"metric": "CNN training throughput (staged 16x16 proposal)",
+            "value": res[args.train_kernels[-1]]["samples_per_s"], "unit": "samples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "data": "synthetic (plain-sweep windows at beta_c)", "dtype": "bf16/f32",
+            "config": {"workload": "train steps of 512 windows x 8 network stages (16x16 staged proposal)",
+                       "flop_per_sample": flop},
+            "kernels": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_quad(args):
     """The paper's quadripartition workloads (Fig. 5b/5d) for the Ising model:
     time per sweep on the square-octagon lattice (J1 = J2 = 1) and on the square
@@ -1216,10 +1274,14 @@ def main(argv=None):
     ap.add_argument("--precision-L", type=int, default=1024)
     ap.add_argument("--sw-L", type=int, default=16384, help="lattice size of --workload sw_step")
     ap.add_argument("--pass-L", type=int, default=256, help="lattice size of --workload staged_pass")
+    ap.add_argument("--train-precision", choices=sorted(TRAIN_PRECISIONS), default="bf16_tc",
+                    help="training kernel of the learned workloads")
+    ap.add_argument("--train-kernels", nargs="*", choices=sorted(TRAIN_PRECISIONS),
+                    default=["fp32", "bf16_tc"], help="kernels timed by --workload train")
     ap.add_argument("--nn-engine", choices=sorted(NN_ENGINES), default="mma_sync",
                     help="engine of the staged proposal's second convolution (staged_pass)")
     ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw", "quad",
-                                           "xy_precision", "sw_step", "staged_pass"],
+                                           "xy_precision", "sw_step", "staged_pass", "train"],
                     default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
@@ -1251,6 +1313,8 @@ def main(argv=None):
         return run_sw_step(args)
     if args.workload == "staged_pass":
         return run_staged_pass(args)
+    if args.workload == "train":
+        return run_train(args)
     return run_ours(args)
 
 

@@ -448,6 +448,17 @@ int ising_nn_set_proposal(ising_nn* nn, int kind);
 /* Layer-2 engine of ising_nn_stage_logits / ising_nn_log_q (as
  * ising_set_nn_engine; training keeps its own FP32 path). */
 int ising_nn_set_engine(ising_nn* nn, int engine);
+/* Training kernel of ising_nn_loss_grad / ising_nn_train_step.
+ * FP32 (default): every layer in FP32 on the CUDA cores (gradients to FP32
+ * rounding order of the float64 objective).
+ * BF16_TC: the 32 -> 32 convolution's forward, input-gradient and
+ * weight-gradient contractions on the tensor cores (mma.sync m16n8k16, BF16
+ * operands: activations, dL/dz2 and the weights rounded to BF16; FP32
+ * accumulation); layers 1 and 3 in FP32.  Same objective, gradients to BF16
+ * rounding.  The FP32 master weights and Adam are unchanged.  ISING_EINVAL for
+ * other values. */
+enum { ISING_NN_TRAIN_FP32 = 0, ISING_NN_TRAIN_BF16_TC = 1 };
+int ising_nn_set_train_precision(ising_nn* nn, int precision);
 /* Logits of stage `stage` of the trainer's proposal for count windows on the
  * device (BF16 inference path): network stages give the CNN logits, exact
  * stages the exact log-odds at beta, at the stage's sites; other sites 0.

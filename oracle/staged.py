@@ -277,10 +277,26 @@ def _interior(B):
 # training of the staged proposal
 # ---------------------------------------------------------------------------
 
-def masked_loss_and_grads(params, frames, targets, tmask):
+def masked_loss_and_grads(params, frames, targets, tmask, bf16_operands=False):
     """Mean over samples of sum over tmask sites of BCE(logit, (t+1)/2) and
-    its gradients.  frames (N, 2, F, F), targets (N, B, B) +-1, tmask (N, B, B)."""
-    logits, (x0, z1, h1, z2, h2, z3) = cnn.forward(params, frames, keep=True)
+    its gradients.  frames (N, 2, F, F), targets (N, B, B) +-1, tmask (N, B, B).
+
+    bf16_operands: the same objective with the operands of the 32 -> 32
+    convolution rounded to bfloat16 where a BF16-operand / FP32-accumulate
+    tensor-core implementation rounds them (BF16 weights with FP32
+    accumulation): W2, the layer-1 output h1 (forward and weight gradient),
+    the layer-2 output h2 (which layer 3 and its gradient read) and dL/dz2
+    (input and weight gradients of layer 2; the bias gradient sums it
+    unrounded).  Everything else stays float64."""
+    r = cnn.bf16_round if bf16_operands else (lambda a: a)
+    W2 = r(params["W2"])
+    x0 = frames
+    z1 = cnn.conv3x3(x0, params["W1"], params["b1"])
+    h1 = r(np.maximum(z1, 0.0))
+    z2 = cnn.conv3x3(h1, W2, params["b2"])
+    h2 = r(np.maximum(z2, 0.0))
+    z3 = cnn.conv3x3(h2, params["W3"], params["b3"])
+    logits = z3[:, 0, 1:-1, 1:-1]
     y = (targets.astype(np.float64) + 1.0) / 2.0
     w = tmask.astype(np.float64)
     N = frames.shape[0]
@@ -290,7 +306,8 @@ def masked_loss_and_grads(params, frames, targets, tmask):
     gz3[:, 0, 1:-1, 1:-1] = g
     gh2, gW3, gb3 = cnn.conv3x3_backward(h2, params["W3"], gz3)
     gz2 = gh2 * (z2 > 0)
-    gh1, gW2, gb2 = cnn.conv3x3_backward(h1, params["W2"], gz2)
+    gh1, gW2, _ = cnn.conv3x3_backward(h1, W2, r(gz2))
+    gb2 = gz2.sum(axis=(0, 2, 3))
     gz1 = gh1 * (z1 > 0)
     _, gW1, gb1 = cnn.conv3x3_backward(x0, params["W1"], gz1)
     return loss, {"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2, "W3": gW3, "b3": gb3}
@@ -316,11 +333,12 @@ def training_samples(windows, B, stages=None):
     return np.stack(frs), np.stack(tg), np.stack(tm)
 
 
-def staged_loss_and_grads(params, windows, B, stages=None):
-    """Loss = mean over windows of sum over network stages of the masked BCE."""
+def staged_loss_and_grads(params, windows, B, stages=None, bf16_operands=False):
+    """Loss = mean over windows of sum over network stages of the masked BCE
+    (bf16_operands as in masked_loss_and_grads)."""
     frs, tg, tm = training_samples(windows, B, stages)
     n_net = frs.shape[0] // len(windows)
-    loss, g = masked_loss_and_grads(params, frs, tg, tm)
+    loss, g = masked_loss_and_grads(params, frs, tg, tm, bf16_operands)
     return loss * n_net, {k: v * n_net for k, v in g.items()}
 
 

@@ -33,6 +33,8 @@ ISING_PROPOSAL_ONESHOT = 0
 ISING_PROPOSAL_STAGED = 1
 ISING_NN_ENGINE_MMA_SYNC = 0
 ISING_NN_ENGINE_TCGEN05 = 1
+ISING_NN_TRAIN_FP32 = 0
+ISING_NN_TRAIN_BF16_TC = 1
 
 ISING_KERNEL_AUTO = 0
 ISING_KERNEL_HALF = 1
@@ -127,6 +129,7 @@ _PROTOS = [
     ("ising_set_nn_engine", _i, [_p, _i]),
     ("ising_batch_set_nn_engine", _i, [_p, _i]),
     ("ising_nn_set_engine", _i, [_p, _i]),
+    ("ising_nn_set_train_precision", _i, [_p, _i]),
     ("ising_proposal_schedule", _i, [_i, _i, _p, _p, _i, ctypes.POINTER(_i)]),
     ("ising_nn_stage_logits", _i, [_p, _p, _i, _i, ctypes.c_double, _p]),
     ("ising_nn_log_q", _i, [_p, _p, _i, ctypes.c_double, _p]),
@@ -739,6 +742,10 @@ def ising_batch_set_nn_engine(b: int, engine: int) -> None:
 
 def ising_nn_set_engine(nn: int, engine: int) -> None:
     _check(lib().ising_nn_set_engine(nn, int(engine)))
+
+
+def ising_nn_set_train_precision(nn: int, precision: int) -> None:
+    _check(lib().ising_nn_set_train_precision(nn, int(precision)))
 
 
 def ising_proposal_schedule(block: int, kind: int = ISING_PROPOSAL_STAGED):

@@ -529,6 +529,7 @@ __global__ void __launch_bounds__(kInferThreads) k_nn_const(const __nv_bfloat16*
 // ---------------------------------------------------------------------------
 struct TrainSmem {
   float prm[kNParams];
+  float gacc[kNParams];  // this CTA's gradient sums over its samples (flushed once)
   float x0[(kMaxB + 2) * (kMaxB + 2)];   // ring spins
   float x1[(kMaxB + 2) * (kMaxB + 2)];   // ring mask
   float h1[(kMaxB + 2) * (kMaxB + 2) * kC];
@@ -553,7 +554,10 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   const int F = frame_of(B), FF = F * F;
   const float invn = 1.f / (float)n;
-  for (int i = threadIdx.x; i < kNParams; i += blockDim.x) S.prm[i] = params[i];
+  for (int i = threadIdx.x; i < kNParams; i += blockDim.x) {
+    S.prm[i] = params[i];
+    S.gacc[i] = 0.f;
+  }
   __syncthreads();
   const float* W1 = S.prm + kOffW1;
   const float* b1 = S.prm + kOffB1;
@@ -626,7 +630,7 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
       float s = 0.f;
       if (i == kC * 9) {
         for (int p = 0; p < FF; ++p) s += S.g3[p];
-        atomicAdd(&grads[kOffB3], s);
+        S.gacc[kOffB3] += s;
       } else {
         const int c = i / 9, t = i % 9, dy = t / 3 - 1, dx = t % 3 - 1;
         for (int p = 0; p < FF; ++p) {
@@ -634,7 +638,7 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
           const int fy = p / F, fx = p - (p / F) * F;
           s += S.g3[p] * at(S.h2, F, fy + dy, fx + dx, kC, c);
         }
-        atomicAdd(&grads[kOffW3 + i], s);
+        S.gacc[kOffW3 + i] += s;
       }
     }
     for (int i = threadIdx.x; i < FF * kC; i += blockDim.x) {
@@ -654,7 +658,7 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
       if (i >= kC * kC * 9) {
         const int o = i - kC * kC * 9;
         for (int p = 0; p < FF; ++p) s += S.gz2[p * kC + o];
-        atomicAdd(&grads[kOffB2 + o], s);
+        S.gacc[kOffB2 + o] += s;
       } else {
         const int o = i / (kC * 9), c = (i / 9) % kC, t = i % 9, dy = t / 3 - 1, dx = t % 3 - 1;
         for (int p = 0; p < FF; ++p) {
@@ -663,7 +667,7 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
           const int fy = p / F, fx = p - (p / F) * F;
           s += g * at(S.h1, F, fy + dy, fx + dx, kC, c);
         }
-        atomicAdd(&grads[kOffW2 + i], s);
+        S.gacc[kOffW2 + i] += s;
       }
     }
     __syncthreads();
@@ -685,7 +689,7 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
       if (i >= kC * 18) {
         const int o = i - kC * 18;
         for (int p = 0; p < FF; ++p) s += S.h2[p * kC + o];
-        atomicAdd(&grads[kOffB1 + o], s);
+        S.gacc[kOffB1 + o] += s;
       } else {
         const int o = i / 18, ci = (i / 9) % 2, t = i % 9, dy = t / 3 - 1, dx = t % 3 - 1;
         const float* xin = ci == 0 ? S.x0 : S.x1;
@@ -696,11 +700,15 @@ __global__ void __launch_bounds__(kThreads) k_nn_train(const int8_t* __restrict_
           if (fy < 0 || fy >= F || fx < 0 || fx >= F) continue;
           s += g * xin[fy * F + fx];
         }
-        atomicAdd(&grads[kOffW1 + i], s);
+        S.gacc[kOffW1 + i] += s;
       }
     }
     __syncthreads();
   }
+  // gradients: one global add per parameter and CTA (each parameter's sum is
+  // written by one thread per sample, so the shared sums need no atomics)
+  for (int i = threadIdx.x; i < kNParams; i += blockDim.x)
+    if (S.gacc[i] != 0.f) atomicAdd(&grads[i], S.gacc[i]);
   // loss
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_loss += __shfl_xor_sync(0xffffffffu, my_loss, o);
@@ -867,6 +875,7 @@ struct ising_nn {
   int B = 16;
   int kind = kProposalOneShot;
   int engine = kEngineMmaSync;  // layer-2 engine of the staged inference entry points
+  int train_prec = kTrainFp32;   // FP32 CUDA-core or BF16 tensor-core training kernel
   StagedPlan* plan = nullptr;  // device copy of the proposal plan
   int n_net = 1;
   cudaStream_t stream = nullptr;
@@ -874,6 +883,21 @@ struct ising_nn {
   __nv_bfloat16 *wbf = nullptr, *w2t = nullptr;
   int64_t step = 0;
 };
+
+namespace {
+
+// loss and gradients of count windows with the trainer's kernel
+cudaError_t launch_train(ising_nn* n, const int8_t* dev_windows, int count) {
+  if (n->train_prec == kTrainBf16Tc)
+    return nn_train_tc(dev_windows, count, n->plan, n->n_net, n->p, n->g, n->loss, sms_of_current(),
+                       n->stream);
+  const int grid = std::max(1, std::min(count * n->n_net, sms_of_current()));
+  k_nn_train<<<grid, kThreads, train_smem(), n->stream>>>(dev_windows, count, n->B, n->plan, n->p, n->g,
+                                                          n->loss);
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -962,10 +986,7 @@ int ising_nn_loss_grad(ising_nn* n, const int8_t* dev_windows, int count, float*
   if (!n || !dev_windows || count <= 0) return nfail(ISING_EINVAL, "bad arguments");
   NTRY(cudaMemsetAsync(n->g, 0, kNParams * 4, n->stream));
   NTRY(cudaMemsetAsync(n->loss, 0, 4, n->stream));
-  const int grid = std::max(1, std::min(count * n->n_net, sms_of_current()));
-  k_nn_train<<<grid, kThreads, train_smem(), n->stream>>>(dev_windows, count, n->B, n->plan, n->p,
-                                                          n->g, n->loss);
-  NTRY(cudaGetLastError());
+  NTRY(launch_train(n, dev_windows, count));
   if (loss) NTRY(cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
   if (host_grads) NTRY(cudaMemcpyAsync(host_grads, n->g, kNParams * 4, cudaMemcpyDeviceToHost, n->stream));
   NTRY(cudaStreamSynchronize(n->stream));
@@ -977,10 +998,7 @@ int ising_nn_train_step(ising_nn* n, const int8_t* dev_windows, int count, float
   if (!n || !dev_windows || count <= 0 || !(lr >= 0.f)) return nfail(ISING_EINVAL, "bad arguments");
   NTRY(cudaMemsetAsync(n->g, 0, kNParams * 4, n->stream));
   NTRY(cudaMemsetAsync(n->loss, 0, 4, n->stream));
-  const int grid = std::max(1, std::min(count * n->n_net, sms_of_current()));
-  k_nn_train<<<grid, kThreads, train_smem(), n->stream>>>(dev_windows, count, n->B, n->plan, n->p,
-                                                          n->g, n->loss);
-  NTRY(cudaGetLastError());
+  NTRY(launch_train(n, dev_windows, count));
   n->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
@@ -1016,6 +1034,15 @@ int ising_nn_set_proposal(ising_nn* n, int kind) {
     return nfail(ISING_EINVAL, "proposal kind must be ISING_PROPOSAL_ONESHOT or ISING_PROPOSAL_STAGED");
   NTRY(nn_upload_plan(n->B, kind, &n->plan, &n->n_net, n->stream));
   n->kind = kind;
+  set_last_error("");
+  return ISING_OK;
+}
+
+int ising_nn_set_train_precision(ising_nn* n, int precision) {
+  if (!n) return nfail(ISING_EINVAL, "null trainer");
+  if (precision != kTrainFp32 && precision != kTrainBf16Tc)
+    return nfail(ISING_EINVAL, "precision must be ISING_NN_TRAIN_FP32 or ISING_NN_TRAIN_BF16_TC");
+  n->train_prec = precision;
   set_last_error("");
   return ISING_OK;
 }

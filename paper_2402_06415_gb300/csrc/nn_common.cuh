@@ -143,6 +143,15 @@ cudaError_t nn_stage_logits(const int8_t* windows, int count, const StagedPlan* 
 cudaError_t nn_log_q(const int8_t* windows, int count, const StagedPlan* d_plan, float beta, int engine,
                      const __nv_bfloat16* wbf, const __nv_bfloat16* w2t, float* out,
                      cudaStream_t s);
+// Loss and gradient sums (added to grads, loss) of count windows on the tensor
+// cores (nn_train_tc.cu): the objective of the FP32 training kernel with BF16
+// operands and FP32 accumulation in the 32 -> 32 convolution; at most `grid`
+// CTAs (one per SM fits).
+cudaError_t nn_train_tc(const int8_t* windows, int count, const StagedPlan* d_plan, int n_net,
+                        const float* params, float* grads, float* loss, int grid, cudaStream_t s);
+// training precisions
+constexpr int kTrainFp32 = 0;
+constexpr int kTrainBf16Tc = 1;
 
 }  // namespace nnc
 }  // namespace ising

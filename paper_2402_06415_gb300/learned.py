@@ -50,12 +50,14 @@ class Trainer:
     """FP32 master weights + Adam on the GPU (ising_nn_*)."""
 
     def __init__(self, block: int = 16, seed: int = 0, params: dict | None = None, stream=None,
-                 proposal: int = B.ISING_PROPOSAL_ONESHOT):
+                 proposal: int = B.ISING_PROPOSAL_ONESHOT, precision: int = B.ISING_NN_TRAIN_FP32):
         self.block = block
         self.proposal = proposal
         self.h = B.ising_nn_create(block, B.NN_CHANNELS, stream)
         if proposal != B.ISING_PROPOSAL_ONESHOT:
             B.ising_nn_set_proposal(self.h, proposal)
+        if precision != B.ISING_NN_TRAIN_FP32:
+            B.ising_nn_set_train_precision(self.h, precision)
         if params is None:
             params = init_params(seed)
         B.ising_nn_set_params(self.h, B.nn_flatten(params))

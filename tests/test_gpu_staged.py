@@ -150,6 +150,66 @@ def test_loss_and_gradients_elementwise(torch, proposal):
         assert err.max() < 1e-4, (k, err.max())
 
 
+@pytest.mark.parametrize("proposal,block", [(ising.ISING_PROPOSAL_ONESHOT, 4), (STAGED, 4), (STAGED, 16)])
+def test_tensor_core_gradients_elementwise(torch, proposal, block):
+    """The BF16 tensor-core training kernel, element by element, against the
+    float64 objective whose 32 -> 32 convolution operands are rounded to BF16
+    at the same points (oracle/staged.py, bf16_operands): what is left is FP32
+    accumulation order and the odd operand rounded from an FP32 instead of a
+    float64 value, so every element within 5e-3 of max(|ref|, a tenth of the
+    tensor's largest element), the loss within 1e-4.  Against the exact
+    objective the layer-3 gradients (one rounded operand) stay within 2e-2 of
+    the tensor's largest element; the layer-2 and layer-1 gradients also see
+    ReLU masks that the rounding flips near zero (oracle pin in
+    test_oracle_staged.py) and are checked against the exact objective only to
+    0.15 of the largest element."""
+    p32 = learned.init_params(seed=6)
+    for k in p32:
+        p32[k] = p32[k] + (0.05 * np.random.default_rng(60).standard_normal(p32[k].shape)).astype(np.float32)
+    wins = _windows(64, 24, block, seed=7)
+    with learned.Trainer(block, params=p32, proposal=proposal) as tr:
+        ising.ising_nn_set_train_precision(tr.h, ising.ISING_NN_TRAIN_BF16_TC)
+        d = torch.from_numpy(wins).cuda()
+        loss, g = ising.ising_nn_loss_grad(tr.h, d, len(wins))
+        with pytest.raises(ising.IsingError):
+            ising.ising_nn_set_train_precision(tr.h, 2)
+    p64 = {k: v.astype(np.float64) for k, v in p32.items()}
+    st = None if proposal == STAGED else [("net", [(i, j) for i in range(block) for j in range(block)])]
+    emu_loss, emu_g = staged.staged_loss_and_grads(p64, wins, block, st, bf16_operands=True)
+    ex_loss, ex_g = staged.staged_loss_and_grads(p64, wins, block, st)
+    assert abs(loss - emu_loss) < 1e-4 * abs(emu_loss), (loss, emu_loss)
+    G = ising.nn_unflatten(g)
+    for k in emu_g:
+        ref = emu_g[k]
+        scale = 0.1 * np.abs(ref).max()
+        err = np.abs(G[k] - ref) / np.maximum(np.abs(ref), scale)
+        assert err.max() < 5e-3, (k, err.max())
+        assert np.abs(ref).max() > 0
+    for k in ex_g:
+        ref = ex_g[k]
+        d = np.abs(G[k] - ref).max() / np.abs(ref).max()
+        assert d < (2e-2 if k in ("W3", "b3") else 0.15), (k, d)
+
+
+def test_tensor_core_training_lowers_loss_and_accepts(torch):
+    """Training the staged 16 x 16 proposal with the tensor-core kernel lowers
+    the loss like the FP32 kernel, and the trained network's block moves are
+    accepted on a beta_c lattice."""
+    wins = learned.generate_windows([64, 128], BETA_C, 3072, 16, seed=71, thermalise=2000, thin=40)
+    with learned.Trainer(16, seed=72, proposal=STAGED) as tr:
+        ising.ising_nn_set_train_precision(tr.h, ising.ISING_NN_TRAIN_BF16_TC)
+        losses = tr.fit(wins, epochs=2, batch=256, lr=2e-3, seed=73)
+        blob = tr.blob()
+    assert np.mean(losses[-5:]) < 0.9 * np.mean(losses[:5])
+    with ising.Lattice(64, BETA_C, ising.ISING_LAYOUT_BITS, seed=74) as lat:
+        ising.ising_nn_load(lat.ctx, blob)
+        ising.ising_set_proposal(lat.ctx, STAGED)
+        lat.sweep(2000, 0)
+        ising.ising_block_pass(lat.ctx, 200, 16)
+        p, a = ising.ising_block_stats(lat.ctx)
+    assert a > 0.01 * p, (a, p)
+
+
 def test_adam_and_bf16_export_match_reference(torch):
     """Three Adam steps with the oracle's gradients on both sides: FP32 master
     weights vs the float64 Adam, and the BF16 blob = bf16(master weights)."""

@@ -276,3 +276,28 @@ def test_adam_two_steps_by_hand():
     p2 = p1 - 0.1 * (0.02 / 0.19) / (math.sqrt(3.1225e-4 / 1.999e-3) + 1e-8)
     assert abs(p["w"][0] - p2) < 1e-14
     assert abs(p2 - 0.8733663) < 1e-7
+
+
+def test_bf16_operand_objective_within_rounding_of_exact():
+    """The BF16-operand objective (the tensor-core training path's rounding
+    points) differs from the exact one and stays close to it: the loss to
+    1e-3 relative, the layer-3 gradients (one rounded operand, h2) to 1e-2 of
+    the tensor's largest element, the others to 0.15 of it.  The loose bound is
+    not rounding noise: rounding W2 and h1 moves z2, which flips the ReLU mask
+    of the odd position near zero, and each flip changes whole terms of the
+    layer-2 and layer-1 gradients."""
+    B = 4
+    p = cnn.init_params(seed=3)
+    rng = np.random.default_rng(4)
+    wins = rng.choice(np.array([-1, 1], dtype=np.int8), size=(12, B + 2, B + 2))
+    l0, g0 = staged.staged_loss_and_grads(p, wins, B)
+    l1, g1 = staged.staged_loss_and_grads(p, wins, B, bf16_operands=True)
+    assert l1 != l0 and abs(l1 - l0) < 1e-3 * abs(l0)
+    for k in g0:
+        assert not np.array_equal(g1[k], g0[k])
+        d = np.abs(g1[k] - g0[k]).max() / np.abs(g0[k]).max()
+        assert d < (1e-2 if k in ("W3", "b3") else 0.15), (k, d)
+    # rounding is the identity on values that are already BF16: with every
+    # rounded quantity exact (zero network), both objectives agree exactly
+    z = {k: np.zeros_like(v) for k, v in p.items()}
+    assert staged.staged_loss_and_grads(z, wins, B)[0] == staged.staged_loss_and_grads(z, wins, B, bf16_operands=True)[0]
