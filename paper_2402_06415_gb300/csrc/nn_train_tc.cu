@@ -36,8 +36,11 @@ struct TrainTcSmem {
   __nv_bfloat16 h2[kGrid * kCP];   // layer-2 output, zero outside the frame
   __nv_bfloat16 gz2[kGrid * kCP];  // dL/dz2, zero outside the frame
   float gz1[kMaxFrame * kC];       // dL/dz1 (FP32, frame positions)
-  float w1[kC * 18], b1[kC], b2[kC], w3[kC * 9 + 1];
-  float x0[kMaxFrame], x1[kMaxFrame], g3[kMaxFrame];
+  float w1t[18 * kC];              // W1 as [ci * 9 + t][c] (lanes = channels)
+  float b1[kC], b2[kC], w3[kC * 9 + 1];
+  float xg[2][kGrid];              // input channels on the padded grid (zero border)
+  float g3g[kGrid];                // dL/dz3 on the padded grid (zero outside the sites)
+  float red[8][kC * 18 + kC];      // per-warp layer-1 gradient sums, reduced at the end
   float tgt[kMaxB * kMaxB];
   uint8_t tmask[kMaxB * kMaxB];
   int16_t sites[kMaxB * kMaxB];    // frame positions of this sample's loss terms
@@ -143,7 +146,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
     S.w2r[c * kK2P + t * kC + o] = v;
   }
   for (int i = threadIdx.x; i < kC * 18; i += blockDim.x) {
-    S.w1[i] = params[kOffW1 + i];
+    const int c = i / 18, j = i % 18;  // W1[c][ci][t], j = ci * 9 + t
+    S.w1t[j * kC + c] = params[kOffW1 + i];
     S.gw1[i] = 0.f;
   }
   for (int i = threadIdx.x; i < kC * 9 + 1; i += blockDim.x) S.w3[i] = params[kOffW3 + i];
@@ -158,6 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
   // grids start (and outside the frame stay) zero
   const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
   for (int i = threadIdx.x; i < kGrid * kCP; i += blockDim.x) S.h1[i] = S.h2[i] = S.gz2[i] = z;
+  for (int i = threadIdx.x; i < kGrid; i += blockDim.x) S.xg[0][i] = S.xg[1][i] = S.g3g[i] = 0.f;
   __syncthreads();
 
   // dW2 accumulators: warp w owns tap w (both 16-row o tiles x four 8-column c
@@ -167,6 +172,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
   for (int a = 0; a < 9; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) dw[a][b] = 0.f;
+  // layer-1 gradient sums of this thread: channel o = lane, positions of
+  // warp `warp`'s slice, all samples (j = ci * 9 + t; gw1s[18] = bias)
+  float gw1s[19];
+#pragma unroll
+  for (int j = 0; j < 19; ++j) gw1s[j] = 0.f;
   float my_loss = 0.f;
   const int n_net = plan->n_net;
   const int total = n * n_net;
@@ -177,9 +187,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
     for (int i = threadIdx.x; i < FF; i += blockDim.x) {
       const int fy = i / F, fx = i - (i / F) * F;
       const bool e = known_at(*plan, fy, fx, stage);
-      S.x0[i] = e ? (float)win[i] : 0.f;
-      S.x1[i] = e ? 1.f : 0.f;
-      S.g3[i] = 0.f;
+      const int gi = grid_of_frame(i, F);
+      S.xg[0][gi] = e ? (float)win[i] : 0.f;
+      S.xg[1][gi] = e ? 1.f : 0.f;
+      S.g3g[gi] = 0.f;
       if (fy >= 1 && fy <= B && fx >= 1 && fx <= B) {
         const int ii = (fy - 1) * B + fx - 1;
         S.tgt[ii] = win[i] > 0 ? 1.f : 0.f;
@@ -193,17 +204,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
       S.n_sites = m;
     }
     __syncthreads();
-    // layer 1 (FP32): h1 = relu(W1 * x + b1), stored in BF16
+    // layer 1 (FP32): h1 = relu(W1 * x + b1), stored in BF16; lanes = channels
     for (int i = threadIdx.x; i < FF * kC; i += blockDim.x) {
-      const int c = i % kC, p = i / kC, fy = p / F, fx = p - (p / F) * F;
+      const int c = i % kC, p = i / kC, gp = grid_of_frame(p, F);
       float zz = S.b1[c];
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int yy = fy + t / 3 - 1, xx = fx + t % 3 - 1;
-        if (yy < 0 || yy >= F || xx < 0 || xx >= F) continue;
-        zz += S.w1[(c * 2) * 9 + t] * S.x0[yy * F + xx] + S.w1[(c * 2 + 1) * 9 + t] * S.x1[yy * F + xx];
-      }
-      S.h1[grid_of_frame(p, F) * kCP + c] = __float2bfloat16_rn(fmaxf(zz, 0.f));
+      for (int t = 0; t < 9; ++t)
+        zz += S.w1t[t * kC + c] * S.xg[0][gp + tap_off(t)] + S.w1t[(9 + t) * kC + c] * S.xg[1][gp + tap_off(t)];
+      S.h1[gp * kCP + c] = __float2bfloat16_rn(fmaxf(zz, 0.f));
     }
     __syncthreads();
     // layer 2 forward on the tensor cores
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
         const int fy = p / F, fx = p - (p / F) * F;
         const float y = S.tgt[(fy - 1) * B + fx - 1];
         my_loss += (fmaxf(zz, 0.f) - zz * y + log1pf(expf(-fabsf(zz)))) * invn;
-        S.g3[p] = (1.f / (1.f + expf(-zz)) - y) * invn;
+        S.g3g[grid_of_frame(p, F)] = (1.f / (1.f + expf(-zz)) - y) * invn;
       }
     }
     __syncthreads();
@@ -243,12 +251,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
     for (int i = threadIdx.x; i < kC * 9 + 1; i += blockDim.x) {
       float s = 0.f;
       for (int j = 0; j < S.n_sites; ++j) {
-        const int p = S.sites[j];
+        const int gp = grid_of_frame(S.sites[j], F);
         if (i == kC * 9) {
-          s += S.g3[p];
+          s += S.g3g[gp];
         } else {
           const int c = i / 9, t = i % 9;
-          s += S.g3[p] * bf(S.h2[(grid_of_frame(p, F) + tap_off(t)) * kCP + c]);
+          s += S.g3g[gp] * bf(S.h2[(gp + tap_off(t)) * kCP + c]);
         }
       }
       if (i == kC * 9)
@@ -257,15 +265,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
         S.gw3[i] += s;
     }
     for (int i = threadIdx.x; i < FF * kC; i += blockDim.x) {
-      const int c = i % kC, q = i / kC, qy = q / F, qx = q - (q / F) * F;
+      const int c = i % kC, q = i / kC, gqp = grid_of_frame(q, F);
       float s = 0.f;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int py = qy - (t / 3 - 1), px = qx - (t % 3 - 1);
-        if (py < 0 || py >= F || px < 0 || px >= F) continue;
-        s += S.w3[c * 9 + t] * S.g3[py * F + px];
-      }
-      const int gq = grid_of_frame(q, F) * kCP + c;
+      for (int t = 0; t < 9; ++t) s += S.w3[c * 9 + t] * S.g3g[gqp - tap_off(t)];
+      const int gq = gqp * kCP + c;
       const float v = bf(S.h2[gq]) > 0.f ? s : 0.f;
       S.gz2[gq] = __float2bfloat16_rn(v);
       S.gz1[q * kC + c] = v;  // FP32 dL/dz2 for the bias sum below (overwritten by g1)
@@ -325,24 +329,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
       S.gz1[q * kC + c] = bf(S.h1[grid_of_frame(q, F) * kCP + c]) > 0.f ? v : 0.f;
     });
     __syncthreads();
-    // layer 1 gradients (FP32)
-    for (int i = threadIdx.x; i < kC * 18 + kC; i += blockDim.x) {
-      float s = 0.f;
-      if (i >= kC * 18) {
-        const int o = i - kC * 18;
-        for (int p = 0; p < FF; ++p) s += S.gz1[p * kC + o];
-        S.gb1[o] += s;
-      } else {
-        const int o = i / 18, ci = (i / 9) % 2, t = i % 9, dy = t / 3 - 1, dx = t % 3 - 1;
-        const float* xin = ci == 0 ? S.x0 : S.x1;
-        for (int p = 0; p < FF; ++p) {
-          const float g = S.gz1[p * kC + o];
-          if (g == 0.f) continue;
-          const int fy = p / F + dy, fx = p - (p / F) * F + dx;
-          if (fy < 0 || fy >= F || fx < 0 || fx >= F) continue;
-          s += g * xin[fy * F + fx];
-        }
-        S.gw1[i] += s;
+    // layer 1 gradients (FP32): lane = output channel, warp = a slice of the
+    // positions, sums kept in registers over all samples
+    for (int p = warp; p < FF; p += (int)(blockDim.x >> 5)) {
+      const float g = S.gz1[p * kC + lane];
+      const int gp = grid_of_frame(p, F);
+      gw1s[18] += g;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        gw1s[t] += g * S.xg[0][gp + tap_off(t)];
+        gw1s[9 + t] += g * S.xg[1][gp + tap_off(t)];
       }
     }
     __syncthreads();
@@ -363,6 +359,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_train_tc(const int8_t* __res
       for (int nt = 0; nt < 4; ++nt) put(dw[mt * 4 + nt], warp, mt, nt);
     put(dw[8], 8, warp >> 2, warp & 3);
   }
+  // layer-1 sums: reduce the warps' partial sums in shared memory
+#pragma unroll
+  for (int j = 0; j < 18; ++j) S.red[warp][lane * 18 + j] = gw1s[j];
+  S.red[warp][kC * 18 + lane] = gw1s[18];
+  __syncthreads();
+  for (int i = threadIdx.x; i < kC * 18 + kC; i += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += S.red[w][i];
+    if (i < kC * 18)
+      S.gw1[i] += s;  // [o][ci * 9 + t] = W1[o][ci][t]
+    else
+      S.gb1[i - kC * 18] += s;
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < kC * 18; i += blockDim.x)
     if (S.gw1[i] != 0.f) atomicAdd(&grads[kOffW1 + i], S.gw1[i]);
   for (int i = threadIdx.x; i < kC * 9; i += blockDim.x)
