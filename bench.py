@@ -142,7 +142,10 @@ def measured_peaks() -> dict:
 # ncu capture of the current kernel (profiles/k_tiled32_bits_L16384_k2.md):
 # 33.70 MB read + 0.66 MB written per launch (2 sweeps) after ncu's cache flush.
 # Reported only for that shape; any other shape reports null.
-NCU_TRAFFIC = {"shape": (2, 228, 64), "bytes_per_launch": 33.70e6 + 0.66e6}
+# DRAM bytes (read + write) per launch of the sweep kernel from one ncu capture
+# of the current kernel, by launch shape (sweeps per launch, row strips, words
+# per tile row); profiles/k_tiled32_bits_L16384_k2.md has the commands
+NCU_TRAFFIC = {(3, 228, 64): 33.75e6 + 0.575e6, (2, 228, 64): 33.70e6 + 0.448e6}
 # Algorithmic work of the bit-sliced, lazily evaluated acceptance test per
 # 32-site word, by the pipe it issues to.  ALU pipe (three-input logic, shifts):
 # neighbour classes + funnel shift + update 13; per Philox4x32-10 block
@@ -371,8 +374,7 @@ def run_ours(args):
     roofline = {
         "bound": "alu", "achieved": alu_gops, "peak": peak, "unit": "Gop/s",
         "frac": alu_gops / peak,
-        "traffic": (NCU_TRAFFIC["bytes_per_launch"]
-                    if (cfg["k"], cfg["tile_rows"], cfg["tile_words"]) == NCU_TRAFFIC["shape"] else None),
+        "traffic": NCU_TRAFFIC.get((cfg["k"], cfg["tile_rows"], cfg["tile_words"])),
         "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
                    if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
         "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 83.2 ALU-pipe and "
