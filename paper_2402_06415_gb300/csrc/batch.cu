@@ -141,6 +141,34 @@ __device__ __forceinline__ void planes_tab(uint32_t g, uint32_t t, uint32_t rep,
   }
 }
 
+// planes_tab<B0, B1, false> for two independent words (two replicas' masks),
+// with both Philox chains in flight.
+template <int B0, int B1>
+__device__ __forceinline__ void planes_tab2(uint32_t ga, uint32_t gb, uint32_t t, uint32_t repa, uint32_t repb,
+                                            uint32_t colour, const uint32_t (&rk0)[10], const uint32_t (&rk1)[10],
+                                            const uint2* __restrict__ tma, const uint2* __restrict__ tmb,
+                                            uint32_t& Da, uint32_t clsa, uint32_t& acca,
+                                            uint32_t& Db, uint32_t clsb, uint32_t& accb) {
+#pragma unroll
+  for (int b = B0; b < B1; ++b) {
+    const uint32_t cw = ctr_w(kTagMet, colour, b);
+    const uint4 ra = philox10_rk(make_uint4(ga, t, repa, cw), rk0, rk1);
+    const uint4 rb = philox10_rk(make_uint4(gb, t, repb, cw), rk0, rk1);
+    const uint32_t pa[4] = {ra.x, ra.y, ra.z, ra.w};
+    const uint32_t pb[4] = {rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint2 ma = tma[4 * b + q], mb = tmb[4 * b + q];
+      const uint32_t ta = (clsa & ma.x) | (~clsa & ma.y);
+      const uint32_t tb = (clsb & mb.x) | (~clsb & mb.y);
+      acca |= Da & ta & ~pa[q];
+      accb |= Db & tb & ~pb[q];
+      Da &= ~(ta ^ pa[q]);
+      Db &= ~(tb ^ pb[q]);
+    }
+  }
+}
+
 // One round (ns sweeps from global sweep t0) of one item, in shared memory.
 struct ItemSmem {
   uint2 tm[kMaxRepPerItem][32];  // per replica and plane: threshold masks (t4, t8)
@@ -188,41 +216,67 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
     const uint32_t t = t0 + (uint32_t)s;
     for (int c = 0; c < 2; ++c) {
       const int cur = c;  // queue counter of this half sweep (the other is reset meanwhile)
-      for (int b0 = threadIdx.x & ~31; b0 < words; b0 += blockDim.x) {
-        const int idx = b0 + lane;
-        const bool active = idx < words;
-        const int qq = active ? (int)fdiv((uint32_t)idx, fplane) : 0;
-        const int rem = active ? idx - qq * plane : 0;
-        const int y = (int)fdiv((uint32_t)rem, fwc), w = rem - y * Wc;
-        uint32_t* So = sm + qq * per_rep + c * plane;
-        const uint32_t* Sn = sm + qq * per_rep + (1 - c) * plane;
-        const uint32_t* rm = Sn + y * Wc;
-        const uint32_t sv = So[y * Wc + w];
-        const uint32_t up = Sn[(y == 0 ? L - 1 : y - 1) * Wc + w];
-        const uint32_t dn = Sn[(y == L - 1 ? 0 : y + 1) * Wc + w];
-        const uint32_t mid = rm[w];
-        const uint32_t side = side_word_bf(rm, w, Wc, n, (y + c) & 1);
-        const uint32_t valid = active ? valid_mask_bf(w, Wc, n) : 0u;
-        const Classes k = classify(sv, up, dn, mid, side);
-        uint32_t D = (k.one | k.zero) & valid, acc = 0;
-        const uint32_t g = (uint32_t)(y * Wc + w), rep = (uint32_t)(r0 + qq);
-        planes_tab<0, 2, false>(g, t, rep, (uint32_t)c, d.rk0, d.rk1, X.tm[qq], D, k.one, acc);
-        if (active) So[y * Wc + w] = sv ^ ((k.ge2 & valid) | acc);
-        bool ovf = false;
-        if (D != 0u) {  // D != 0 only for active words
-          const int slot = atomicAdd(&X.q_n[cur], 1);
-          if (slot < kQueueCap) {
-            X.q_idx[slot] = (uint32_t)idx;
-            X.q_d[slot] = D;
-            X.q_cls[slot] = k.one;
-          } else {
-            ovf = true;
-          }
+      auto enq = [&](int idx, uint32_t D, uint32_t cls) {  // returns true if the queue was full
+        if (D == 0u) return false;
+        const int slot = atomicAdd(&X.q_n[cur], 1);
+        if (slot < kQueueCap) {
+          X.q_idx[slot] = (uint32_t)idx;
+          X.q_d[slot] = D;
+          X.q_cls[slot] = cls;
+          return false;
         }
-        if (__any_sync(0xffffffffu, ovf)) {  // queue full: finish in place
-          uint32_t e = ovf ? D : 0u, acc2 = 0;
-          planes_tab<2, 8, true>(g, t, rep, (uint32_t)c, d.rk0, d.rk1, X.tm[qq], e, k.one, acc2);
-          if (ovf) So[y * Wc + w] ^= acc2;
+        return true;
+      };
+      // two words per lane (idx and idx + blockDim): their Philox chains
+      // interleave; 80 registers keep three CTAs of 256 threads per SM
+      for (int b0 = threadIdx.x & ~31; b0 < words; b0 += 2 * blockDim.x) {
+        int idxs[2];
+        bool act[2];
+        uint32_t* So[2];
+        uint32_t sv[2], D[2], cls[2], acc[2], ge2[2], valid[2], g[2], rep[2];
+        int q[2], pos[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int idx = b0 + h * blockDim.x + lane;
+          idxs[h] = idx;
+          act[h] = idx < words;
+          const int qq = act[h] ? (int)fdiv((uint32_t)idx, fplane) : 0;
+          const int rem = act[h] ? idx - qq * plane : 0;
+          const int y = (int)fdiv((uint32_t)rem, fwc), w = rem - y * Wc;
+          So[h] = sm + qq * per_rep + c * plane;
+          const uint32_t* Sn = sm + qq * per_rep + (1 - c) * plane;
+          const uint32_t* rm = Sn + y * Wc;
+          sv[h] = So[h][y * Wc + w];
+          const uint32_t up = Sn[(y == 0 ? L - 1 : y - 1) * Wc + w];
+          const uint32_t dn = Sn[(y == L - 1 ? 0 : y + 1) * Wc + w];
+          const uint32_t mid = rm[w];
+          const uint32_t side = side_word_bf(rm, w, Wc, n, (y + c) & 1);
+          valid[h] = act[h] ? valid_mask_bf(w, Wc, n) : 0u;
+          const Classes k = classify(sv[h], up, dn, mid, side);
+          D[h] = (k.one | k.zero) & valid[h];
+          cls[h] = k.one;
+          ge2[h] = k.ge2;
+          acc[h] = 0;
+          g[h] = (uint32_t)(y * Wc + w);
+          rep[h] = (uint32_t)(r0 + qq);
+          q[h] = qq;
+          pos[h] = y * Wc + w;
+        }
+        planes_tab2<0, 2>(g[0], g[1], t, rep[0], rep[1], (uint32_t)c, d.rk0, d.rk1, X.tm[q[0]], X.tm[q[1]],
+                          D[0], cls[0], acc[0], D[1], cls[1], acc[1]);
+        bool ovf[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (act[h]) So[h][pos[h]] = sv[h] ^ ((ge2[h] & valid[h]) | acc[h]);
+          ovf[h] = enq(idxs[h], D[h], cls[h]);
+        }
+        if (__any_sync(0xffffffffu, ovf[0] || ovf[1])) {  // queue full: finish in place
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t e = ovf[h] ? D[h] : 0u, acc2 = 0;
+            planes_tab<2, 8, true>(g[h], t, rep[h], (uint32_t)c, d.rk0, d.rk1, X.tm[q[h]], e, cls[h], acc2);
+            if (ovf[h]) So[h][pos[h]] ^= acc2;
+          }
         }
       }
       __syncthreads();
@@ -329,7 +383,7 @@ __device__ void exchange_ladder(const BatchDev& d, int l, uint32_t n_step) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_batch(BatchDev d, int n_sweeps) {
+__global__ void __launch_bounds__(256, 3) k_batch(BatchDev d, int n_sweeps) {
   extern __shared__ uint32_t sm[];
   __shared__ uint32_t s_t4[kMaxRepPerItem], s_t8[kMaxRepPerItem];
   __shared__ unsigned int s_anti[kMaxRepPerItem], s_ones[kMaxRepPerItem];
