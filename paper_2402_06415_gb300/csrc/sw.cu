@@ -335,16 +335,32 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_sw_local(const uint32_t* __
 // cluster's coin into mark[] (0 / 1) and leaves its entry alone.
 __global__ void k_sw_resolve(uint32_t* __restrict__ parent, uint8_t* __restrict__ mark, long long N,
                              uint32_t step, RngParams rng) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    if (mark[i] != 2) continue;
-    const uint32_t m = find_root_ro(parent, (uint32_t)i);
-    if (m == (uint32_t)i) {
-      const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
-      const uint32_t w = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
-      mark[i] = (uint8_t)(w >> 31);
-    } else {
-      parent[i] = m;
+  // 16 marks per thread and iteration from one 16-byte load (N is a multiple
+  // of 16 on the tiled path); only the local roots among them do any work
+  const long long n16 = N >> 4;
+  for (long long i16 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i16 < n16;
+       i16 += (long long)gridDim.x * blockDim.x) {
+    const uint4 m4 = reinterpret_cast<const uint4*>(mark)[i16];
+    const uint32_t w[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // bytes equal to 2 are the zero bytes of x; the high bit of each zero byte
+      // of x, exactly (seven-bit sums cannot carry into the next byte)
+      const uint32_t x = w[q] ^ 0x02020202u;
+      uint32_t z = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+      while (z) {
+        const int byte = (__ffs(z) - 1) >> 3;
+        z &= z - 1;
+        const long long i = (i16 << 4) + 4 * q + byte;
+        const uint32_t m = find_root_ro(parent, (uint32_t)i);
+        if (m == (uint32_t)i) {
+          const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
+          const uint32_t wd = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
+          mark[i] = (uint8_t)(wd >> 31);
+        } else {
+          parent[i] = m;
+        }
+      }
     }
   }
 }
@@ -356,9 +372,22 @@ __global__ void k_sw_resolve(uint32_t* __restrict__ parent, uint8_t* __restrict_
 // it to another local root), and every local root now holds its cluster's coin.
 __global__ void k_sw_coin_copy(const uint32_t* __restrict__ parent, uint8_t* __restrict__ mark,
                                long long N) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    if (mark[i] == 2) mark[i] = mark[parent[i]];
+  const long long n16 = N >> 4;  // 16 marks per thread and iteration, as k_sw_resolve
+  for (long long i16 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i16 < n16;
+       i16 += (long long)gridDim.x * blockDim.x) {
+    const uint4 m4 = reinterpret_cast<const uint4*>(mark)[i16];
+    const uint32_t w[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t x = w[q] ^ 0x02020202u;
+      uint32_t z = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+      while (z) {
+        const int byte = (__ffs(z) - 1) >> 3;
+        z &= z - 1;
+        const long long i = (i16 << 4) + 4 * q + byte;
+        mark[i] = mark[parent[i]];
+      }
+    }
   }
 }
 
