@@ -245,17 +245,32 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_sw_local(const uint32_t* __
     }
   }
   __syncthreads();
-  // horizontal runs: one warp per row, four consecutive sites per lane
+  // horizontal runs: one warp per row, four consecutive sites per lane; the
+  // same pass lists the vertical bonds that need a union (warp ballots, one
+  // shared-memory atomic per warp per row)
   {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int ly = warp; ly < kTileY; ly += nwarps) {
       const int base = ly * kTileX + 4 * lane;
+      // this lane's four flag bytes, the byte left of them, and the same in the row below
+      const uint32_t cw = *reinterpret_cast<const uint32_t*>(&st[base]);
+      const uint32_t pb = lane > 0 ? st[base - 1] : 0u;
+      const bool below = ly + 1 < kTileY;
+      const uint32_t dw = below ? *reinterpret_cast<const uint32_t*>(&st[base + kTileX]) : 0u;
+      const uint32_t dpb = (below && lane > 0) ? st[base - 1 + kTileX] : 0u;
       int start[4], last = -1;
+      bool need[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int lx = 4 * lane + k;
-        if (lx == 0 || !(st[base + k - 1] & 2u)) last = lx;
+        const uint32_t own = (cw >> (8 * k)) & 0xffu;
+        const uint32_t left = k == 0 ? pb : (cw >> (8 * (k - 1))) & 0xffu;
+        const uint32_t below_left = k == 0 ? dpb : (dw >> (8 * (k - 1))) & 0xffu;
+        if (lx == 0 || !(left & 2u)) last = lx;
         start[k] = last;
+        // a vertical bond needs a union unless the left neighbour's vertical
+        // bond already joined the same two runs
+        need[k] = (own & 4u) && !(lx > 0 && (left & 6u) == 6u && (below_left & 2u));
       }
       // carry: the last run start of lanes below (inclusive max-scan)
       int carry = last;
@@ -268,37 +283,41 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_sw_local(const uint32_t* __
       if (lane == 0) prev = -1;
 #pragma unroll
       for (int k = 0; k < 4; ++k) lab[base + k] = (uint32_t)(ly * kTileX + (start[k] >= 0 ? start[k] : prev));
-    }
-  }
-  __syncthreads();
-  // vertical bonds unite runs: list the bonds that need a union (warp ballot,
-  // one shared-memory atomic per warp), then unite with every lane busy
-  {
-    const int lane = threadIdx.x & 31;
-    for (int li = threadIdx.x; li < kTileSites; li += blockDim.x) {
-      const int lx = li % kTileX;
-      // skipped: no vertical bond, or the left neighbour's vertical bond
-      // already joined the same two runs
-      const bool need = (st[li] & 4u) && !(lx > 0 && (st[li - 1] & 6u) == 6u && (st[li - 1 + kTileX] & 2u));
-      const uint32_t m = __ballot_sync(0xffffffffu, need);
-      int base = 0;
-      if (lane == 0 && m) base = atomicAdd(&s_nu, __popc(m));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (need) {
-        const int slot = base + __popc(m & ((1u << lane) - 1u));
-        if (slot < kUnionCap)
-          ulist[slot] = (uint16_t)li;
-        else
-          sunite(lab, (uint32_t)(li + kTileX), (uint32_t)li);
+      uint32_t m[4];
+      int total = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        m[k] = __ballot_sync(0xffffffffu, need[k]);
+        total += __popc(m[k]);
+      }
+      int slot0 = 0;
+      if (lane == 0 && total) slot0 = atomicAdd(&s_nu, total);
+      slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+      const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (need[k]) {
+          const int slot = slot0 + __popc(m[k] & lt);
+          if (slot < kUnionCap) ulist[slot] = (uint16_t)(base + k);
+        }
+        slot0 += __popc(m[k]);
       }
     }
   }
   __syncthreads();
-  {
-    const int nu = min(s_nu, kUnionCap);
-    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+  // vertical bonds unite runs, every lane of a warp on a listed bond; if the
+  // list overflowed (not at beta_c tile sizes), every needed bond is united
+  // by a scan instead (uniting listed bonds twice is harmless)
+  if (s_nu <= kUnionCap) {
+    for (int i = threadIdx.x; i < s_nu; i += blockDim.x) {
       const uint32_t li = ulist[i];
       sunite(lab, li + kTileX, li);
+    }
+  } else {
+    for (int li = threadIdx.x; li < kTileSites; li += blockDim.x) {
+      const int lx = li % kTileX;
+      if ((st[li] & 4u) && !(lx > 0 && (st[li - 1] & 6u) == 6u && (st[li - 1 + kTileX] & 2u)))
+        sunite(lab, (uint32_t)(li + kTileX), (uint32_t)li);
     }
   }
   __syncthreads();

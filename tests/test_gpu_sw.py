@@ -95,6 +95,31 @@ def test_sw_tiled_labelling_bit_exact(L, beta):
     assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
 
 
+@pytest.mark.parametrize("pattern", ["stripes", "stripes_noise"])
+def test_sw_tiled_union_list_overflow(pattern):
+    """Vertical stripes at large beta: every vertical bond is active and no
+    horizontal one, so each tile has ~8000 vertical bonds that need a union, more
+    than its union list holds; the tile kernel then unites by a scan.  One step
+    (the stripes themselves) and a few more from the noisier start."""
+    L, beta, seed = 2048, 50.0, 77
+    s = np.empty((L, L), dtype=np.int8)
+    s[:, 0::2] = 1
+    s[:, 1::2] = -1
+    n = 1
+    if pattern == "stripes_noise":
+        flip = np.random.default_rng(78).random((L, L)) < 0.02
+        s[flip] *= -1
+        n = 3
+    with ising.Lattice(L, beta, seed=seed) as lat:
+        lat.set_spins(s)
+        lat.sw_step(n, 1)
+        got = lat.spins()
+        E, M = lat.series(n)
+    E_ref, M_ref, _ = oracle.sw_steps(s, beta, seed, n)
+    assert np.array_equal(got, s)
+    assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
+
+
 def test_sw_large_lattice_one_step():
     """A 4096^2 lattice (16.8 M sites, clusters spanning many CTAs) at beta_c."""
     L, seed = 4096, 5
