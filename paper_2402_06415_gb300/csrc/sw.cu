@@ -352,35 +352,60 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_sw_local(const uint32_t* __
 // After the edge unions: every local root (mark 2) finds its final root; a
 // non-final one stores it (its own entry only), a final root draws its
 // cluster's coin into mark[] (0 / 1) and leaves its entry alone.
-__global__ void k_sw_resolve(uint32_t* __restrict__ parent, uint8_t* __restrict__ mark, long long N,
-                             uint32_t step, RngParams rng) {
-  // 16 marks per thread and iteration from one 16-byte load (N is a multiple
-  // of 16 on the tiled path); only the local roots among them do any work
+__global__ void __launch_bounds__(256) k_sw_resolve(uint32_t* __restrict__ parent, uint8_t* __restrict__ mark,
+                                                    long long N, uint32_t step, RngParams rng) {
+  // A warp takes 512 sites at a time (16 marks per lane from one 16-byte load;
+  // N is a multiple of 16 on the tiled path), lists their local roots in shared
+  // memory (prefix sum over the lanes), then resolves the list with every lane
+  // busy instead of each lane walking its own roots while the others wait.
+  __shared__ uint32_t roots[8][512];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long n16 = N >> 4;
-  for (long long i16 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i16 < n16;
-       i16 += (long long)gridDim.x * blockDim.x) {
-    const uint4 m4 = reinterpret_cast<const uint4*>(mark)[i16];
-    const uint32_t w[4] = {m4.x, m4.y, m4.z, m4.w};
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; c0 < n16; c0 += warps * 32) {
+    const long long i16 = c0 + lane;
+    uint32_t z[4] = {0u, 0u, 0u, 0u};
+    int cnt = 0;
+    if (i16 < n16) {
+      const uint4 m4 = reinterpret_cast<const uint4*>(mark)[i16];
+      const uint32_t w[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      // bytes equal to 2 are the zero bytes of x; the high bit of each zero byte
-      // of x, exactly (seven-bit sums cannot carry into the next byte)
-      const uint32_t x = w[q] ^ 0x02020202u;
-      uint32_t z = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
-      while (z) {
-        const int byte = (__ffs(z) - 1) >> 3;
-        z &= z - 1;
-        const long long i = (i16 << 4) + 4 * q + byte;
-        const uint32_t m = find_root_ro(parent, (uint32_t)i);
-        if (m == (uint32_t)i) {
-          const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
-          const uint32_t wd = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
-          mark[i] = (uint8_t)(wd >> 31);
-        } else {
-          parent[i] = m;
-        }
+      for (int q = 0; q < 4; ++q) {
+        // bytes equal to 2 are the zero bytes of x; the high bit of each zero
+        // byte of x, exactly (seven-bit sums cannot carry into the next byte)
+        const uint32_t x = w[q] ^ 0x02020202u;
+        z[q] = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+        cnt += __popc(z[q]);
       }
     }
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = incl - cnt;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      while (z[q]) {
+        const int byte = (__ffs(z[q]) - 1) >> 3;
+        z[q] &= z[q] - 1;
+        roots[warp][pos++] = (uint32_t)((i16 << 4) + 4 * q + byte);
+      }
+    __syncwarp();
+    for (int e = lane; e < total; e += 32) {
+      const uint32_t i = roots[warp][e];
+      const uint32_t m = find_root_ro(parent, i);
+      if (m == i) {
+        const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
+        const uint32_t wd = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
+        mark[i] = (uint8_t)(wd >> 31);
+      } else {
+        parent[i] = m;
+      }
+    }
+    __syncwarp();
   }
 }
 
