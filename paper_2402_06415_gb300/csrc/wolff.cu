@@ -209,13 +209,59 @@ __device__ __forceinline__ uint32_t find_root_ro(const uint32_t* parent, uint32_
 // Gated on need_label: every site that may head a subtree (mark 2 after the
 // tiled labelling; every site otherwise) stores its final root in its own
 // entry, so parent[parent[i]] is every site's root afterwards.
-__global__ void k_wolff_resolve(uint32_t* __restrict__ parent, const uint8_t* __restrict__ mark, long long N,
-                                bool tiled, const WolffCtl* __restrict__ ctl) {
+__global__ void __launch_bounds__(256) k_wolff_resolve(uint32_t* __restrict__ parent,
+                                                       const uint8_t* __restrict__ mark, long long N, bool tiled,
+                                                       const WolffCtl* __restrict__ ctl) {
   if (ctl->need_label == 0) return;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    if (tiled && mark[i] != 2) continue;
-    parent[i] = find_root_ro(parent, (uint32_t)i);
+  if (!tiled) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+      parent[i] = find_root_ro(parent, (uint32_t)i);
+    return;
+  }
+  // tiled path: a warp lists the local roots (mark 2) of 512 sites in shared
+  // memory (16 marks per lane from one 16-byte load, prefix sum over the
+  // lanes) and walks them with every lane busy
+  __shared__ uint32_t roots[8][512];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long n16 = N >> 4;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; c0 < n16; c0 += warps * 32) {
+    const long long i16 = c0 + lane;
+    uint32_t z[4] = {0u, 0u, 0u, 0u};
+    int cnt = 0;
+    if (i16 < n16) {
+      const uint4 m4 = reinterpret_cast<const uint4*>(mark)[i16];
+      const uint32_t w[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // the high bit of each byte equal to 2, exactly
+        const uint32_t x = w[q] ^ 0x02020202u;
+        z[q] = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+        cnt += __popc(z[q]);
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = incl - cnt;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      while (z[q]) {
+        const int byte = (__ffs(z[q]) - 1) >> 3;
+        z[q] &= z[q] - 1;
+        roots[warp][pos++] = (uint32_t)((i16 << 4) + 4 * q + byte);
+      }
+    __syncwarp();
+    for (int e = lane; e < total; e += 32) {
+      const uint32_t i = roots[warp][e];
+      parent[i] = find_root_ro(parent, i);
+    }
+    __syncwarp();
   }
 }
 
