@@ -1090,6 +1090,41 @@ def run_train(args):
     return 0
 
 
+def run_xy_step(args):
+    """Time per sweep of the XY model (T = 0.85) on one L x L lattice in one
+    precision (--xy-L, --xy-precision), one launch per half sweep: W warm-up
+    sweeps (2 W launches of k_xy_half) then K timed sweeps with one CUDA-event
+    pair."""
+    import torch
+
+    import paper_2402_06415_gb300 as ising
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    L, beta, prec = args.xy_L, 1.0 / 0.85, args.xy_precision
+    with ising.XY(L, beta, prec, stream=stream, seed=2) as x:
+        x.set_mode(1)
+        x.sweep(args.warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.sweep(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "XY sweep time", "value": ms * 1e3, "unit": "us/sweep", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "data": "synthetic", "dtype": "f%d" % prec,
+            "config": {"workload": "XY model at T = 0.85 on a %d^2 lattice, FP%d, one launch per half sweep"
+                                   % (L, prec)},
+            "site_updates_per_ns": L * L / (ms * 1e6)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_quad(args):
     """The paper's quadripartition workloads (Fig. 5b/5d) for the Ising model:
     time per sweep on the square-octagon lattice (J1 = J2 = 1) and on the square
@@ -1275,6 +1310,9 @@ def main(argv=None):
     ap.add_argument("--precision-sweeps", type=int, default=20000)
     ap.add_argument("--precision-L", type=int, default=1024)
     ap.add_argument("--sw-L", type=int, default=16384, help="lattice size of --workload sw_step")
+    ap.add_argument("--xy-L", type=int, default=4096, help="lattice size of --workload xy_step")
+    ap.add_argument("--xy-precision", type=int, choices=[32, 64], default=32,
+                    help="precision of --workload xy_step")
     ap.add_argument("--pass-L", type=int, default=256, help="lattice size of --workload staged_pass")
     ap.add_argument("--train-precision", choices=sorted(TRAIN_PRECISIONS), default="bf16_tc",
                     help="training kernel of the learned workloads")
@@ -1283,7 +1321,7 @@ def main(argv=None):
     ap.add_argument("--nn-engine", choices=sorted(NN_ENGINES), default="mma_sync",
                     help="engine of the staged proposal's second convolution (staged_pass)")
     ap.add_argument("--workload", choices=["plain", "batch", "learned", "batch_learned", "xy", "sw", "quad",
-                                           "xy_precision", "sw_step", "staged_pass", "train"],
+                                           "xy_precision", "sw_step", "staged_pass", "train", "xy_step"],
                     default="plain",
                     help="plain: one L=16384 lattice (default); batch: 4096 replicas with "
                          "parallel tempering")
@@ -1317,6 +1355,8 @@ def main(argv=None):
         return run_staged_pass(args)
     if args.workload == "train":
         return run_train(args)
+    if args.workload == "xy_step":
+        return run_xy_step(args)
     return run_ours(args)
 
 
