@@ -444,21 +444,43 @@ __global__ void k_sw_coin_copy(const uint32_t* __restrict__ parent, uint8_t* __r
 __global__ void __launch_bounds__(256) k_sw_apply2(uint32_t* __restrict__ planes, int L, int Wc,
                                                    const uint32_t* __restrict__ parent,
                                                    const uint8_t* __restrict__ coin) {
+  // four segments per warp and iteration, their loads in flight together; lanes
+  // 0..3 apply the flip masks of segments 0..3
+  constexpr int kU = 4;
   const int lane = threadIdx.x & 31;
   const uint32_t segs = (uint32_t)L * (uint32_t)Wc;  // 64-site row segments
   const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t i = warp0; i < segs; i += nwarps) {
-    const uint32_t y = i / (uint32_t)Wc, w = i - y * (uint32_t)Wc;
-    const uint2 pr = __ldg(reinterpret_cast<const uint2*>(parent + (size_t)y * L + 64 * w + 2 * lane));
-    const bool f0 = __ldg(&coin[pr.x]) != 0;  // x even: colour y & 1
-    const bool f1 = __ldg(&coin[pr.y]) != 0;  // x odd: the other colour
-    const uint32_t m0 = __ballot_sync(0xffffffffu, f0);
-    const uint32_t m1 = __ballot_sync(0xffffffffu, f1);
-    if (lane == 0) {
+  for (uint32_t i0 = warp0 * kU; i0 < segs; i0 += nwarps * kU) {
+    uint2 pr[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t i = i0 + u < segs ? i0 + u : i0;
+      const uint32_t y = i / (uint32_t)Wc, w = i - y * (uint32_t)Wc;
+      pr[u] = __ldg(reinterpret_cast<const uint2*>(parent + (size_t)y * L + 64 * w + 2 * lane));
+    }
+    bool f[kU][2];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      f[u][0] = __ldg(&coin[pr[u].x]) != 0;  // x even: colour y & 1
+      f[u][1] = __ldg(&coin[pr[u].y]) != 0;  // x odd: the other colour
+    }
+    uint32_t mine0 = 0, mine1 = 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t m0 = __ballot_sync(0xffffffffu, f[u][0]);
+      const uint32_t m1 = __ballot_sync(0xffffffffu, f[u][1]);
+      if (lane == u) {
+        mine0 = m0;
+        mine1 = m1;
+      }
+    }
+    const uint32_t i = i0 + (uint32_t)lane;
+    if (lane < kU && i < segs) {
+      const uint32_t y = i / (uint32_t)Wc, w = i - y * (uint32_t)Wc;
       const uint32_t c0 = y & 1u;
-      if (m0) planes[(size_t)c0 * L * Wc + (size_t)y * Wc + w] ^= m0;
-      if (m1) planes[(size_t)(c0 ^ 1u) * L * Wc + (size_t)y * Wc + w] ^= m1;
+      if (mine0) planes[(size_t)c0 * L * Wc + (size_t)y * Wc + w] ^= mine0;
+      if (mine1) planes[(size_t)(c0 ^ 1u) * L * Wc + (size_t)y * Wc + w] ^= mine1;
     }
   }
 }
