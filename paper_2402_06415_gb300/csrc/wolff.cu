@@ -284,23 +284,36 @@ __global__ void __launch_bounds__(256) k_wolff_apply(uint32_t* __restrict__ plan
   const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   uint32_t count = 0;
-  for (uint32_t i = warp0; i < words; i += nwarps) {
-    const int c = (int)fdiv(i, fplane);
-    const uint32_t rem = i - (uint32_t)c * fplane.d;
-    const int y = (int)fdiv(rem, fwc), w = (int)(rem - (uint32_t)y * (uint32_t)Wc);
-    const int j = 32 * w + lane;
-    bool f = false;
-    if (j < n) {
-      const int x = 2 * j + ((y + c) & 1);
-      f = __ldg(&parent[__ldg(&parent[(size_t)y * L + x])]) == root;
+  // four words per warp and iteration, their loads in flight together; lanes
+  // 0..3 apply the masks of words 0..3
+  constexpr int kU = 4;
+  for (uint32_t i0 = warp0 * kU; i0 < words; i0 += nwarps * kU) {
+    uint32_t p1[kU];
+    bool ok[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t i = i0 + u < words ? i0 + u : i0;
+      const int c = (int)fdiv(i, fplane);
+      const uint32_t rem = i - (uint32_t)c * fplane.d;
+      const int y = (int)fdiv(rem, fwc), w = (int)(rem - (uint32_t)y * (uint32_t)Wc);
+      const int j = 32 * w + lane;
+      ok[u] = j < n && i0 + u < words;
+      const int x = 2 * (ok[u] ? j : 0) + ((y + c) & 1);
+      p1[u] = __ldg(&parent[(size_t)y * L + x]);
     }
-    const uint32_t mask = __ballot_sync(0xffffffffu, f);
-    if (lane == 0 && mask) {
-      planes[i] ^= mask;
-      count += __popc(mask);
+    uint32_t mine = 0;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const bool f = ok[u] && __ldg(&parent[p1[u]]) == root;
+      const uint32_t mask = __ballot_sync(0xffffffffu, f);
+      if (lane == u) mine = mask;
+    }
+    if (lane < kU && mine) {
+      planes[i0 + lane] ^= mine;
+      count += __popc(mine);
     }
   }
-  if (lane == 0 && count) atomicAdd(&s_count, count);
+  if (count) atomicAdd(&s_count, count);  // lanes 0..3 hold counts
   __syncthreads();
   if (threadIdx.x == 0 && s_count) {
     atomicAdd(&ctl->last_size, s_count);
