@@ -394,15 +394,33 @@ __global__ void __launch_bounds__(256) k_sw_resolve(uint32_t* __restrict__ paren
         roots[warp][pos++] = (uint32_t)((i16 << 4) + 4 * q + byte);
       }
     __syncwarp();
-    for (int e = lane; e < total; e += 32) {
-      const uint32_t i = roots[warp][e];
-      const uint32_t m = find_root_ro(parent, i);
-      if (m == i) {
-        const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
-        const uint32_t wd = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
-        mark[i] = (uint8_t)(wd >> 31);
-      } else {
-        parent[i] = m;
+    // two walks per lane, interleaved so that both loads are in flight
+    for (int e = lane; e < total; e += 64) {
+      const bool two = e + 32 < total;
+      const uint32_t ia = roots[warp][e], ib = two ? roots[warp][e + 32] : ia;
+      uint32_t a = ia, b = ib;
+      bool da = false, db = !two;
+      while (!(da && db)) {
+        if (!da) {
+          const uint32_t p = __ldcg(&parent[a]);
+          if (p == a) da = true; else a = p;
+        }
+        if (!db) {
+          const uint32_t p = __ldcg(&parent[b]);
+          if (p == b) db = true; else b = p;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        const uint32_t i = h ? ib : ia, m = h ? b : a;
+        if (m == i) {
+          const uint4 r = philox10_rk(make_uint4(m >> 2, step, rng.replica, kTagSWFlip << 16), rng.rk0, rng.rk1);
+          const uint32_t wd = (m & 3) == 0 ? r.x : ((m & 3) == 1 ? r.y : ((m & 3) == 2 ? r.z : r.w));
+          mark[i] = (uint8_t)(wd >> 31);
+        } else {
+          parent[i] = m;
+        }
       }
     }
     __syncwarp();
