@@ -257,9 +257,24 @@ __global__ void __launch_bounds__(256) k_wolff_resolve(uint32_t* __restrict__ pa
         roots[warp][pos++] = (uint32_t)((i16 << 4) + 4 * q + byte);
       }
     __syncwarp();
-    for (int e = lane; e < total; e += 32) {
-      const uint32_t i = roots[warp][e];
-      parent[i] = find_root_ro(parent, i);
+    // two walks per lane, interleaved so that both loads are in flight
+    for (int e = lane; e < total; e += 64) {
+      const bool two = e + 32 < total;
+      const uint32_t ia = roots[warp][e], ib = two ? roots[warp][e + 32] : ia;
+      uint32_t a = ia, b = ib;
+      bool da = false, db = !two;
+      while (!(da && db)) {
+        if (!da) {
+          const uint32_t p = __ldcg(&parent[a]);
+          if (p == a) da = true; else a = p;
+        }
+        if (!db) {
+          const uint32_t p = __ldcg(&parent[b]);
+          if (p == b) db = true; else b = p;
+        }
+      }
+      parent[ia] = a;
+      if (two) parent[ib] = b;
     }
     __syncwarp();
   }
