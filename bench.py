@@ -138,24 +138,23 @@ def measured_peaks() -> dict:
 # ---------------------------------------------------------------------------
 # roofline model of the dominant kernel
 # ---------------------------------------------------------------------------
-# DRAM bytes (read + write) of one launch of the benchmark kernel shape, from an
-# ncu capture of the current kernel (profiles/k_tiled32_bits_L16384_k2.md):
-# 33.70 MB read + 0.66 MB written per launch (2 sweeps) after ncu's cache flush.
-# Reported only for that shape; any other shape reports null.
 # DRAM bytes (read + write) per launch of the sweep kernel from one ncu capture
 # of the current kernel, by launch shape (sweeps per launch, row strips, words
-# per tile row); profiles/k_tiled32_bits_L16384_k2.md has the commands
-NCU_TRAFFIC = {(3, 228, 64): 33.75e6 + 0.575e6, (2, 228, 64): 33.70e6 + 0.448e6}
+# per tile row); profiles/k_tiled32_bits_L16384.md has the commands.  A shape
+# without a capture reports null.
+NCU_TRAFFIC = {(4, 114, 32): 33.80e6 + 0.581e6, (3, 228, 64): 33.75e6 + 0.616e6,
+               (2, 228, 64): 33.70e6 + 0.562e6}
 # Algorithmic work of the bit-sliced, lazily evaluated acceptance test per
 # 32-site word, by the pipe it issues to.  ALU pipe (three-input logic, shifts):
 # neighbour classes + funnel shift + update 13; per Philox4x32-10 block
-# 10 rounds x 2 three-input XORs = 20, plus 4 planes x 4 logic ops (threshold
-# bit 1, accept 2 -- four inputs: acc | (D & t & ~p) --, still undecided 1) = 16;
-# E[blocks] = 1.95 for independent words: 13 + 1.95 x 36 = 83.2.  FMA pipe: per
-# block 10 rounds x 2 wide integer multiplies = 20, i.e. 39 per word.  Both pipes
-# take 64 lanes per SM per clock, so the ALU pipe binds: per site 83.2 / 32
-# lane-ops.
-ALU_OPS_PER_WORD = 13.0 + 1.95 * 36.0
+# 10 rounds x 2 three-input XORs = 20, plus 4 planes x 3 logic ops (the lane's
+# threshold bit, the borrow of u - T as a majority function, the equality
+# chain) and 1 to merge the block's verdict into (acc, D) = 13;
+# E[blocks] = 1.95 for independent words: 13 + 1.95 x 33 = 77.35.  FMA pipe:
+# per block 10 rounds x 2 wide integer multiplies = 20, i.e. 39 per word.  Both
+# pipes take 64 lanes per SM per clock, so the ALU pipe binds: per site
+# 77.35 / 32 lane-ops.
+ALU_OPS_PER_WORD = 13.0 + 1.95 * 33.0
 FMA_OPS_PER_WORD = 1.95 * 20.0
 ALU_OPS_PER_SITE = ALU_OPS_PER_WORD / 32.0
 ALU_LANES_PER_SM = 64
@@ -377,7 +376,7 @@ def run_ours(args):
         "traffic": NCU_TRAFFIC.get((cfg["k"], cfg["tile_rows"], cfg["tile_words"])),
         "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
                    if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
-        "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 83.2 ALU-pipe and "
+        "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 77.35 ALU-pipe and "
                        "39 FMA-pipe lane-ops per 32-site word, both pipes 64 lanes/SM/clock): "
                        "152 SMs x 64 lanes x median SM clock under load",
         "alu_ceiling_flips_per_ns": 32.0 * peak / ALU_OPS_PER_WORD,

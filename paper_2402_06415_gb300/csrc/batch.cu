@@ -141,32 +141,41 @@ __device__ __forceinline__ void planes_tab(uint32_t g, uint32_t t, uint32_t rep,
   }
 }
 
-// planes_tab<B0, B1, false> for two independent words (two replicas' masks),
-// with both Philox chains in flight.
-template <int B0, int B1>
-__device__ __forceinline__ void planes_tab2(uint32_t ga, uint32_t gb, uint32_t t, uint32_t repa, uint32_t repb,
-                                            uint32_t colour, const uint32_t (&rk0)[10], const uint32_t (&rk1)[10],
-                                            const uint2* __restrict__ tma, const uint2* __restrict__ tmb,
-                                            uint32_t& Da, uint32_t clsa, uint32_t& acca,
-                                            uint32_t& Db, uint32_t clsb, uint32_t& accb) {
+// Planes 0..7 (Philox blocks 0 and 1) of two independent words (two replicas'
+// masks), all drawn, as one strict comparison of the top 8 bits: u_8 < T_8 is
+// the borrow out of the bit-sliced subtraction u_8 - T_8, carried from plane 7
+// up to plane 0 with one majority function per plane, borrow' = maj(~u_k, T_k,
+// borrow); lanes whose 8 bits equal the threshold's stay undecided.  Same
+// (acc, D) as planes_tab<0, 2, false> with one logic operation less per plane;
+// block 1 is drawn first so that one block's planes are live at a time.
+__device__ __forceinline__ void planes8_tab2(uint32_t ga, uint32_t gb, uint32_t t, uint32_t repa, uint32_t repb,
+                                             uint32_t colour, const uint32_t (&rk0)[10], const uint32_t (&rk1)[10],
+                                             const uint2* __restrict__ tma, const uint2* __restrict__ tmb,
+                                             uint32_t& Da, uint32_t clsa, uint32_t& acca,
+                                             uint32_t& Db, uint32_t clsb, uint32_t& accb) {
+  uint32_t bora = 0u, borb = 0u, eqa = Da, eqb = Db;
 #pragma unroll
-  for (int b = B0; b < B1; ++b) {
+  for (int b = 1; b >= 0; --b) {
     const uint32_t cw = ctr_w(kTagMet, colour, b);
     const uint4 ra = philox10_rk(make_uint4(ga, t, repa, cw), rk0, rk1);
     const uint4 rb = philox10_rk(make_uint4(gb, t, repb, cw), rk0, rk1);
     const uint32_t pa[4] = {ra.x, ra.y, ra.z, ra.w};
     const uint32_t pb[4] = {rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 3; q >= 0; --q) {
       const uint2 ma = tma[4 * b + q], mb = tmb[4 * b + q];
       const uint32_t ta = (clsa & ma.x) | (~clsa & ma.y);
       const uint32_t tb = (clsb & mb.x) | (~clsb & mb.y);
-      acca |= Da & ta & ~pa[q];
-      accb |= Db & tb & ~pb[q];
-      Da &= ~(ta ^ pa[q]);
-      Db &= ~(tb ^ pb[q]);
+      bora = (~pa[q] & ta) | (~pa[q] & bora) | (ta & bora);
+      borb = (~pb[q] & tb) | (~pb[q] & borb) | (tb & borb);
+      eqa &= ~(ta ^ pa[q]);
+      eqb &= ~(tb ^ pb[q]);
     }
   }
+  acca |= Da & bora;
+  accb |= Db & borb;
+  Da = eqa;
+  Db = eqb;
 }
 
 // One round (ns sweeps from global sweep t0) of one item, in shared memory.
@@ -262,8 +271,8 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
           q[h] = qq;
           pos[h] = y * Wc + w;
         }
-        planes_tab2<0, 2>(g[0], g[1], t, rep[0], rep[1], (uint32_t)c, d.rk0, d.rk1, X.tm[q[0]], X.tm[q[1]],
-                          D[0], cls[0], acc[0], D[1], cls[1], acc[1]);
+        planes8_tab2(g[0], g[1], t, rep[0], rep[1], (uint32_t)c, d.rk0, d.rk1, X.tm[q[0]], X.tm[q[1]],
+                     D[0], cls[0], acc[0], D[1], cls[1], acc[1]);
         bool ovf[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {

@@ -201,13 +201,58 @@ __device__ __forceinline__ void lazy_planes2(uint32_t ga, uint32_t gb, uint32_t 
   }
 }
 
+// Planes 0..7 (Philox blocks 0 and 1) of one or two words, all evaluated, as
+// one strict comparison of the top 8 bits: u_8 < T_8 is the borrow out of the
+// bit-sliced subtraction u_8 - T_8, carried from plane 7 (the least
+// significant of the eight) up to plane 0 with one majority function per
+// plane, borrow' = maj(~u_k, T_k, borrow); lanes whose 8 bits equal the
+// threshold's stay undecided.  Gives the same (acc, D) as the MSB-first test
+// over the same planes with one logic operation less per plane.  Block 1 is
+// drawn first, so only one block's planes are live at a time.
+template <int NW>
+__device__ __forceinline__ void planes8(const uint32_t (&g)[NW], uint32_t t, uint32_t rep,
+                                        uint32_t colour, const RngParams& rng, uint32_t (&D)[NW],
+                                        const uint32_t (&cls)[NW], uint32_t (&acc)[NW]) {
+  uint32_t bor[NW], eq[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    bor[w] = 0u;
+    eq[w] = D[w];
+  }
+#pragma unroll
+  for (int b = 1; b >= 0; --b) {
+    const uint32_t cw = ctr_w(kTagMet, colour, b);
+    uint4 r[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) r[w] = philox10_rk(make_uint4(g[w], t, rep, cw), rng.rk0, rng.rk1);
+#pragma unroll
+    for (int q = 3; q >= 0; --q) {
+      const int k = 4 * b + q;
+      const uint32_t m4 = rng.tm4[k], m8 = rng.tm8[k];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t p = q == 0 ? r[w].x : q == 1 ? r[w].y : q == 2 ? r[w].z : r[w].w;
+        const uint32_t tm = (cls[w] & m4) | (~cls[w] & m8);  // lane's threshold bit
+        bor[w] = (~p & tm) | (~p & bor[w]) | (tm & bor[w]);
+        eq[w] &= ~(tm ^ p);
+      }
+    }
+  }
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    acc[w] |= D[w] & bor[w];
+    D[w] = eq[w];
+  }
+}
+
 // Tiled sweep with one warp per 32-word tile row segment.  Same tiling, halo
 // and results as k_tiled_bits; differences are for speed only:
 //  * the inner 32*TWW words of a row are updated by TWW warps (lane = word), the
 //    two halo words per row by a separate short pass, so no integer division
 //    or modulo runs per word;
-//  * phase 1 evaluates the first two Philox blocks (8 planes) of every word;
-//    words with lanes still undecided (about 1 in 10) go to a shared-memory
+//  * phase 1 evaluates the first two Philox blocks (8 planes) of every word as
+//    one 8-bit comparison (planes8); words with lanes still undecided (about 1
+//    in 10) go to a shared-memory
 //    queue, and phase 2 finishes them with all lanes of a warp busy on queued
 //    words, instead of every warp waiting for its slowest word;
 //  * per-sweep observables are summed in shared memory, not registers.
@@ -303,10 +348,12 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
                                      : ((mid >> 1) | (Sn[r * SP + col + 1] << 31));
         const Classes k = classify(s, up, dn, mid, side);
         const uint32_t valid = active ? 0xffffffffu : 0u;
-        uint32_t D = (k.one | k.zero) & valid, acc = 0;
         const uint32_t cls = k.one;
         const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
-        lazy_planes<0, 2>(g, t, rng.replica, c, rng, D, cls, acc);
+        uint32_t Dv[1] = {(k.one | k.zero) & valid}, accv[1] = {0u};
+        const uint32_t gv[1] = {g}, clsv[1] = {cls};
+        planes8<1>(gv, t, rng.replica, c, rng, Dv, clsv, accv);
+        const uint32_t D = Dv[0], acc = accv[0];
         bool ovf = false;
         if (active) {
           So[r * SP + col] = s ^ ((k.ge2 & valid) | acc);
@@ -358,13 +405,15 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
         }
         const Classes ka = classify(sa, u0, m1, m0, side_a);
         const Classes kb = classify(sb, m0, d1, m1, side_b);
-        uint32_t Da = ka.one | ka.zero, Db = kb.one | kb.zero, acca = 0, accb = 0;
         const int gya = grow(r);
         const int gyb = gya + 1 == L ? 0 : gya + 1;
         const uint32_t gw = (uint32_t)(w0 + col - 4);  // inner column: no wrap
         const uint32_t ga = (uint32_t)gya * (uint32_t)Wc + gw;
         const uint32_t gb = (uint32_t)gyb * (uint32_t)Wc + gw;
-        lazy_planes2<0, 2>(ga, gb, t, rng.replica, c, rng, Da, ka.one, acca, Db, kb.one, accb);
+        uint32_t Dv[2] = {ka.one | ka.zero, kb.one | kb.zero}, accv[2] = {0u, 0u};
+        const uint32_t gv[2] = {ga, gb}, clsv[2] = {ka.one, kb.one};
+        planes8<2>(gv, t, rng.replica, c, rng, Dv, clsv, accv);
+        const uint32_t Da = Dv[0], Db = Dv[1], acca = accv[0], accb = accv[1];
         So[r * SP + col] = sa ^ (ka.ge2 | acca);
         So[(r + 1) * SP + col] = sb ^ (kb.ge2 | accb);
         const bool ovfa = Da != 0u && !enqueue(r, col, Da, ka.one);
