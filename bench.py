@@ -142,19 +142,20 @@ def measured_peaks() -> dict:
 # of the current kernel, by launch shape (sweeps per launch, row strips, words
 # per tile row); profiles/k_tiled32_bits_L16384.md has the commands.  A shape
 # without a capture reports null.
-NCU_TRAFFIC = {(4, 114, 32): 33.80e6 + 0.581e6, (3, 228, 64): 33.75e6 + 0.616e6,
-               (2, 228, 64): 33.70e6 + 0.562e6}
+NCU_TRAFFIC = {(4, 114, 32): 33.80e6 + 0.519e6, (3, 114, 32): 33.74e6 + 0.550e6,
+               (4, 76, 32): 33.80e6 + 0.280e6, (3, 228, 64): 33.75e6 + 0.530e6,
+               (2, 228, 64): 33.69e6 + 0.469e6}
 # Algorithmic work of the bit-sliced, lazily evaluated acceptance test per
 # 32-site word, by the pipe it issues to.  ALU pipe (three-input logic, shifts):
-# neighbour classes + funnel shift + update 13; per Philox4x32-10 block
-# 10 rounds x 2 three-input XORs = 20, plus 4 planes x 3 logic ops (the lane's
-# threshold bit, the borrow of u - T as a majority function, the equality
-# chain) and 1 to merge the block's verdict into (acc, D) = 13;
-# E[blocks] = 1.95 for independent words: 13 + 1.95 x 33 = 77.35.  FMA pipe:
-# per block 10 rounds x 2 wide integer multiplies = 20, i.e. 39 per word.  Both
-# pipes take 64 lanes per SM per clock, so the ALU pipe binds: per site
-# 77.35 / 32 lane-ops.
-ALU_OPS_PER_WORD = 13.0 + 1.95 * 33.0
+# neighbour classes as two half adders (half sums, carries, ge2 and the class
+# mask: 7), funnel shift 1, update 1 = 9; per Philox4x32-10 block 10 rounds x 2
+# three-input XORs = 20, plus 4 planes x 3 logic ops (the lane's threshold bit,
+# the borrow of u - T as a majority function, the equality chain) and 1 to merge
+# the block's verdict into (acc, D) = 13; E[blocks] = 1.95 for independent
+# words: 9 + 1.95 x 33 = 73.35.  FMA pipe: per block 10 rounds x 2 wide integer
+# multiplies = 20, i.e. 39 per word.  Both pipes take 64 lanes per SM per
+# clock, so the ALU pipe binds: per site 73.35 / 32 lane-ops.
+ALU_OPS_PER_WORD = 9.0 + 1.95 * 33.0
 FMA_OPS_PER_WORD = 1.95 * 20.0
 ALU_OPS_PER_SITE = ALU_OPS_PER_WORD / 32.0
 ALU_LANES_PER_SM = 64
@@ -376,7 +377,7 @@ def run_ours(args):
         "traffic": NCU_TRAFFIC.get((cfg["k"], cfg["tile_rows"], cfg["tile_words"])),
         "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
                    if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
-        "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 77.35 ALU-pipe and "
+        "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 73.35 ALU-pipe and "
                        "39 FMA-pipe lane-ops per 32-site word, both pipes 64 lanes/SM/clock): "
                        "152 SMs x 64 lanes x median SM clock under load",
         "alu_ceiling_flips_per_ns": 32.0 * peak / ALU_OPS_PER_WORD,

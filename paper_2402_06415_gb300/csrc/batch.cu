@@ -131,13 +131,18 @@ __device__ __forceinline__ void planes_tab(uint32_t g, uint32_t t, uint32_t rep,
     if (VOTE && !__any_sync(0xffffffffu, D != 0u)) break;
     const uint4 r = philox10_rk(make_uint4(g, t, rep, ctr_w(kTagMet, colour, b)), rk0, rk1);
     const uint32_t p[4] = {r.x, r.y, r.z, r.w};
+    // the block's 4 planes as one 4-bit comparison (borrow of u - T from the
+    // block's last plane up, equality chain), then merged into (acc, D)
+    uint32_t bor = 0u, eq = D;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 3; q >= 0; --q) {
       const uint2 m = tm[4 * b + q];
       const uint32_t tk = (cls & m.x) | (~cls & m.y);  // lane's threshold bit
-      acc |= D & tk & ~p[q];
-      D &= ~(tk ^ p[q]);
+      bor = (~p[q] & tk) | (~p[q] & bor) | (tk & bor);
+      eq &= ~(tk ^ p[q]);
     }
+    acc |= D & bor;
+    D = eq;
   }
 }
 
@@ -261,9 +266,9 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
           const uint32_t mid = rm[w];
           const uint32_t side = side_word_bf(rm, w, Wc, n, (y + c) & 1);
           valid[h] = act[h] ? valid_mask_bf(w, Wc, n) : 0u;
-          const Classes k = classify(sv[h], up, dn, mid, side);
-          D[h] = (k.one | k.zero) & valid[h];
-          cls[h] = k.one;
+          const HalfClasses k = classify_hs(sv[h], up ^ dn, up, dn, mid, side);
+          D[h] = ~k.ge2 & valid[h];
+          cls[h] = k.cls;
           ge2[h] = k.ge2;
           acc[h] = 0;
           g[h] = (uint32_t)(y * Wc + w);

@@ -76,6 +76,24 @@ __device__ __forceinline__ Classes classify(uint32_t s, uint32_t n1, uint32_t n2
   return k;
 }
 
+// Neighbour classes of a word s in the form the plane test needs, with the
+// four neighbours taken as two pairs (m, n) and (x, y): ge2 = at least two
+// antiparallel neighbours (always flips), cls = 1 on lanes with exactly one
+// and 0 on lanes with none (lanes of ge2 are never tested, so their cls is
+// free).  Per pair the antiparallel count is a half sum plus a carry, where s
+// cancels from the half sum (h = (s^m) ^ (s^n) = m ^ n), so a word pair that
+// shares a neighbour pair computes h1 once.
+struct HalfClasses {
+  uint32_t ge2, cls;
+};
+__device__ __forceinline__ HalfClasses classify_hs(uint32_t s, uint32_t h1, uint32_t m, uint32_t n,
+                                                   uint32_t x, uint32_t y) {
+  const uint32_t c1 = (s ^ m) & (s ^ n);
+  const uint32_t h2 = x ^ y;
+  const uint32_t c2 = (s ^ x) & (s ^ y);
+  return {c1 | c2 | (h1 & h2), h1 | h2};
+}
+
 // Bit-serial "u < T" for the undecided lanes D over the 4 planes of one Philox
 // block (planes 4b .. 4b+3, plane 0 = most significant bit of u).  For lanes
 // of class `one` T = t4, for class `zero` T = t8.  Lanes whose plane bit equals

@@ -161,14 +161,19 @@ __device__ __forceinline__ void lazy_planes(uint32_t g, uint32_t t, uint32_t rep
     if (!__any_sync(0xffffffffu, D != 0u)) break;
     const uint4 r = philox10_rk(make_uint4(g, t, rep, ctr_w(kTagMet, colour, b)), rng.rk0, rng.rk1);
     const uint32_t p[4] = {r.x, r.y, r.z, r.w};
+    // the block's 4 planes as one 4-bit comparison (borrow of u - T from the
+    // block's last plane up, equality chain), then merged into (acc, D)
+    uint32_t bor = 0u, eq = D;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 3; q >= 0; --q) {
       const int k = 4 * b + q;
       const uint32_t m4 = rng.tm4[k], m8 = rng.tm8[k];
       const uint32_t tm = (cls & m4) | (~cls & m8);  // lane's threshold bit
-      acc |= D & tm & ~p[q];                          // u bit 0 < T bit 1: accept
-      D &= ~(tm ^ p[q]);                              // equal bits: still undecided
+      bor = (~p[q] & tm) | (~p[q] & bor) | (tm & bor);
+      eq &= ~(tm ^ p[q]);
     }
+    acc |= D & bor;
+    D = eq;
   }
 }
 
@@ -187,17 +192,22 @@ __device__ __forceinline__ void lazy_planes2(uint32_t ga, uint32_t gb, uint32_t 
     const uint4 rb = philox10_rk(make_uint4(gb, t, rep, cw), rng.rk0, rng.rk1);
     const uint32_t pa[4] = {ra.x, ra.y, ra.z, ra.w};
     const uint32_t pb[4] = {rb.x, rb.y, rb.z, rb.w};
+    uint32_t bora = 0u, borb = 0u, eqa = Da, eqb = Db;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 3; q >= 0; --q) {
       const int k = 4 * b + q;
       const uint32_t m4 = rng.tm4[k], m8 = rng.tm8[k];
       const uint32_t ta = (clsa & m4) | (~clsa & m8);
       const uint32_t tb = (clsb & m4) | (~clsb & m8);
-      acca |= Da & ta & ~pa[q];
-      accb |= Db & tb & ~pb[q];
-      Da &= ~(ta ^ pa[q]);
-      Db &= ~(tb ^ pb[q]);
+      bora = (~pa[q] & ta) | (~pa[q] & bora) | (ta & bora);
+      borb = (~pb[q] & tb) | (~pb[q] & borb) | (tb & borb);
+      eqa &= ~(ta ^ pa[q]);
+      eqb &= ~(tb ^ pb[q]);
     }
+    acca |= Da & bora;
+    accb |= Db & borb;
+    Da = eqa;
+    Db = eqb;
   }
 }
 
@@ -346,11 +356,11 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
         const int o = (y0 + r + c) & 1;
         const uint32_t side = o == 0 ? ((mid << 1) | (Sn[r * SP + col - 1] >> 31))
                                      : ((mid >> 1) | (Sn[r * SP + col + 1] << 31));
-        const Classes k = classify(s, up, dn, mid, side);
+        const HalfClasses k = classify_hs(s, up ^ dn, up, dn, mid, side);
         const uint32_t valid = active ? 0xffffffffu : 0u;
-        const uint32_t cls = k.one;
+        const uint32_t cls = k.cls;
         const uint32_t g = (uint32_t)grow(r) * (uint32_t)Wc + (uint32_t)gcol(col);
-        uint32_t Dv[1] = {(k.one | k.zero) & valid}, accv[1] = {0u};
+        uint32_t Dv[1] = {~k.ge2 & valid}, accv[1] = {0u};
         const uint32_t gv[1] = {g}, clsv[1] = {cls};
         planes8<1>(gv, t, rng.replica, c, rng, Dv, clsv, accv);
         const uint32_t D = Dv[0], acc = accv[0];
@@ -403,24 +413,26 @@ __global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restr
           side_a = (m0 >> 1) | (Sn[r * SP + col + 1] << 31);
           side_b = (m1 << 1) | (Sn[(r + 1) * SP + col - 1] >> 31);
         }
-        const Classes ka = classify(sa, u0, m1, m0, side_a);
-        const Classes kb = classify(sb, m0, d1, m1, side_b);
+        // both words have rows r and r+1 of the other colour as neighbours
+        const uint32_t h01 = m0 ^ m1;
+        const HalfClasses ka = classify_hs(sa, h01, m0, m1, u0, side_a);
+        const HalfClasses kb = classify_hs(sb, h01, m0, m1, d1, side_b);
         const int gya = grow(r);
         const int gyb = gya + 1 == L ? 0 : gya + 1;
         const uint32_t gw = (uint32_t)(w0 + col - 4);  // inner column: no wrap
         const uint32_t ga = (uint32_t)gya * (uint32_t)Wc + gw;
         const uint32_t gb = (uint32_t)gyb * (uint32_t)Wc + gw;
-        uint32_t Dv[2] = {ka.one | ka.zero, kb.one | kb.zero}, accv[2] = {0u, 0u};
-        const uint32_t gv[2] = {ga, gb}, clsv[2] = {ka.one, kb.one};
+        uint32_t Dv[2] = {~ka.ge2, ~kb.ge2}, accv[2] = {0u, 0u};
+        const uint32_t gv[2] = {ga, gb}, clsv[2] = {ka.cls, kb.cls};
         planes8<2>(gv, t, rng.replica, c, rng, Dv, clsv, accv);
         const uint32_t Da = Dv[0], Db = Dv[1], acca = accv[0], accb = accv[1];
         So[r * SP + col] = sa ^ (ka.ge2 | acca);
         So[(r + 1) * SP + col] = sb ^ (kb.ge2 | accb);
-        const bool ovfa = Da != 0u && !enqueue(r, col, Da, ka.one);
-        const bool ovfb = Db != 0u && !enqueue(r + 1, col, Db, kb.one);
+        const bool ovfa = Da != 0u && !enqueue(r, col, Da, ka.cls);
+        const bool ovfb = Db != 0u && !enqueue(r + 1, col, Db, kb.cls);
         if (__any_sync(0xffffffffu, ovfa || ovfb)) {  // queue full: finish in place
           uint32_t ea = ovfa ? Da : 0u, eb = ovfb ? Db : 0u, xa = 0, xb = 0;
-          lazy_planes2<2, 8>(ga, gb, t, rng.replica, c, rng, ea, ka.one, xa, eb, kb.one, xb);
+          lazy_planes2<2, 8>(ga, gb, t, rng.replica, c, rng, ea, ka.cls, xa, eb, kb.cls, xb);
           if (ovfa) So[r * SP + col] ^= xa;
           if (ovfb) So[(r + 1) * SP + col] ^= xb;
         }
