@@ -225,7 +225,9 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
   // replicas.)
   const int lane = threadIdx.x & 31;
   const int words = nr * plane;
+  const int half = plane / 2, pairs = nr * half;  // word pairs (rows 2 yy, 2 yy + 1)
   const FastDiv fplane = make_fastdiv((uint32_t)plane), fwc = make_fastdiv((uint32_t)Wc);
+  const FastDiv fhalf = make_fastdiv((uint32_t)half);
   for (int s = 0; s < ns; ++s) {
     const uint32_t t = t0 + (uint32_t)s;
     for (int c = 0; c < 2; ++c) {
@@ -241,56 +243,50 @@ __device__ void run_item(const BatchDev& d, int item, uint32_t t0, int ns, bool 
         }
         return true;
       };
-      // two words per lane (idx and idx + blockDim): their Philox chains
-      // interleave; 80 registers keep three CTAs of 256 threads per SM
-      for (int b0 = threadIdx.x & ~31; b0 < words; b0 += 2 * blockDim.x) {
-        int idxs[2];
-        bool act[2];
-        uint32_t* So[2];
-        uint32_t sv[2], D[2], cls[2], acc[2], ge2[2], valid[2], g[2], rep[2];
-        int q[2], pos[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int idx = b0 + h * blockDim.x + lane;
-          idxs[h] = idx;
-          act[h] = idx < words;
-          const int qq = act[h] ? (int)fdiv((uint32_t)idx, fplane) : 0;
-          const int rem = act[h] ? idx - qq * plane : 0;
-          const int y = (int)fdiv((uint32_t)rem, fwc), w = rem - y * Wc;
-          So[h] = sm + qq * per_rep + c * plane;
-          const uint32_t* Sn = sm + qq * per_rep + (1 - c) * plane;
-          const uint32_t* rm = Sn + y * Wc;
-          sv[h] = So[h][y * Wc + w];
-          const uint32_t up = Sn[(y == 0 ? L - 1 : y - 1) * Wc + w];
-          const uint32_t dn = Sn[(y == L - 1 ? 0 : y + 1) * Wc + w];
-          const uint32_t mid = rm[w];
-          const uint32_t side = side_word_bf(rm, w, Wc, n, (y + c) & 1);
-          valid[h] = act[h] ? valid_mask_bf(w, Wc, n) : 0u;
-          const HalfClasses k = classify_hs(sv[h], up ^ dn, up, dn, mid, side);
-          D[h] = ~k.ge2 & valid[h];
-          cls[h] = k.cls;
-          ge2[h] = k.ge2;
-          acc[h] = 0;
-          g[h] = (uint32_t)(y * Wc + w);
-          rep[h] = (uint32_t)(r0 + qq);
-          q[h] = qq;
-          pos[h] = y * Wc + w;
+      // two vertically adjacent words of one replica per lane (rows 2 yy and
+      // 2 yy + 1; L is even): they share the other colour's rows 2 yy, 2 yy + 1
+      // as neighbours (and the half sum of that pair), the replica and the
+      // index division, and their two Philox chains interleave; 80 registers
+      // keep three CTAs of 256 threads per SM
+      for (int p0 = threadIdx.x & ~31; p0 < pairs; p0 += blockDim.x) {
+        const int p = p0 + lane;
+        const bool act = p < pairs;
+        const int qq = act ? (int)fdiv((uint32_t)p, fhalf) : 0;
+        const int rem = act ? p - qq * half : 0;
+        const int yy = (int)fdiv((uint32_t)rem, fwc), w = rem - yy * Wc;
+        const int ya = 2 * yy;
+        uint32_t* So = sm + qq * per_rep + c * plane;
+        const uint32_t* Sn = sm + qq * per_rep + (1 - c) * plane;
+        const uint32_t* rowa = Sn + ya * Wc;  // other colour, rows ya and ya + 1
+        const uint32_t* rowb = rowa + Wc;
+        const int pa = ya * Wc + w, pb = pa + Wc;
+        const uint32_t sa = So[pa], sb = So[pb];
+        const uint32_t u0 = Sn[(ya == 0 ? L - 1 : ya - 1) * Wc + w];
+        const uint32_t m0 = rowa[w], m1 = rowb[w];
+        const uint32_t d1 = Sn[(ya + 2 == L ? 0 : ya + 2) * Wc + w];
+        // x-offset (y + c) & 1: c for the even row ya, the other for ya + 1
+        const uint32_t side_a = side_word_bf(rowa, w, Wc, n, c);
+        const uint32_t side_b = side_word_bf(rowb, w, Wc, n, c ^ 1);
+        const uint32_t valid = act ? valid_mask_bf(w, Wc, n) : 0u;
+        const uint32_t h01 = m0 ^ m1;
+        const HalfClasses ka = classify_hs(sa, h01, m0, m1, u0, side_a);
+        const HalfClasses kb = classify_hs(sb, h01, m0, m1, d1, side_b);
+        uint32_t Da = ~ka.ge2 & valid, Db = ~kb.ge2 & valid, acca = 0, accb = 0;
+        const uint32_t rep = (uint32_t)(r0 + qq);
+        planes8_tab2((uint32_t)pa, (uint32_t)pb, t, rep, rep, (uint32_t)c, d.rk0, d.rk1, X.tm[qq], X.tm[qq],
+                     Da, ka.cls, acca, Db, kb.cls, accb);
+        if (act) {
+          So[pa] = sa ^ ((ka.ge2 & valid) | acca);
+          So[pb] = sb ^ ((kb.ge2 & valid) | accb);
         }
-        planes8_tab2(g[0], g[1], t, rep[0], rep[1], (uint32_t)c, d.rk0, d.rk1, X.tm[q[0]], X.tm[q[1]],
-                     D[0], cls[0], acc[0], D[1], cls[1], acc[1]);
-        bool ovf[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (act[h]) So[h][pos[h]] = sv[h] ^ ((ge2[h] & valid[h]) | acc[h]);
-          ovf[h] = enq(idxs[h], D[h], cls[h]);
-        }
-        if (__any_sync(0xffffffffu, ovf[0] || ovf[1])) {  // queue full: finish in place
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t e = ovf[h] ? D[h] : 0u, acc2 = 0;
-            planes_tab<2, 8, true>(g[h], t, rep[h], (uint32_t)c, d.rk0, d.rk1, X.tm[q[h]], e, cls[h], acc2);
-            if (ovf[h]) So[h][pos[h]] ^= acc2;
-          }
+        const bool ovfa = enq(qq * plane + pa, Da, ka.cls);
+        const bool ovfb = enq(qq * plane + pb, Db, kb.cls);
+        if (__any_sync(0xffffffffu, ovfa || ovfb)) {  // queue full: finish in place
+          uint32_t ea = ovfa ? Da : 0u, eb = ovfb ? Db : 0u, xa = 0, xb = 0;
+          planes_tab<2, 8, true>((uint32_t)pa, t, rep, (uint32_t)c, d.rk0, d.rk1, X.tm[qq], ea, ka.cls, xa);
+          planes_tab<2, 8, true>((uint32_t)pb, t, rep, (uint32_t)c, d.rk0, d.rk1, X.tm[qq], eb, kb.cls, xb);
+          if (ovfa) So[pa] ^= xa;
+          if (ovfb) So[pb] ^= xb;
         }
       }
       __syncthreads();
