@@ -143,8 +143,17 @@ def measured_peaks() -> dict:
 # per tile row); profiles/k_tiled32_bits_L16384.md has the commands.  A shape
 # without a capture reports null.
 NCU_TRAFFIC = {(4, 114, 32): 33.80e6 + 0.519e6, (3, 114, 32): 33.74e6 + 0.550e6,
-               (4, 76, 32): 33.80e6 + 0.280e6, (3, 228, 64): 33.75e6 + 0.530e6,
+               (4, 76, 32): 33.80e6 + 0.336e6, (3, 228, 64): 33.75e6 + 0.530e6,
                (2, 228, 64): 33.69e6 + 0.469e6}
+
+
+def tiled32_ctas_per_sm(L: int, k: int, n_ty: int, tile_words: int) -> int:
+    """Register-budget variant the library launches for a tiled shape: 3 when
+    three CTAs' shared memory fits an SM (228 KiB; dynamic tile + ~9.3 KB static
+    queue + 1 KiB reserved per CTA), else 2 (the variant with up to 128 registers)."""
+    ty_max = -(-L // n_ty)
+    per_cta = 2 * (ty_max + 4 * k) * (tile_words + 8) * 4 + 9296 + 1024
+    return 3 if 3 * per_cta <= 228 * 1024 else 2
 # Algorithmic work of the bit-sliced, lazily evaluated acceptance test per
 # 32-site word, by the pipe it issues to.  ALU pipe (three-input logic, shifts):
 # neighbour classes as two half adders (half sums, carries, ge2 and the class
@@ -375,7 +384,9 @@ def run_ours(args):
         "bound": "alu", "achieved": alu_gops, "peak": peak, "unit": "Gop/s",
         "frac": alu_gops / peak,
         "traffic": NCU_TRAFFIC.get((cfg["k"], cfg["tile_rows"], cfg["tile_words"])),
-        "kernel": ("k_tiled32_bits<%d,%d>" % (cfg["k"], cfg["tile_words"] // 32)
+        "kernel": ("k_tiled32_bits<%d,%d,%d>" % (cfg["k"], cfg["tile_words"] // 32,
+                                                 tiled32_ctas_per_sm(L, cfg["k"], cfg["tile_rows"],
+                                                                     cfg["tile_words"]))
                    if cfg["tile_words"] in (32, 64) else "k_tiled_bits<%d>" % cfg["k"]),
         "peak_source": "ALU pipe (the binding pipe of the algorithmic mix: 73.35 ALU-pipe and "
                        "39 FMA-pipe lane-ops per 32-site word, both pipes 64 lanes/SM/clock): "

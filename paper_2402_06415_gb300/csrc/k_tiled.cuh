@@ -266,8 +266,12 @@ __device__ __forceinline__ void planes8(const uint32_t (&g)[NW], uint32_t t, uin
 //    queue, and phase 2 finishes them with all lanes of a warp busy on queued
 //    words, instead of every warp waiting for its slowest word;
 //  * per-sweep observables are summed in shared memory, not registers.
-template <int K, int TWW>
-__global__ void __launch_bounds__(256, 3) k_tiled32_bits(const uint32_t* __restrict__ in,
+//
+// MINB is the number of CTAs per SM the register budget is sized for: 3 (80
+// registers) for tiles that fit three CTAs' shared memory on an SM, 2 (up to
+// 128 registers) for taller tiles, which fit only two.
+template <int K, int TWW, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_tiled32_bits(const uint32_t* __restrict__ in,
                                                          uint32_t* __restrict__ out, int L, int Wc,
                                                          int n_ty, uint32_t t0, RngParams rng,
                                                          RecordSlots slots,
@@ -533,41 +537,57 @@ cudaError_t launch_tiled_k(const BitsLattice& in, uint32_t* out, const RngParams
   return cudaGetLastError();
 }
 
-template <int K, int TWW>
-cudaError_t launch_tiled32_k(const BitsLattice& in, uint32_t* out, const RngParams& rng,
-                                    uint32_t sweep0, const RecordSlots& slots,
-                                    unsigned long long* rec, int n_ty, int grid, cudaStream_t s) {
-  const size_t smem = tiled32_smem_bytes(in.L, K, n_ty, 32 * TWW);
+template <int K, int TWW, int MINB>
+cudaError_t launch_tiled32_v(const BitsLattice& in, uint32_t* out, const RngParams& rng,
+                             uint32_t sweep0, const RecordSlots& slots, unsigned long long* rec,
+                             int n_ty, int grid, size_t smem, int per_sm, cudaStream_t s) {
   static DeviceCache configured;  // per instantiation and device
   if ((long long)smem > configured.get()) {
-    cudaError_t e = cudaFuncSetAttribute(k_tiled32_bits<K, TWW>,
+    cudaError_t e = cudaFuncSetAttribute(k_tiled32_bits<K, TWW, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured.set((long long)smem);
   }
   const int n_tiles = n_ty * (in.Wc / (32 * TWW));
   if (grid <= 0) {
-    // resident CTAs, cached per device as (shared-memory size << 20 | grid)
-    static DeviceCache occ;
-    const long long memo = occ.get();
-    if ((memo >> 20) == (long long)smem) {
-      grid = (int)(memo & 0xfffff);
-    } else {
-      int per_sm = 0, dev = 0, sms = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per_sm, k_tiled32_bits<K, TWW>, 256, smem);
-      if (e != cudaSuccess) return e;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      grid = per_sm * sms;
-      occ.set(((long long)smem << 20) | (long long)grid);
-    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = per_sm * sms;
   }
   if (grid > n_tiles) grid = n_tiles;
   if (grid < 1) grid = 1;
-  k_tiled32_bits<K, TWW><<<grid, 256, smem, s>>>(in.planes, out, in.L, in.Wc, n_ty, sweep0, rng,
-                                                 slots, rec);
+  k_tiled32_bits<K, TWW, MINB><<<grid, 256, smem, s>>>(in.planes, out, in.L, in.Wc, n_ty, sweep0,
+                                                       rng, slots, rec);
   return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the 3-CTA variant decide the variant: three or more
+// run it, fewer (tiles too tall for three CTAs' shared memory) run the 2-CTA
+// variant with its larger register budget.
+template <int K, int TWW>
+cudaError_t launch_tiled32_k(const BitsLattice& in, uint32_t* out, const RngParams& rng,
+                                    uint32_t sweep0, const RecordSlots& slots,
+                                    unsigned long long* rec, int n_ty, int grid, cudaStream_t s) {
+  const size_t smem = tiled32_smem_bytes(in.L, K, n_ty, 32 * TWW);
+  // CTAs per SM of the 3-CTA variant, cached per device as (smem << 20 | CTAs)
+  static DeviceCache occ;
+  int per_sm = 0;
+  const long long memo = occ.get();
+  if ((memo >> 20) == (long long)smem) {
+    per_sm = (int)(memo & 0xfffff);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_tiled32_bits<K, TWW, 3>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiled32_bits<K, TWW, 3>, 256, smem);
+    if (e != cudaSuccess) return e;
+    occ.set(((long long)smem << 20) | (long long)per_sm);
+  }
+  if (per_sm >= 3)
+    return launch_tiled32_v<K, TWW, 3>(in, out, rng, sweep0, slots, rec, n_ty, grid, smem, per_sm, s);
+  return launch_tiled32_v<K, TWW, 2>(in, out, rng, sweep0, slots, rec, n_ty, grid, smem,
+                                     per_sm < 1 ? 1 : per_sm, s);
 }
 
 }  // namespace

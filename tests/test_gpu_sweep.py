@@ -100,11 +100,14 @@ def test_sweeps_bit_exact(layout, kernel, kargs, L, beta):
     assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
 
 
-@pytest.mark.parametrize("kargs", [(2, 37, 64), (1, 152, 32), (4, 64, 32), (2, 16, 64)])
+@pytest.mark.parametrize("kargs", [(2, 37, 64), (1, 152, 32), (4, 64, 32), (2, 16, 64), (4, 19, 32)])
 def test_tiled32_L4096(kargs):
     """Warp-per-row tiled kernel with its compaction queue, 64- and 32-word tiles;
     (2, 37, 64) and (2, 16, 64) (256-row strips, ~1700 undecided words per half
-    sweep) overflow the queue, so the in-place path runs too."""
+    sweep) overflow the queue, so the in-place path runs too.  Tiles too tall for
+    three CTAs' shared memory per SM ((2, 37, 64), (2, 16, 64), and (4, 19, 32):
+    216-row strips of 32 words, K = 4) run the variant compiled for two CTAs per
+    SM with the larger register budget; the others the three-CTA variant."""
     L, beta, seed, n = 4096, BETA_C, 31, 7
     ref, E_ref, M_ref = _oracle_run(L, beta, seed, n)
     got, E, M = _gpu_run(L, beta, seed, n, BITS, TILED, kargs)
