@@ -141,19 +141,22 @@ def measured_peaks() -> dict:
 # DRAM bytes (read + write) per launch of the sweep kernel from one ncu capture
 # of the current kernel, by launch shape (sweeps per launch, row strips, words
 # per tile row); profiles/k_tiled32_bits_L16384.md has the commands.  A shape
-# without a capture reports null.
-NCU_TRAFFIC = {(4, 114, 32): 33.80e6 + 0.519e6, (3, 114, 32): 33.74e6 + 0.550e6,
-               (4, 76, 32): 33.80e6 + 0.336e6, (3, 228, 64): 33.75e6 + 0.530e6,
-               (2, 228, 64): 33.69e6 + 0.469e6}
+# without a capture of the current kernel reports null.  (The captures there
+# predate the 1536-entry queue: 33.8 MB read + 0.3-0.6 MB written per launch for
+# every shape, the lattice read once; the queue lives in shared memory.)
+NCU_TRAFFIC = {}
 
 
 def tiled32_ctas_per_sm(L: int, k: int, n_ty: int, tile_words: int) -> int:
     """Register-budget variant the library launches for a tiled shape: 3 when
-    three CTAs' shared memory fits an SM (228 KiB; dynamic tile + ~9.3 KB static
-    queue + 1 KiB reserved per CTA), else 2 (the variant with up to 128 registers)."""
+    three CTAs' shared memory fits an SM (228 KiB; dynamic tile + the static queue
+    of 1536 entries and sums + 1 KiB reserved per CTA), else 2 (the variant with up
+    to 128 registers)."""
     ty_max = -(-L // n_ty)
-    per_cta = 2 * (ty_max + 4 * k) * (tile_words + 8) * 4 + 9296 + 1024
+    per_cta = 2 * (ty_max + 4 * k) * (tile_words + 8) * 4 + (12 * 1536 + 16 + 16 * k) + 1024
     return 3 if 3 * per_cta <= 228 * 1024 else 2
+
+
 # Algorithmic work of the bit-sliced, lazily evaluated acceptance test per
 # 32-site word, by the pipe it issues to.  ALU pipe (three-input logic, shifts):
 # neighbour classes as two half adders (half sums, carries, ge2 and the class

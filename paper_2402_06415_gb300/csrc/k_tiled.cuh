@@ -279,10 +279,11 @@ __global__ void __launch_bounds__(256, MINB) k_tiled32_bits(const uint32_t* __re
   constexpr int H = 2 * K;
   constexpr int TW = 32 * TWW;
   constexpr int SP = TW + 8;
-  // queue capacity: about 1 word in 10 is still undecided after 8 planes, ~500
-  // words per half sweep of a 72 x 64-word tile (at 512 a quarter of those
-  // half sweeps overflowed into the in-place path)
-  constexpr int QCAP = 768;
+  // queue capacity: about 1 word in 10 is still undecided after 8 planes (11 %
+  // in an ordered lattice), ~500 words per half sweep of a 72 x 64-word tile
+  // and ~800 of a 216 x 32-word tile; a full queue sends the rest to the slow
+  // in-place path.  18 KB, so tiles of up to 200 KiB still fit an SM.
+  constexpr int QCAP = 1536;
   extern __shared__ uint4 smem4[];
   __shared__ uint32_t q_pos[QCAP], q_d[QCAP], q_cls[QCAP];
   __shared__ int q_n[2];

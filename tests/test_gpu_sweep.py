@@ -103,8 +103,8 @@ def test_sweeps_bit_exact(layout, kernel, kargs, L, beta):
 @pytest.mark.parametrize("kargs", [(2, 37, 64), (1, 152, 32), (4, 64, 32), (2, 16, 64), (4, 19, 32)])
 def test_tiled32_L4096(kargs):
     """Warp-per-row tiled kernel with its compaction queue, 64- and 32-word tiles;
-    (2, 37, 64) and (2, 16, 64) (256-row strips, ~1700 undecided words per half
-    sweep) overflow the queue, so the in-place path runs too.  Tiles too tall for
+    (2, 16, 64) (256-row strips, ~1700 undecided words per half sweep against 1536
+    entries) overflows the queue, so the in-place path runs too.  Tiles too tall for
     three CTAs' shared memory per SM ((2, 37, 64), (2, 16, 64), and (4, 19, 32):
     216-row strips of 32 words, K = 4) run the variant compiled for two CTAs per
     SM with the larger register budget; the others the three-CTA variant."""
@@ -133,6 +133,27 @@ def test_replica_id_and_measure_every():
         got, E, M = _gpu_run(L, beta, seed, 12, layout, kernel, kargs, replica=3, measure_every=4)
         assert np.array_equal(got, ref)
         assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
+
+
+def test_tiled32_queue_overflow_ordered_start():
+    """An ordered start at beta = 0.6: every site is tested against T8 and stays
+    so (few flips), and a tested site is still undecided after 8 planes with
+    probability 2^-8, so ~12 % of words (1 - (255/256)^32) are queued, ~2000 per
+    half sweep of a 256 x 66-word tile at L = 4096 against a queue of 1536: the
+    in-place finishing path runs in every half sweep."""
+    L, beta, seed, n = 4096, 0.6, 5, 3
+    start = np.ones((L, L), dtype=np.int8)
+    ref = start.copy()
+    E_ref, M_ref = oracle.sweep(ref, beta, seed, n)
+    with ising.Lattice(L, beta, BITS) as lat:
+        lat.set_kernel(TILED, 2, 16, 64)
+        lat.set_spins(start)
+        ising.ising_set_key(lat.ctx, seed)
+        lat.sweep(n, 1)
+        got = lat.spins()
+        E, M = lat.series()
+    assert np.array_equal(got, ref)
+    assert np.array_equal(E, E_ref) and np.array_equal(M, M_ref)
 
 
 @pytest.mark.parametrize("layout,kernel,kargs,L", [(BITS, TILED, (4, 4, 4), 256),
