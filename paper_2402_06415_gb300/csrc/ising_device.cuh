@@ -8,7 +8,10 @@
 //   local energy change (Eq. S1 analogue), dE = 8 - 4 n_anti.
 // * The acceptance test "p < P(dE)" (step 3) against integer thresholds,
 //   evaluated bit-serially from the most significant plane: exact, and
-//   usually decided after a handful of planes.
+//   usually decided after a handful of planes.  (The tiled and batched
+//   kernels compare the planes of a Philox block as one borrow chain, the
+//   borrow of u - T carried up from the block's last plane, which gives the
+//   same verdicts with one logic operation less per plane.)
 //
 // Spin words: bit i of word w of colour-row (y, c) is site j = 32 w + i of the
 // L/2 colour-c sites of row y, at x = 2 j + ((y + c) & 1); bit = 1 means +1.
