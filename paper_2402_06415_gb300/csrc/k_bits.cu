@@ -11,13 +11,6 @@
 namespace ising {
 namespace {
 
-constexpr int kFull = 0xffffffff;
-
-__device__ __forceinline__ int wrap(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
 // Adds (a, b) over the block to dst[0], dst[1] (one atomic pair per block).
 // Every thread of the block must call it.
 __device__ void block_add2(unsigned long long a, unsigned long long b, unsigned long long* dst) {

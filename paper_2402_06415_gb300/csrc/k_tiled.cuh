@@ -10,8 +10,6 @@
 namespace ising {
 namespace {
 
-constexpr int kFull = 0xffffffff;
-
 __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
